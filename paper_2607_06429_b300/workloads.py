@@ -1,0 +1,360 @@
+"""Seeded synthetic workloads for the nested-sphere Helmholtz transmission problem.
+
+This module only *generates inputs*: tetrahedral volume meshes of a voxelised ball
+(each kept voxel Kuhn-split into six tetrahedra), icosphere interface meshes, and the
+material fields rho(x), c(x) sampled per element.  It contains none of the VSIE
+method's arithmetic (no quadrature, no Green's function, no operator weights), so it
+can feed both the CUDA library and the FP64 CPU oracle without coupling them.
+
+Geometry follows the nested layout of Sec. 2.1 (Fig. 1): Omega_2 inside Omega_1 inside
+the homogeneous exterior Omega_0, interfaces Gamma_1 (outer) and Gamma_2 (inner), every
+interface triangle oriented so that its normal points out of the subdomain it encloses.
+
+Mesh conventions handed to the library:
+  * ``vert``      float64 (n_vert, 3)
+  * ``tet``       int32 (n_tet, 4) vertex indices
+  * ``tri``       int32 (n_tri, 3) vertex indices, (b-a)x(c-a) points outward
+  * ``tri_iface`` int8 (n_tri,) 1 for Gamma_1, 2 for Gamma_2
+Material conventions:
+  * ``rho``, ``c``  float64 per tetrahedron
+  * ``grad_alpha``  float64 (n_tet, 3) or None (piecewise-constant density)
+  * ``tri_rho_in``  density limit on the side the triangle normal points away from
+  * ``tri_rho_out`` density limit on the side the normal points into
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable, Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    vert: np.ndarray
+    tet: np.ndarray
+    tri: np.ndarray
+    tri_iface: np.ndarray
+    rho: np.ndarray
+    c: np.ndarray
+    grad_alpha: Optional[np.ndarray]
+    tri_rho_in: np.ndarray
+    tri_rho_out: np.ndarray
+    k0: float
+    rho0: float = 1.0
+    c0: float = 1.0
+    tet_far_points: int = 1
+    near_radius: float = 0.0
+    tri_near_radius: float = 0.0
+    h: float = 0.0
+    R1: float = 1.0
+    R2: float = 0.0
+    layers: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def n_tet(self) -> int:
+        return int(self.tet.shape[0])
+
+    @property
+    def n_tri(self) -> int:
+        return int(self.tri.shape[0])
+
+    @property
+    def n(self) -> int:
+        return self.n_tet + self.n_tri
+
+    def n_far_sources(self) -> int:
+        return self.n_tet * self.tet_far_points + 3 * self.n_tri
+
+
+# ----------------------------------------------------------------------------- meshes
+
+_KUHN_PERMS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+
+
+def voxel_ball(n_grid: int, R1: float = 1.0):
+    """Voxel grid on [-R1, R1]^3 with n_grid cells per axis; a voxel is kept iff its
+    centre lies strictly inside the ball |x| < R1.  Each kept voxel is split into the six
+    Kuhn tetrahedra sharing its main diagonal.  Returns (vert, tet, h)."""
+    N = int(n_grid)
+    h = 2.0 * R1 / N
+    ctr = -R1 + (np.arange(N) + 0.5) * h
+    cx, cy, cz = np.meshgrid(ctr, ctr, ctr, indexing="ij")
+    keep = cx * cx + cy * cy + cz * cz < R1 * R1
+    vi, vj, vk = (a.astype(np.int64) for a in np.nonzero(keep))
+    nv = vi.shape[0]
+    M = N + 1
+
+    def node(i, j, k):
+        return (i * M + j) * M + k
+
+    unit = np.eye(3, dtype=np.int64)
+    tets = np.empty((nv, 6, 4), dtype=np.int64)
+    base = np.stack([vi, vj, vk], axis=1)
+    for t, perm in enumerate(_KUHN_PERMS):
+        p0 = base
+        p1 = p0 + unit[perm[0]]
+        p2 = p1 + unit[perm[1]]
+        p3 = p0 + 1
+        for q, pq in enumerate((p0, p1, p2, p3)):
+            tets[:, t, q] = node(pq[:, 0], pq[:, 1], pq[:, 2])
+    tets = tets.reshape(-1, 4)
+    used, inv = np.unique(tets, return_inverse=True)
+    tet = inv.reshape(-1, 4).astype(np.int32)
+    ii = used // (M * M)
+    jj = (used // M) % M
+    kk = used % M
+    vert = np.stack([-R1 + ii * h, -R1 + jj * h, -R1 + kk * h], axis=1).astype(np.float64)
+    return vert, tet, h
+
+
+def _icosahedron():
+    t = (1.0 + math.sqrt(5.0)) / 2.0
+    v = np.array(
+        [[-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0],
+         [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
+         [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]], dtype=np.float64)
+    f = np.array(
+        [[0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11],
+         [1, 5, 9], [5, 11, 4], [11, 10, 2], [10, 7, 6], [7, 1, 8],
+         [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8], [3, 8, 9],
+         [4, 9, 5], [2, 4, 11], [6, 2, 10], [8, 6, 7], [9, 8, 1]], dtype=np.int64)
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return v, f
+
+
+def icosphere(subdiv: int, radius: float):
+    """Icosphere of the given radius: the icosahedron refined ``subdiv`` times by edge
+    midpoints projected back to the sphere (20 * 4^subdiv triangles), every triangle
+    oriented outward.  Returns (vert, tri)."""
+    v, f = _icosahedron()
+    for _ in range(int(subdiv)):
+        e = np.concatenate([f[:, [0, 1]], f[:, [1, 2]], f[:, [2, 0]]], axis=0)
+        e.sort(axis=1)
+        ue, inv = np.unique(e, axis=0, return_inverse=True)
+        inv = inv.reshape(-1)
+        mid = v[ue[:, 0]] + v[ue[:, 1]]
+        mid /= np.linalg.norm(mid, axis=1, keepdims=True)
+        nf = f.shape[0]
+        mab = inv[:nf] + v.shape[0]
+        mbc = inv[nf:2 * nf] + v.shape[0]
+        mca = inv[2 * nf:] + v.shape[0]
+        v = np.concatenate([v, mid], axis=0)
+        a, b, c = f[:, 0], f[:, 1], f[:, 2]
+        f = np.concatenate([
+            np.stack([a, mab, mca], 1), np.stack([b, mbc, mab], 1),
+            np.stack([c, mca, mbc], 1), np.stack([mab, mbc, mca], 1)], axis=0)
+    v = v * radius
+    a, b, c = v[f[:, 0]], v[f[:, 1]], v[f[:, 2]]
+    outward = np.einsum("ij,ij->i", np.cross(b - a, c - a), a + b + c) > 0
+    f[~outward] = f[~outward][:, [0, 2, 1]]
+    return v, f.astype(np.int32)
+
+
+def _centroids(vert, idx):
+    return vert[idx].mean(axis=1)
+
+
+# ----------------------------------------------------------------------------- builders
+
+def nested_sphere(n_grid: int, R1: float, R2: float, subdiv1: int, subdiv2: Optional[int],
+                  k0: float, rho_fn: Callable, c_fn: Callable,
+                  grad_alpha_fn: Optional[Callable] = None,
+                  tet_far_points: int = 1, near_factor: float = 2.0,
+                  tri_near_factor: float = 2.0,
+                  rho0: float = 1.0, c0: float = 1.0, name: str = "nested",
+                  layers: Optional[dict] = None) -> Workload:
+    """Nested (or, with R2 = 0, single) penetrable ball.
+
+    ``rho_fn(x, dom)`` and ``c_fn(x, dom)`` give the material of subdomain ``dom`` (1 or
+    2) at points ``x`` (m, 3); ``grad_alpha_fn(x, dom)`` the gradient of
+    alpha = rho0/rho - 1 where the density varies smoothly.  A tetrahedron belongs to
+    Omega_2 iff its centroid satisfies |x| < R2.  Targets closer than
+    ``tri_near_factor`` times the longest interface edge to a triangle's centroid use the
+    accurate near rule for that triangle.
+    """
+    vert, tet, h = voxel_ball(n_grid, R1)
+    cen = _centroids(vert, tet)
+    dom = np.where(np.linalg.norm(cen, axis=1) < R2, 2, 1).astype(np.int8)
+    rho = np.empty(tet.shape[0])
+    c = np.empty(tet.shape[0])
+    ga = None if grad_alpha_fn is None else np.zeros((tet.shape[0], 3))
+    for d in (1, 2):
+        m = dom == d
+        if not m.any():
+            continue
+        rho[m] = rho_fn(cen[m], d)
+        c[m] = c_fn(cen[m], d)
+        if ga is not None:
+            ga[m] = grad_alpha_fn(cen[m], d)
+
+    verts = [vert]
+    tris = []
+    iface = []
+    rin = []
+    rout = []
+    off = vert.shape[0]
+    max_edge = 0.0
+    shells = [(1, R1, subdiv1)]
+    if R2 > 0 and subdiv2 is not None:
+        shells.append((2, R2, subdiv2))
+    for g, R, s in shells:
+        sv, sf = icosphere(s, R)
+        tc = sv[sf].mean(axis=1)
+        for q in range(3):
+            max_edge = max(max_edge, float(np.max(np.linalg.norm(
+                sv[sf[:, q]] - sv[sf[:, (q + 1) % 3]], axis=1))))
+        verts.append(sv)
+        tris.append(sf + off)
+        iface.append(np.full(sf.shape[0], g, dtype=np.int8))
+        if g == 1:
+            rin.append(rho_fn(tc, 1))
+            rout.append(np.full(sf.shape[0], rho0))
+        else:
+            rin.append(rho_fn(tc, 2))
+            rout.append(rho_fn(tc, 1))
+        off += sv.shape[0]
+    # Near-field cut: "within near_factor voxel widths".  Tetrahedron centroids sit on a
+    # lattice of spacing h/4, so squared centroid distances are multiples of h^2/16; the
+    # cut is placed halfway between the shell (near_factor*h)^2 and the next one, so
+    # rounding of coordinates can never flip an inclusion decision.
+    near = 0.0
+    if tet_far_points == 1 and near_factor > 0:
+        near = h * math.sqrt(near_factor ** 2 + 1.0 / 32.0)
+    return Workload(
+        name=name, vert=np.concatenate(verts, axis=0).astype(np.float64), tet=tet,
+        tri=np.concatenate(tris, axis=0).astype(np.int32),
+        tri_iface=np.concatenate(iface), rho=rho, c=c, grad_alpha=ga,
+        tri_rho_in=np.concatenate(rin).astype(np.float64),
+        tri_rho_out=np.concatenate(rout).astype(np.float64),
+        k0=float(k0), rho0=rho0, c0=c0, tet_far_points=int(tet_far_points),
+        near_radius=near, tri_near_radius=tri_near_factor * max_edge, h=h, R1=R1, R2=R2, layers=layers or {})
+
+
+def _const(v1, v2=None):
+    def f(x, dom):
+        return np.full(x.shape[0], v1 if dom == 1 else v2, dtype=np.float64)
+    return f
+
+
+def single_ball(n_grid=12, subdiv=3, k0=2.0, rho1=1.5, c1=0.7) -> Workload:
+    """Single penetrable unit ball, homogeneous inside, all tetrahedra on the 4-point rule
+    (the small FP64 workload; its exterior/interior field has the Mie series)."""
+    return nested_sphere(n_grid, 1.0, 0.0, subdiv, None, k0, _const(rho1), _const(c1),
+                         tet_far_points=4, name=f"ball{n_grid}_k{k0:g}",
+                         layers=dict(rho1=rho1, c1=c1))
+
+
+def layered_ball(n_grid, subdiv1, subdiv2, k0, R2=0.5, rho1=1.2, c1=0.8, rho2=3.0, c2=0.5,
+                 tet_far_points=1) -> Workload:
+    """Nested balls with constant layers (the layered-sphere series applies)."""
+    return nested_sphere(n_grid, 1.0, R2, subdiv1, subdiv2, k0, _const(rho1, rho2),
+                         _const(c1, c2), tet_far_points=tet_far_points,
+                         name=f"layered{n_grid}_k{k0:g}",
+                         layers=dict(rho1=rho1, c1=c1, rho2=rho2, c2=c2))
+
+
+def shell_x0(seed: int = 0, r_in: float = 0.5, r_out: float = 1.0) -> np.ndarray:
+    """Seeded point uniform in the spherical shell r_in < |x| < r_out."""
+    rng = np.random.default_rng(seed)
+    d = rng.normal(size=3)
+    d /= np.linalg.norm(d)
+    r = (rng.uniform(r_in ** 3, r_out ** 3)) ** (1.0 / 3.0)
+    return d * r
+
+
+def nested_k10(n_grid=80, subdiv=6, k0=10.0, seed=0) -> Workload:
+    """Nested spheres r=1 / r=0.5 at k0=10: shell rho=1.2 with a Gaussian sound-speed bump
+    c = 0.8 + 0.2 exp(-|x-x0|^2/0.1) (x0 seeded in the shell), core rho=3, c=0.5;
+    centroid rule in the far field, 4-point rule within two voxel widths."""
+    x0 = shell_x0(seed)
+
+    def rho_fn(x, dom):
+        return np.full(x.shape[0], 1.2 if dom == 1 else 3.0)
+
+    def c_fn(x, dom):
+        if dom == 2:
+            return np.full(x.shape[0], 0.5)
+        return 0.8 + 0.2 * np.exp(-np.sum((x - x0) ** 2, axis=1) / 0.1)
+
+    return nested_sphere(n_grid, 1.0, 0.5, subdiv, subdiv, k0, rho_fn, c_fn,
+                         tet_far_points=1, name=f"nested{n_grid}_k{k0:g}",
+                         layers=dict(rho1=1.2, rho2=3.0, c2=0.5, x0=x0.tolist()))
+
+
+def nested_k25(n_grid=128, subdiv=7, k0=25.0, seed=0) -> Workload:
+    """Nested spheres r=1 / r=0.6 at k0=25 with the layer densities of the k0=10 case and
+    a seeded random-phase sound speed c = 1 + 0.3 * mean_m cos(g_m.x + phi_m), |g_m| = k0/2,
+    which stays inside [0.7, 1.3]."""
+    rng = np.random.default_rng(seed)
+    g = rng.normal(size=(8, 3))
+    g *= (k0 / 2.0) / np.linalg.norm(g, axis=1, keepdims=True)
+    phi = rng.uniform(0, 2 * np.pi, size=8)
+
+    def rho_fn(x, dom):
+        return np.full(x.shape[0], 1.2 if dom == 1 else 3.0)
+
+    def c_fn(x, dom):
+        return 1.0 + 0.3 * np.mean(np.cos(x @ g.T + phi), axis=1)
+
+    return nested_sphere(n_grid, 1.0, 0.6, subdiv, subdiv, k0, rho_fn, c_fn,
+                         tet_far_points=1, name=f"nested{n_grid}_k{k0:g}")
+
+
+def nested_perturbed(n_grid=40, subdiv=5, k0=6.0, seed=0, sigma=0.05) -> Workload:
+    """Nested spheres r=1 / r=0.5 at k0=6 with per-element multiplicative perturbations
+    rho_e = rho_layer (1 + d_rho), c_e = c_layer (1 + d_c), d ~ N(0, sigma^2) seeded."""
+    w = nested_k10(n_grid, subdiv, k0, seed)
+    rng_r = np.random.default_rng(seed)
+    rng_c = np.random.default_rng(seed + 1)
+    w.rho = w.rho * (1.0 + sigma * rng_r.normal(size=w.n_tet))
+    w.c = w.c * (1.0 + sigma * rng_c.normal(size=w.n_tet))
+    w.name = f"perturbed{n_grid}_k{k0:g}"
+    return w
+
+
+def smooth_density_ball(n_grid=8, subdiv1=2, subdiv2=1, k0=3.0, R2=0.5) -> Workload:
+    """Small nested case with a smooth linear density perturbation in both layers, so that
+    all three operator kinds (volume single layer, volume adjoint double layer, interface
+    double layer on both interfaces) are active.  alpha = rho0/rho - 1 is linear:
+    alpha = a_d + g.x in layer d, with analytic gradient g."""
+    g = np.array([0.15, -0.1, 0.05])
+    a = {1: -0.2, 2: -0.5}
+
+    def rho_fn(x, dom):
+        return 1.0 / (1.0 + a[dom] + x @ g)
+
+    def c_fn(x, dom):
+        return np.full(x.shape[0], 0.9 if dom == 1 else 0.7)
+
+    def ga_fn(x, dom):
+        return np.tile(g, (x.shape[0], 1))
+
+    return nested_sphere(n_grid, 1.0, R2, subdiv1, subdiv2, k0, rho_fn, c_fn, ga_fn,
+                         tet_far_points=1, name=f"smooth{n_grid}_k{k0:g}")
+
+
+def random_vector(n: int, seed: int, nrhs: int = 1) -> np.ndarray:
+    """Seeded complex test vector(s), column-major (n, nrhs) when nrhs > 1."""
+    rng = np.random.default_rng(seed)
+    v = rng.normal(size=(n, nrhs)) + 1j * rng.normal(size=(n, nrhs))
+    return v[:, 0].copy() if nrhs == 1 else np.asfortranarray(v)
+
+
+def fibonacci_dirs(m: int) -> np.ndarray:
+    """m unit vectors on the golden-angle (Fibonacci) spiral."""
+    i = np.arange(m) + 0.5
+    z = 1.0 - 2.0 * i / m
+    r = np.sqrt(1.0 - z * z)
+    th = np.pi * (3.0 - math.sqrt(5.0)) * np.arange(m)
+    return np.stack([r * np.cos(th), r * np.sin(th), z], axis=1)
+
+
+CONFIGS = {
+    "ball12_k2": lambda: single_ball(12, 3, 2.0),
+    "nested80_k10": lambda: nested_k10(80, 6, 10.0),
+    "perturbed40_k6": lambda: nested_perturbed(40, 5, 6.0),
+    "nested128_k25": lambda: nested_k25(128, 7, 25.0),
+}

@@ -1,0 +1,385 @@
+"""Pins of the FP64 oracle against things other than itself: exactness of quadrature
+rules, closed forms checked against the PDE, finite differences of the Green's function,
+Gauss' theorem, the algebraic special cases of Sec. 2.2.6 (Remarks on a single domain,
+continuous density and the Lippmann-Schwinger equation), the mass-function identities
+of the interface-trace Lemma, GMRES against a direct solve, and the spherical-harmonic
+series of Sec. 3.2."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import series as S
+from oracle import vsie_oracle as O
+from paper_2607_06429_b300 import workloads as W
+
+RNG = np.random.default_rng(1234)
+
+
+def _bary(P, x):
+    """Barycentric coordinates of points x in the simplex P (independent solve)."""
+    d = P.shape[0] - 1
+    M = np.vstack([P.T, np.ones(d + 1)])
+    return np.linalg.lstsq(M, np.vstack([x.T, np.ones(x.shape[0])]), rcond=None)[0].T
+
+
+# ----------------------------------------------------------------------- quadrature
+
+def test_tet_rule_exact_degree2():
+    # int_T lam_i lam_j = |T|/20 (i != j), lam_i^2 -> |T|/10, lam_i -> |T|/4
+    # (Dirichlet integral 6|T| a!b!c!d!/(a+b+c+d+3)!).
+    P = RNG.normal(size=(4, 3))
+    vol = O.tet_volumes(P[None])[0]
+    pts = O.tet_rule4_points(P[None])[0]
+    lam = _bary(P, pts)
+    w = np.full(4, vol / 4)
+    for i in range(4):
+        assert np.isclose(w @ lam[:, i], vol / 4, rtol=1e-13)
+        assert np.isclose(w @ lam[:, i] ** 2, vol / 10, rtol=1e-13)
+        for j in range(i + 1, 4):
+            assert np.isclose(w @ (lam[:, i] * lam[:, j]), vol / 20, rtol=1e-13)
+    # degree 3 is not exact (sanity: the rule is genuinely degree 2)
+    assert not np.isclose(w @ lam[:, 0] ** 3, 6 * vol * 6 / math.factorial(6), rtol=1e-6)
+
+
+def test_tri_rule_exact_degree2():
+    P = RNG.normal(size=(3, 3))
+    area = 0.5 * np.linalg.norm(np.cross(P[1] - P[0], P[2] - P[0]))
+    pts = O.tri_rule3_points(P[None])[0]
+    # barycentrics in the triangle's plane
+    e1 = P[1] - P[0]
+    e2 = P[2] - P[0]
+    G = np.array([[e1 @ e1, e1 @ e2], [e1 @ e2, e2 @ e2]])
+    uv = np.linalg.solve(G, np.stack([(pts - P[0]) @ e1, (pts - P[0]) @ e2]))
+    lam = np.stack([1 - uv[0] - uv[1], uv[0], uv[1]], axis=1)
+    w = np.full(3, area / 3)
+    for i in range(3):
+        assert np.isclose(w @ lam[:, i], area / 3, rtol=1e-13)
+        assert np.isclose(w @ lam[:, i] ** 2, area / 6, rtol=1e-13)
+        for j in range(i + 1, 3):
+            assert np.isclose(w @ (lam[:, i] * lam[:, j]), area / 12, rtol=1e-13)
+
+
+# ----------------------------------------------------------------------- kernel
+
+@pytest.mark.parametrize("k", [0.7, 10.0, 25.0])
+def test_self_integral_vs_quadrature(k):
+    a = 0.037
+    re = integrate.quad(lambda r: math.cos(k * r) * r, 0, a, epsabs=1e-15)[0]
+    im = integrate.quad(lambda r: math.sin(k * r) * r, 0, a, epsabs=1e-15)[0]
+    # int_{|y|<a} e^{ikr}/(4 pi r) dy = int_0^a e^{ikr} r dr
+    assert np.isclose(O.ball_green_integral(a, k), re + 1j * im, rtol=1e-11)
+    assert np.isclose(O.ball_green_integral(a, 1e-4), a * a / 2, rtol=1e-6)
+
+
+@pytest.mark.parametrize("k", [1.0, 10.0, 25.0])
+def test_pair_kernel_vs_finite_differences(k):
+    x = RNG.normal(size=3) * 0.3
+    y = RNG.normal(size=3) * 0.3
+    v = RNG.normal(size=3)
+    hstep = 1e-6
+
+    def G(xx, yy):
+        r = np.linalg.norm(xx - yy)
+        return np.exp(1j * k * r) / (4 * np.pi * r)
+
+    grad = np.array([(G(x + hstep * e, y) - G(x - hstep * e, y)) / (2 * hstep)
+                     for e in np.eye(3)])
+    s = 0.37
+    val = O.pair_kernel((x - y)[None], np.array([s]), v[None], k)[0]
+    assert np.isclose(val, -G(x, y) * s + grad @ v, rtol=1e-7)
+    # double layer: v = -n w reproduces the normal derivative in y, dG/dn_y
+    n = RNG.normal(size=3)
+    n /= np.linalg.norm(n)
+    dGdn = (G(x, y + hstep * n) - G(x, y - hstep * n)) / (2 * hstep)
+    val = O.pair_kernel((x - y)[None], np.array([0.0]), (-n)[None], k)[0]
+    assert np.isclose(val, dGdn, rtol=1e-7)
+    # coincident points are masked to zero
+    assert O.pair_kernel(np.zeros((1, 3)), np.array([1.0]), v[None], k)[0] == 0
+
+
+def test_solid_angle_gauss():
+    v, f = W.icosphere(2, 1.0)
+    P = v[f]
+    for x, expect in [(np.array([0.1, -0.2, 0.3]), 4 * np.pi), (np.array([1.5, 0.3, 0.0]), 0.0)]:
+        om = O.solid_angle(P[:, 0], P[:, 1], P[:, 2], x[None])
+        assert abs(om.sum() - expect) < 1e-10
+
+
+def _refined(P, levels):
+    sub = P[None]
+    for _ in range(levels):
+        A, B, C = sub[:, 0], sub[:, 1], sub[:, 2]
+        ab, bc, ca = (A + B) / 2, (B + C) / 2, (C + A) / 2
+        sub = np.concatenate([np.stack(t, 1) for t in
+                              [(A, ab, ca), (B, bc, ab), (C, ca, bc), (ab, bc, ca)]])
+    return sub
+
+
+@pytest.mark.parametrize("k,tol", [(1e-6, 2e-6), (3.0, 2e-3)])
+def test_double_layer_near_vs_refined_quadrature(k, tol):
+    # brute force: 4^7 and 4^8 midpoint subtriangles, Richardson-extrapolated.  The
+    # Laplace part of the near rule is exact (k -> 0); at k > 0 only the bounded
+    # remainder carries the three-point rule's error.
+    P = np.array([[0.0, 0, 0], [0.1, 0, 0], [0.02, 0.09, 0]])
+    n = np.cross(P[1] - P[0], P[2] - P[0])
+    area = 0.5 * np.linalg.norm(n)
+    n /= np.linalg.norm(n)
+    for x in [np.array([0.04, 0.03, 0.02]), np.array([0.04, 0.03, -0.05]),
+              np.array([0.3, 0.2, 0.1])]:
+        vals = []
+        for L in (7, 8):
+            sub = _refined(P, L)
+            cen = sub.mean(axis=1)
+            w = area / sub.shape[0]
+            vals.append(np.sum(O.pair_kernel(x - cen, np.zeros(cen.shape[0]),
+                                             np.tile(-n * w, (cen.shape[0], 1)), k)))
+        ref = (4 * vals[1] - vals[0]) / 3
+        got = O.double_layer_near(x[None], P[None], n[None], np.array([area]), k)[0]
+        assert abs(got - ref) < tol * abs(ref), (x, got, ref)
+
+
+# ----------------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("k", [2.0, 6.0])
+def test_newton_potential_closed_form_solves_pde(k):
+    a = 0.8
+    h = 2e-4
+    for r in [0.2, 0.5, 1.3]:
+        # radial Laplacian u'' + 2u'/r
+        u = lambda rr: S.ball_newton_potential(rr, a, k)
+        lap = (u(r + h) - 2 * u(r) + u(r - h)) / h ** 2 + 2 / r * (u(r + h) - u(r - h)) / (2 * h)
+        src = 1.0 if r < a else 0.0
+        assert abs(-(lap + k * k * u(r)) - src) < 1e-5
+    # continuity of u and u' at r = a
+    assert np.isclose(S.ball_newton_potential(a - 1e-9, a, k),
+                      S.ball_newton_potential(a + 1e-9, a, k), atol=1e-8)
+    # value at the centre equals the self integral S(a)
+    assert np.isclose(S.ball_newton_potential(0.0, a, k), O.ball_green_integral(a, k))
+    g = S.ball_newton_potential_grad_r(0.4, a, k)
+    fd = (S.ball_newton_potential(0.4 + h, a, k) - S.ball_newton_potential(0.4 - h, a, k)) / (2 * h)
+    assert np.isclose(g, fd, rtol=1e-6)
+
+
+def test_double_layer_closed_form():
+    a, k = 0.7, 5.0
+    h = 2e-4
+    D = lambda rr: S.sphere_double_layer_of_one(rr, a, k)
+    for r in [0.3, 1.4]:
+        lap = (D(r + h) - 2 * D(r) + D(r - h)) / h ** 2 + 2 / r * (D(r + h) - D(r - h)) / (2 * h)
+        assert abs(lap + k * k * D(r)) < 1e-5 * (1 + abs(k * k * D(r)))
+    assert np.isclose(S.sphere_double_layer_of_one(0.2, a, 1e-5), -1.0, atol=1e-8)
+    assert abs(S.sphere_double_layer_of_one(2.0, a, 1e-5)) < 1e-8
+    # jump of the double layer across the sphere (interior - exterior) is -1
+    jump = S.sphere_double_layer_of_one(a - 1e-9, a, k) - S.sphere_double_layer_of_one(a + 1e-9, a, k)
+    assert np.isclose(jump, -1.0, atol=1e-6)
+
+
+# ----------------------------------------------------------------------- operators vs closed forms
+
+def _interior_rows(D, rmax, count=60):
+    r = np.linalg.norm(D.tet_cen, axis=1)
+    idx = np.nonzero(r < rmax)[0]
+    return np.random.default_rng(5).choice(idx, size=min(count, idx.shape[0]), replace=False)
+
+
+def test_volume_single_layer_vs_newton_potential():
+    # rho = rho0 (alpha = 0) and c chosen so that beta = 1: then
+    # (A 1)_i - m_i = -int_ball G dy = -u(x_i); the discrete ball is the voxelised one.
+    k = 2.0
+    errs = []
+    for N in (12, 20):
+        w = W.single_ball(N, 2, k, rho1=1.0, c1=k / math.sqrt(k * k + 1.0))
+        D = O.Discretisation.from_workload(w)
+        assert np.allclose(D.sdens, 1.0)
+        rows = _interior_rows(D, 0.6)
+        p = np.concatenate([np.ones(D.n_tet), np.zeros(D.n_tri)])
+        u = -(D.apply_rows(p, rows) - D.mass[rows])
+        ref = S.ball_newton_potential(np.linalg.norm(D.targets[rows], axis=1), 1.0, k)
+        errs.append(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+    assert errs[0] < 0.03 and errs[1] < errs[0]
+
+
+def test_interface_double_layer_vs_closed_form():
+    # p = 1 on Gamma_1 only, omega = 1 (rho_in = 0.5, rho_out = rho0 = 1): volume rows give
+    # (A p)_i = int_sphere dG/dn_y dS at interior points.
+    k = 3.0
+    errs = []
+    for sd in (2, 3):
+        w = W.single_ball(8, sd, k, rho1=1.0, c1=1.0)
+        w.tri_rho_in[:] = 0.5
+        D = O.Discretisation.from_workload(w)
+        assert np.allclose(D.tri_omega, 1.0)
+        rows = _interior_rows(D, 0.6)
+        p = np.concatenate([np.zeros(D.n_tet), np.ones(D.n_tri)])
+        got = D.apply_rows(p, rows)
+        ref = S.sphere_double_layer_of_one(np.linalg.norm(D.targets[rows], axis=1), 1.0, k)
+        errs.append(np.max(np.abs(got - ref)))
+    # O(h^2) convergence with the icosphere refinement (geometry + three-point rule)
+    assert errs[0] < 0.1 and errs[1] < errs[0] / 3
+
+
+def test_volume_adjoint_double_layer_vs_closed_form():
+    # alpha = a + g.x (linear), c = c0 so that beta - k0^2 alpha = 0 exactly: the volume
+    # rows reduce to m p + T[1] = m + g . grad u(x) with u the ball Newton potential.
+    k = 2.0
+    g = np.array([0.2, -0.1, 0.15])
+    errs = []
+    for N in (12, 20):
+        w = W.nested_sphere(N, 1.0, 0.0, 2, None, k,
+                            lambda x, d: 1.0 / (1.0 + 0.1 + x @ g),
+                            lambda x, d: np.ones(x.shape[0]),
+                            lambda x, d: np.tile(g, (x.shape[0], 1)), tet_far_points=4)
+        D = O.Discretisation.from_workload(w)
+        assert np.max(np.abs(D.sdens)) < 1e-12
+        rows = _interior_rows(D, 0.6)
+        p = np.concatenate([np.ones(D.n_tet), np.zeros(D.n_tri)])
+        got = D.apply_rows(p, rows) - D.mass[rows]
+        x = D.targets[rows]
+        r = np.linalg.norm(x, axis=1)
+        ref = S.ball_newton_potential_grad_r(r, 1.0, k) * (x @ g) / r
+        errs.append(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    assert errs[0] < 0.25 and errs[1] < errs[0]
+
+
+# ----------------------------------------------------------------------- special cases
+
+def test_reduction_lippmann_schwinger():
+    # rho = rho0 everywhere: alpha = 0, m = 1, interface columns vanish (Remark LS).
+    w = W.nested_sphere(6, 1.0, 0.5, 1, 1, 3.0, lambda x, d: np.ones(x.shape[0]),
+                        lambda x, d: np.full(x.shape[0], 0.8 if d == 1 else 0.6))
+    D = O.Discretisation.from_workload(w)
+    A = D.assemble()
+    assert np.all(A[:, D.n_tet:] - np.diag(D.mass)[:, D.n_tet:] == 0)
+    assert np.all(D.mass == 1.0)
+    assert np.allclose(D.sdens, D.beta, rtol=0, atol=0)
+
+
+def test_reduction_continuous_density():
+    # rho continuous across both interfaces: alpha_1 = 0 on Gamma_1 and alpha_2 = alpha_1
+    # on Gamma_2, so every interface column except the mass diagonal vanishes.
+    w = W.nested_sphere(6, 1.0, 0.5, 1, 1, 3.0, lambda x, d: np.ones(x.shape[0]) * 1.0,
+                        lambda x, d: np.full(x.shape[0], 0.9))
+    w.rho[:] = 1.0
+    D = O.Discretisation.from_workload(w)
+    A = D.assemble()
+    off = A[:, D.n_tet:].copy()
+    off[np.arange(D.n_tet, D.n) - 0, np.arange(D.n_tri)] -= D.mass[D.n_tet:]
+    assert np.all(off == 0)
+
+
+def test_reduction_single_domain():
+    # rho_2 = rho_1 and c_2 = c_1: the nested operator equals the single-domain one on the
+    # volume and Gamma_1 blocks, and the Gamma_2 columns vanish (Remark single domain).
+    f_rho = lambda x, d: np.full(x.shape[0], 1.7)
+    f_c = lambda x, d: np.full(x.shape[0], 0.8)
+    wn = W.nested_sphere(6, 1.0, 0.5, 1, 1, 3.0, f_rho, f_c)
+    ws = W.nested_sphere(6, 1.0, 0.0, 1, None, 3.0, f_rho, f_c)
+    ws.tri_near_radius = wn.tri_near_radius
+    Dn = O.Discretisation.from_workload(wn)
+    Ds = O.Discretisation.from_workload(ws)
+    An = Dn.assemble()
+    As = Ds.assemble()
+    nt, n1 = Dn.n_tet, Ds.n_tri
+    assert np.array_equal(An[:nt + n1, :nt + n1], As)
+    g2 = An[:, nt + n1:].copy()
+    g2[nt + n1 + np.arange(g2.shape[1]), np.arange(g2.shape[1])] -= Dn.mass[nt + n1:]
+    assert np.all(g2 == 0)
+
+
+def test_mass_function_identities():
+    # m on Gamma_1 = rho0/rho1 - alpha_1/2 and on Gamma_2 = rho0/rho2 - (alpha_2 - alpha_1)/2
+    w = W.layered_ball(6, 1, 1, 3.0)
+    D = O.Discretisation.from_workload(w)
+    g1 = w.tri_iface == 1
+    g2 = w.tri_iface == 2
+    m_t = D.mass[D.n_tet:]
+    a1 = 1.0 / w.tri_rho_in[g1] - 1.0
+    assert np.allclose(m_t[g1], 1.0 / w.tri_rho_in[g1] - a1 / 2, rtol=1e-15)
+    a2 = 1.0 / w.tri_rho_in[g2] - 1.0
+    a1b = 1.0 / w.tri_rho_out[g2] - 1.0
+    assert np.allclose(m_t[g2], 1.0 / w.tri_rho_in[g2] - (a2 - a1b) / 2, rtol=1e-15)
+    assert np.allclose(D.mass[:D.n_tet], 1.0 / w.rho)
+
+
+# ----------------------------------------------------------------------- solver, adjoint
+
+def test_gmres_matches_direct_solve():
+    n = 120
+    A = np.eye(n) + 0.3 * RNG.normal(size=(n, n)) / math.sqrt(n) + 0.3j * RNG.normal(size=(n, n)) / math.sqrt(n)
+    b = RNG.normal(size=n) + 1j * RNG.normal(size=n)
+    x, it, rel = O.gmres(lambda v: A @ v, b, tol=1e-10, maxiter=n)
+    assert rel <= 1e-10
+    assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) <= 1.01e-10
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-8, atol=1e-9)
+
+
+def test_adjoint_identity():
+    w = W.smooth_density_ball(6, 1, 1)
+    D = O.Discretisation.from_workload(w)
+    x = W.random_vector(D.n, 1)
+    y = W.random_vector(D.n, 2)
+    lhs = np.vdot(y, D.apply(x))
+    rhs = np.vdot(D.adjoint_apply(y), x)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+# ----------------------------------------------------------------------- physics: series
+
+def _solve(D, d):
+    A = D.assemble()
+    return np.linalg.solve(A, D.plane_wave(d))
+
+
+def test_penetrable_ball_vs_mie_series():
+    k, d = 2.0, np.array([0.0, 0.0, 1.0])
+    out = []
+    for N, sd in ((8, 2), (12, 3)):
+        w = W.single_ball(N, sd, k)
+        D = O.Discretisation.from_workload(w)
+        x = _solve(D, d)
+        r = np.linalg.norm(D.tet_cen, axis=1)
+        m = r < 0.8
+        ref_v = S.layered_sphere_field(D.tet_cen[m], d, k, [1.0], [1.5], [0.7])
+        ref_s = S.layered_sphere_field(D.tri_cen, d, k, [1.0], [1.5], [0.7])
+        dirs = W.fibonacci_dirs(32)
+        ref_f = S.layered_sphere_far_field(dirs, d, k, [1.0], [1.5], [0.7])
+        out.append((np.linalg.norm(x[:D.n_tet][m] - ref_v) / np.linalg.norm(ref_v),
+                    np.linalg.norm(x[D.n_tet:] - ref_s) / np.linalg.norm(ref_s),
+                    np.linalg.norm(D.far_field(x, dirs) - ref_f) / np.linalg.norm(ref_f)))
+    (v8, s8, f8), (v12, s12, f12) = out
+    assert v8 < 0.06 and s8 < 0.06 and f8 < 0.12
+    assert v12 < 0.025 and s12 < 0.025 and f12 < 0.04
+    assert v12 < v8 and s12 < s8 and f12 < f8
+
+
+def test_layered_sphere_vs_series():
+    # constant layers with a density jump on both interfaces: both double-layer terms and
+    # the nested mass function matter.
+    k, d = 3.0, np.array([1.0, 0.0, 0.0])
+    w = W.layered_ball(12, 3, 2, k, R2=0.5, rho1=1.2, c1=0.8, rho2=3.0, c2=0.5,
+                       tet_far_points=4)
+    D = O.Discretisation.from_workload(w)
+    x = _solve(D, d)
+    r = np.linalg.norm(D.tet_cen, axis=1)
+    m = (r < 0.8) & (np.abs(r - 0.5) > 0.15)
+    args = (d, k, [1.0, 0.5], [1.2, 3.0], [0.8, 0.5])
+    ref_v = S.layered_sphere_field(D.tet_cen[m], *args)
+    dirs = W.fibonacci_dirs(32)
+    ref_f = S.layered_sphere_far_field(dirs, *args)
+    ev = np.linalg.norm(x[:D.n_tet][m] - ref_v) / np.linalg.norm(ref_v)
+    ef = np.linalg.norm(D.far_field(x, dirs) - ref_f) / np.linalg.norm(ref_f)
+    assert ev < 0.06 and ef < 0.06, (ev, ef)
+
+
+def test_layered_series_reduces_to_single_ball():
+    # two layers with identical material equal one layer
+    d = np.array([0.0, 0.0, 1.0])
+    x = RNG.uniform(-1.2, 1.2, size=(40, 3))
+    a = S.layered_sphere_field(x, d, 2.0, [1.0, 0.5], [1.5, 1.5], [0.7, 0.7])
+    b = S.layered_sphere_field(x, d, 2.0, [1.0], [1.5], [0.7])
+    assert np.allclose(a, b, rtol=1e-9, atol=1e-10)
+    # no contrast: the total field is the incident plane wave
+    c = S.layered_sphere_field(x, d, 2.0, [1.0], [1.0], [1.0])
+    assert np.allclose(c, np.exp(2j * x[:, 2]), atol=1e-10)
