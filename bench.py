@@ -1,0 +1,284 @@
+"""Benchmark of the nested-VSIE operator apply on one B300 (and replicas under torchrun).
+
+A step is one full matrix-free apply of the discretised VSIE operator (charge prescale,
+far-field N-body sums over volume and interface source points, FP64 near-field/self
+correction and mass) on the nested-sphere k0 = 10 workload: 80^3 voxel grid clipped to the
+unit ball (1,608,576 tetrahedra, centroid far rule, four-point rule within two voxel
+widths), two icospheres at subdivision 6 (163,840 triangles), 1,772,416 collocation
+points x 2,100,096 far-field source points = 3.72e12 pair interactions per apply.
+
+metric value: interactions/s of the mixed-precision (FP32 far field) apply, inputs
+resident in HBM.  e2e: the same through vsie_apply_host (host buffers, copies timed).
+--impl reference: the FP64 CPU oracle on a bounded sample of rows of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "nested80_k10"
+METRIC = "Helmholtz interactions/s & GMRES solve time, mixed vs FP64 on 1 B300 at rel err 1e-5"
+UNIT = "interactions/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def make_workload(name):
+    from paper_2607_06429_b300 import workloads as W
+    return W.CONFIGS[name]()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_rows_rate(w, rows_count, seed=0, time_budget=None):
+    """FP64 CPU oracle applied to a seeded sample of rows; returns (interactions/s, sample
+    description, seconds)."""
+    from oracle import vsie_oracle as O
+    from paper_2607_06429_b300 import workloads as W
+    D = O.Discretisation.from_workload(w)
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(w.n, size=rows_count, replace=False))
+    x = W.random_vector(w.n, 1)
+    t0 = time.perf_counter()
+    done = 0
+    for r in rows:
+        D.apply_rows(x, np.array([r]))
+        done += 1
+        if time_budget and time.perf_counter() - t0 > time_budget:
+            break
+    dt = time.perf_counter() - t0
+    nsrc = w.n_far_sources()
+    return done * nsrc / dt, f"{done} seeded rows x {nsrc} far-field source points (FP64 numpy, 1 thread)", dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = make_workload(args.workload)
+    vals = []
+    for _ in range(args.warmup):
+        oracle_rows_rate(w, 2, seed=99)
+    for s in range(args.steps):
+        v, sample, _ = oracle_rows_rate(w, 4, seed=s)
+        vals.append(v)
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"per step: {sample}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def flush_l2(torch, buf):
+    buf.add_(1.0)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", type=int, default=32)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2607_06429_b300 import binding as B
+    from paper_2607_06429_b300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    w = make_workload(args.workload)
+    t0 = time.perf_counter()
+    op = B.Operator.from_workload(w)
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    n, nsrc = op.n, op.n_far_sources
+    inter = float(n) * float(nsrc)
+
+    x = torch.from_numpy(W.random_vector(n, 1 + rank)).cuda()
+    y = torch.empty_like(x)
+    l2buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        op.apply(x, y, precision=args.precision)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    phase_ms = []
+    launches = 0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush_l2(torch, l2buf)
+            ev[s][0].record(stream)
+            op.apply(x, y, precision=args.precision)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        # per-kernel device times of the same apply (events between its phases)
+        for s in range(min(args.steps, 3)):
+            flush_l2(torch, l2buf)
+            ms, launches = op.apply_timed(x, y, precision=args.precision)
+            phase_ms.append(ms)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_ms = float(np.mean(step_ms))
+    if world > 1:
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+        dist.barrier()
+    clocks = clk.summary()
+
+    # end-to-end through the host-buffer entry point (pinned host memory)
+    hx = torch.from_numpy(W.random_vector(n, 3)).pin_memory()
+    hy = torch.empty_like(hx).pin_memory()
+    op.apply_host_ptr(hx.data_ptr(), hy.data_ptr(), 1, args.precision)
+    e2e_ms = []
+    for _ in range(max(2, min(args.steps, 3))):
+        t1 = time.perf_counter()
+        op.apply_host_ptr(hx.data_ptr(), hy.data_ptr(), 1, args.precision)
+        e2e_ms.append((time.perf_counter() - t1) * 1e3)
+    e2e_t = float(np.mean(e2e_ms))
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    value = inter * world / (t_ms * 1e-3)
+    # roofline of the dominant kernel: FP32 far-field sum over volume sources (G class)
+    pk, pk_kind = peaks()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    f_mhz = clocks["sm_mhz"] or pk.get("sm_max_mhz", 2032.0)
+    g_ms = float(np.mean([p["far_volume"] for p in phase_ms]))
+    n_g = nsrc - 3 * w.n_tri if w.grad_alpha is None else None
+    rf = None
+    if n_g:
+        achieved = n * n_g / (g_ms * 1e-3)
+        # ALU roofline: 3 MUFU ops (rsqrt, sin, cos) per pair at 16/clk/SM vs ~20 FP32-pipe
+        # ops per pair at 128/clk/SM; the binding pipe is the MUFU one.
+        xu = n_sm * 16 * f_mhz * 1e6 / 3.0
+        fma = n_sm * 128 * f_mhz * 1e6 / 20.0
+        peak = min(xu, fma)
+        rf = {"bound": "alu", "kernel": "far_g_kernel<float,4>", "achieved": achieved / 1e9,
+              "peak": peak / 1e9, "unit": "Ginteractions/s", "frac": achieved / peak,
+              "peak_basis": f"min(MUFU {n_sm} SMs x 16/clk / 3 per pair, FP32 {n_sm} x 128/clk / 20 per pair) at {f_mhz:.0f} MHz (median SM clock sampled under load)",
+              "traffic": None, "kernel_ms": g_ms}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, sample, dt = oracle_rows_rate(w, 64, seed=0, time_budget=args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               "seconds": round(dt, 2)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_targets": n, "n_far_sources": nsrc,
+                   "interactions_per_step": inter, "nnz_correction": op.nnz,
+                   "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "e2e": {"value": inter / (e2e_t * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 16 * n,
+                "d2h_bytes_per_step": 16 * n, "ms_per_step": e2e_t},
+        "gpu_launches": launches * args.steps,
+        "phase_ms": {k: float(np.mean([p[k] for p in phase_ms])) for k in phase_ms[0]},
+        "create_s": create_s,
+        "roofline": rf, "peaks": pk_kind,
+        "cpu_baseline": cpu,
+        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * vsie.h -- C ABI of libvsie: the matrix-free apply and GMRES solve of the discretised
+ * nested volume-surface integral equation (VSIE) for heterogeneous acoustic
+ * transmission problems, on one NVIDIA B300 (sm_103a).
+ *
+ * Operator (Eq. vsie, Theorem "VSIE", with the block system of Sec. 2.3 "Linear
+ * system"): for every collocation point x_i (tetrahedron centroids, then interface
+ * triangle centroids)
+ *
+ *   (A p)_i = m_i p_i
+ *           - sum_e int_e G(x_i,y) (beta - k0^2 alpha)_e dy p_e          (single layer V)
+ *           + sum_e div_x int_e G(x_i,y) grad(alpha)_e dy p_e            (adjoint DL, T)
+ *           + sum_t int_t dG(x_i,y)/dn_y omega_t dS_y p_t                (double layer K)
+ *
+ * G = exp(i k0 r)/(4 pi r) (Eq. greens_function), alpha = rho0/rho - 1 (Eq. alpha),
+ * beta = (rho0/rho)(omega/c)^2 - (omega/c0)^2 (Eq. beta), m from Eq. (mass_function),
+ * omega_t = alpha_1 on Gamma_1 and alpha_2 - alpha_1 on Gamma_2.  P0 unknowns with point
+ * collocation (Sec. 2.3.4).  Time convention e^{-i omega t}.
+ *
+ * Conventions shared by every call:
+ *  - Unknown order: [tetrahedra in input order | triangles in input order]; n = n_tet + n_tri.
+ *  - Complex vectors are interleaved (re, im) float64, i.e. C99 double _Complex /
+ *    torch.complex128.  Multi-RHS blocks are column-major n x nrhs (column j at x + 2*n*j).
+ *  - Pointers named d_* are DEVICE pointers on the handle's device, caller-owned; the
+ *    library never frees them.  Pointers named h_* are host pointers, caller-owned.
+ *  - ``stream`` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls
+ *    are asynchronous with respect to the host unless stated otherwise; all work of a
+ *    handle must be issued on one stream at a time.
+ *  - No exception crosses the ABI: every call returns a vsie_status; on error
+ *    vsie_last_error() holds a message (thread-local) and outputs are unspecified.
+ */
+#ifndef VSIE_H
+#define VSIE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VSIE_OK = 0,
+  VSIE_ERR_ARG = 1,           /* invalid argument (null pointer, size, option)          */
+  VSIE_ERR_MESH = 2,          /* degenerate element, index out of range                 */
+  VSIE_ERR_CUDA = 3,          /* a CUDA runtime call failed                             */
+  VSIE_ERR_OOM = 4,           /* device allocation failed                               */
+  VSIE_ERR_NOT_CONVERGED = 5, /* solver stopped at its iteration limit (x still written) */
+  VSIE_ERR_BREAKDOWN = 6,     /* Krylov breakdown with a nonzero residual               */
+  VSIE_ERR_NAN = 7            /* non-finite input or intermediate value                 */
+} vsie_status;
+
+typedef struct vsie_handle vsie_handle; /* opaque, library-owned */
+
+/* Geometry of Omega_1, Omega_2, Gamma_1, Gamma_2 (Sec. 2.1, Fig. 1).  Host arrays,
+ * caller-owned, copied during vsie_create. */
+typedef struct {
+  int64_t n_vert;
+  const double* vert;       /* 3*n_vert, xyz per vertex                               */
+  int64_t n_tet;
+  const int32_t* tet;       /* 4*n_tet vertex indices (any orientation)               */
+  int64_t n_tri;
+  const int32_t* tri;       /* 3*n_tri vertex indices; (b-a)x(c-a) must point out of
+                               the subdomain the interface encloses (n_1 on Gamma_1,
+                               n_2 on Gamma_2)                                        */
+} vsie_mesh;
+
+/* Material (Eqs. density, speed_of_sound): per-tetrahedron values and the one-sided
+ * density limits on every interface triangle.  Host arrays, caller-owned, copied. */
+typedef struct {
+  double rho0, c0;          /* exterior density and speed of sound                    */
+  const double* rho;        /* n_tet, > 0                                             */
+  const double* c;          /* n_tet, > 0                                             */
+  const double* grad_alpha; /* 3*n_tet gradient of alpha per tetrahedron, or NULL for
+                               a piecewise-constant density (adjoint DL term absent)  */
+  const double* tri_rho_in; /* n_tri: density limit on the side the normal leaves    */
+  const double* tri_rho_out;/* n_tri: density limit on the side the normal enters
+                               (rho0 on Gamma_1, rho_1 on Gamma_2)                    */
+} vsie_material;
+
+/* Discretisation options (readings of Sec. 2.3.4 for tetrahedra and flat triangles). */
+typedef struct {
+  int32_t tet_far_points;   /* 1: centroid rule in the far field; 4: the degree-2
+                               four-point rule on every tetrahedron                   */
+  double near_radius;       /* with tet_far_points == 1: tetrahedra whose centroid is
+                               closer than this to a target use the four-point rule   */
+  double tri_near_radius;   /* triangles whose centroid is closer than this to a target
+                               use the singularity-subtracted rule (exact Laplace
+                               solid angle + three-point Helmholtz remainder); 0 = off */
+  int32_t tile_override;    /* 0 = library default launch shape                       */
+} vsie_options;
+
+/* Build the discrete operator on the current CUDA device: element geometry, material
+ * weights, far-field source points and the FP64 near-field/self correction matrix
+ * (computed on the device).  k0 = omega/c0 > 0 is the exterior wavenumber.  Blocking.
+ * Errors: VSIE_ERR_ARG (null/size), VSIE_ERR_MESH (index out of range, zero-volume
+ * element, non-positive material), VSIE_ERR_OOM, VSIE_ERR_CUDA. */
+vsie_status vsie_create(const vsie_mesh* mesh, const vsie_material* mat, double k0,
+                        const vsie_options* opt, vsie_handle** out);
+
+void vsie_destroy(vsie_handle* h);
+
+/* Sizes of the discrete system. */
+vsie_status vsie_sizes(const vsie_handle* h, int64_t* n, int64_t* n_far_sources,
+                       int64_t* nnz_correction);
+
+/* y = A x for nrhs columns (Eq. vsie at every collocation point).  precision 32: far-field
+ * sums in FP32 with per-tile FP64 accumulation, correction and mass in FP64;
+ * precision 64: everything in FP64.  x, y: device complex128, n x nrhs column-major,
+ * must not alias.  Errors: VSIE_ERR_ARG, VSIE_ERR_CUDA. */
+vsie_status vsie_apply(vsie_handle* h, const void* d_x, void* d_y, int32_t nrhs,
+                       int32_t precision, void* stream);
+
+/* Same operator with host buffers: copies x to the device, applies, copies y back and
+ * synchronises the stream before returning.  Uses library-owned device buffers. */
+vsie_status vsie_apply_host(vsie_handle* h, const double* h_x, double* h_y, int32_t nrhs,
+                            int32_t precision, void* stream);
+
+/* One vsie_apply (nrhs = 1) with CUDA events recorded on ``stream`` between its phases;
+ * blocks until done.  kernel_ms[4] receives the device time of: the charge prescale, the
+ * far-field sum over volume sources without a vector weight, the far-field sum over
+ * sources with a vector weight (interfaces, heterogeneous density), and the correction
+ * + mass kernel.  *launches (optional) receives the number of kernels launched. */
+vsie_status vsie_apply_timed(vsie_handle* h, const void* d_x, void* d_y, int32_t precision,
+                             void* stream, double* kernel_ms, int32_t* launches);
+
+/* x = A^H y (conjugate transpose), same layouts and precisions as vsie_apply. */
+vsie_status vsie_adjoint_apply(vsie_handle* h, const void* d_y, void* d_x, int32_t nrhs,
+                               int32_t precision, void* stream);
+
+/* Right-hand side of Eq. (planewave): b_i = exp(i k0 x_i . d_j) for ndir unit directions
+ * (host array 3*ndir, normalised by the library); b: device complex128 n x ndir. */
+vsie_status vsie_plane_wave_rhs(vsie_handle* h, const double* h_dirs, int32_t ndir,
+                                void* d_b, void* stream);
+
+/* Far-field pattern of the scattered field from Eq. (vsie) used as a representation
+ * formula in Omega_0 (Sec. 2.3.1): p_inf(xhat) = (1/4pi) sum_j e^{-ik0 xhat.y_j}
+ * (s_j - i k0 xhat.v_j) p_e(j) over the far-field source points.  p: device complex128
+ * n x nrhs; dirs: host 3*ndir; out: device complex128 ndir x nrhs.  FP64. */
+vsie_status vsie_far_field(vsie_handle* h, const void* d_p, int32_t nrhs,
+                           const double* h_dirs, int32_t ndir, void* d_out, void* stream);
+
+typedef struct {
+  int32_t mode;             /* 64: FP64 GMRES with the FP64 apply (the paper's solver,
+                               Sec. 3.1); 32: FP64 iterative refinement whose residual
+                               uses the FP64 apply around inner FP32-apply GMRES       */
+  double tol;               /* relative residual ||b - A x|| / ||b|| to reach          */
+  int32_t max_iters;        /* total GMRES iterations (all inner solves)               */
+  int32_t restart;          /* Krylov basis size; 0 = max_iters (no restart)           */
+  double inner_tol;         /* mode 32: relative tolerance of each inner solve         */
+  int32_t max_refinements;  /* mode 32: outer refinement steps                         */
+} vsie_solve_opts;
+
+typedef struct {
+  int32_t iterations;       /* total GMRES iterations                                  */
+  int32_t refinements;      /* outer steps (mode 32)                                   */
+  double rel_residual;      /* final ||b - A x|| / ||b|| with the FP64 apply           */
+  int32_t fp64_applies;     /* number of FP64 operator applications                    */
+  int32_t fp32_applies;     /* number of FP32 operator applications                    */
+} vsie_solve_info;
+
+/* Solve A x = b for one right-hand side with x0 = 0 (GMRES, no preconditioner, as in
+ * Sec. 3.1).  b, x: device complex128 (n).  Blocking (reads residual norms on the host).
+ * Returns VSIE_ERR_NOT_CONVERGED (x still written, info filled) when the limits are hit. */
+vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
+                       const vsie_solve_opts* opts, vsie_solve_info* info, void* stream);
+
+/* Thread-local description of the last error ("" if none). */
+const char* vsie_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VSIE_H */

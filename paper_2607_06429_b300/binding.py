@@ -1,0 +1,278 @@
+"""Thin ctypes binding of libvsie (argument marshalling only; every step of the operator
+runs in the library's CUDA kernels).  Names follow the C ABI in include/vsie.h.
+
+Device vectors are torch.complex128 CUDA tensors; a block of right-hand sides has shape
+(nrhs, n), which in memory is the column-major n x nrhs layout the library expects.
+There is no CPU fallback: if the library or a CUDA device is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvsie.so")
+
+STATUS = {
+    0: "VSIE_OK", 1: "VSIE_ERR_ARG", 2: "VSIE_ERR_MESH", 3: "VSIE_ERR_CUDA", 4: "VSIE_ERR_OOM",
+    5: "VSIE_ERR_NOT_CONVERGED", 6: "VSIE_ERR_BREAKDOWN", 7: "VSIE_ERR_NAN",
+}
+VSIE_ERR_NOT_CONVERGED = 5
+
+EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_apply_host",
+           "vsie_apply_timed",
+           "vsie_adjoint_apply", "vsie_plane_wave_rhs", "vsie_far_field", "vsie_solve",
+           "vsie_last_error")
+
+
+class VsieError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("n_vert", ctypes.c_int64), ("vert", ctypes.c_void_p),
+                ("n_tet", ctypes.c_int64), ("tet", ctypes.c_void_p),
+                ("n_tri", ctypes.c_int64), ("tri", ctypes.c_void_p)]
+
+
+class _Material(ctypes.Structure):
+    _fields_ = [("rho0", ctypes.c_double), ("c0", ctypes.c_double),
+                ("rho", ctypes.c_void_p), ("c", ctypes.c_void_p),
+                ("grad_alpha", ctypes.c_void_p), ("tri_rho_in", ctypes.c_void_p),
+                ("tri_rho_out", ctypes.c_void_p)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("tet_far_points", ctypes.c_int32), ("near_radius", ctypes.c_double),
+                ("tri_near_radius", ctypes.c_double), ("tile_override", ctypes.c_int32)]
+
+
+class _SolveOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("max_iters", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("inner_tol", ctypes.c_double), ("max_refinements", ctypes.c_int32)]
+
+
+class _SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("fp64_applies", ctypes.c_int32),
+                ("fp32_applies", ctypes.c_int32)]
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    iterations: int
+    refinements: int
+    rel_residual: float
+    fp64_applies: int
+    fp32_applies: int
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libvsie.so (built in-tree by ``paper_2607_06429_b300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libvsie.so not found at {path}; run paper_2607_06429_b300/build.py")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.vsie_create.argtypes = [ctypes.POINTER(_Mesh), ctypes.POINTER(_Material), D,
+                                ctypes.POINTER(_Options), ctypes.POINTER(P)]
+    lib.vsie_destroy.argtypes = [P]
+    lib.vsie_destroy.restype = None
+    lib.vsie_sizes.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    lib.vsie_apply.argtypes = [P, P, P, I32, I32, P]
+    lib.vsie_apply_host.argtypes = [P, P, P, I32, I32, P]
+    lib.vsie_adjoint_apply.argtypes = [P, P, P, I32, I32, P]
+    lib.vsie_apply_timed.argtypes = [P, P, P, I32, P, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(I32)]
+    lib.vsie_plane_wave_rhs.argtypes = [P, P, I32, P, P]
+    lib.vsie_far_field.argtypes = [P, P, I32, P, I32, P, P]
+    lib.vsie_solve.argtypes = [P, P, P, ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), P]
+    lib.vsie_last_error.argtypes = []
+    lib.vsie_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("vsie_destroy", "vsie_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, allow=()):
+    if status != 0 and status not in allow:
+        raise VsieError(status, _lib.vsie_last_error().decode())
+    return status
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex128:
+        raise TypeError(f"{name} must be a CUDA complex128 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Operator:
+    """The discretised nested VSIE operator on the current CUDA device (vsie_create)."""
+
+    def __init__(self, vert, tet, tri, rho, c, tri_rho_in, tri_rho_out, k0, rho0=1.0, c0=1.0,
+                 grad_alpha=None, tet_far_points=1, near_radius=0.0, tri_near_radius=0.0,
+                 tile_override=0):
+        lib = load_library()
+        self._keep = dict(vert=_f64(vert).reshape(-1), tet=_i32(tet).reshape(-1),
+                          tri=_i32(tri).reshape(-1), rho=_f64(rho), c=_f64(c),
+                          ga=None if grad_alpha is None else _f64(grad_alpha).reshape(-1),
+                          rin=_f64(tri_rho_in), rout=_f64(tri_rho_out))
+        k = self._keep
+        mesh = _Mesh(k["vert"].shape[0] // 3, _ptr(k["vert"]), k["tet"].shape[0] // 4,
+                     _ptr(k["tet"]), k["tri"].shape[0] // 3, _ptr(k["tri"]))
+        mat = _Material(float(rho0), float(c0), _ptr(k["rho"]), _ptr(k["c"]), _ptr(k["ga"]),
+                        _ptr(k["rin"]), _ptr(k["rout"]))
+        opt = _Options(int(tet_far_points), float(near_radius), float(tri_near_radius),
+                       int(tile_override))
+        h = ctypes.c_void_p()
+        _check(lib.vsie_create(ctypes.byref(mesh), ctypes.byref(mat), float(k0),
+                               ctypes.byref(opt), ctypes.byref(h)))
+        self._h = h
+        self._keep = None
+        n, nf, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.vsie_sizes(h, ctypes.byref(n), ctypes.byref(nf), ctypes.byref(nnz)))
+        self.n, self.n_far_sources, self.nnz = n.value, nf.value, nnz.value
+        self.k0 = float(k0)
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        return cls(w.vert, w.tet, w.tri, w.rho, w.c, w.tri_rho_in, w.tri_rho_out, w.k0,
+                   w.rho0, w.c0, w.grad_alpha, w.tet_far_points, w.near_radius,
+                   w.tri_near_radius, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.vsie_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ calls
+    def _nrhs(self, x):
+        if x.dim() == 1:
+            if x.shape[0] != self.n:
+                raise ValueError("vector length must equal n")
+            return 1
+        if x.dim() != 2 or x.shape[1] != self.n:
+            raise ValueError("blocks must have shape (nrhs, n)")
+        return x.shape[0]
+
+    def apply(self, x, y=None, precision=32, stream=None):
+        """y = A x  (vsie_apply)."""
+        import torch
+        nrhs = self._nrhs(x)
+        if y is None:
+            y = torch.empty_like(x)
+        _check(_lib.vsie_apply(self._h, _dev(x, "x"), _dev(y, "y"), nrhs, int(precision),
+                               _stream(stream)))
+        return y
+
+    def apply_timed(self, x, y, precision=32, stream=None):
+        """One apply with per-phase device times (vsie_apply_timed).  Returns
+        (dict of ms per phase, number of kernel launches)."""
+        ms = (ctypes.c_double * 4)()
+        nl = ctypes.c_int32()
+        _check(_lib.vsie_apply_timed(self._h, _dev(x, "x"), _dev(y, "y"), int(precision),
+                                     _stream(stream), ms, ctypes.byref(nl)))
+        names = ("prescale", "far_volume", "far_vector", "correction")
+        return dict(zip(names, list(ms))), nl.value
+
+    def apply_host(self, x: np.ndarray, precision=32, stream=None) -> np.ndarray:
+        """y = A x with host buffers (vsie_apply_host); x complex128 (n,) or (nrhs, n)."""
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        nrhs = 1 if x.ndim == 1 else x.shape[0]
+        y = np.empty_like(x)
+        _check(_lib.vsie_apply_host(self._h, _ptr(x), _ptr(y), nrhs, int(precision),
+                                    _stream(stream)))
+        return y
+
+    def apply_host_ptr(self, x_ptr: int, y_ptr: int, nrhs=1, precision=32, stream=None):
+        """vsie_apply_host on raw (e.g. pinned) host pointers."""
+        _check(_lib.vsie_apply_host(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr),
+                                    int(nrhs), int(precision), _stream(stream)))
+
+    def adjoint_apply(self, y, x=None, precision=32, stream=None):
+        """x = A^H y  (vsie_adjoint_apply)."""
+        import torch
+        nrhs = self._nrhs(y)
+        if x is None:
+            x = torch.empty_like(y)
+        _check(_lib.vsie_adjoint_apply(self._h, _dev(y, "y"), _dev(x, "x"), nrhs,
+                                       int(precision), _stream(stream)))
+        return x
+
+    def plane_wave_rhs(self, dirs, stream=None):
+        """b[d] = exp(i k0 x . d)  (vsie_plane_wave_rhs); returns (ndir, n)."""
+        import torch
+        d = _f64(dirs).reshape(-1, 3)
+        b = torch.empty((d.shape[0], self.n), dtype=torch.complex128, device="cuda")
+        _check(_lib.vsie_plane_wave_rhs(self._h, _ptr(d), d.shape[0], _dev(b, "b"),
+                                        _stream(stream)))
+        return b
+
+    def far_field(self, p, dirs, stream=None):
+        """Far-field pattern (vsie_far_field); returns (nrhs, ndir) or (ndir,)."""
+        import torch
+        nrhs = self._nrhs(p)
+        d = _f64(dirs).reshape(-1, 3)
+        out = torch.empty((nrhs, d.shape[0]), dtype=torch.complex128, device="cuda")
+        _check(_lib.vsie_far_field(self._h, _dev(p, "p"), nrhs, _ptr(d), d.shape[0],
+                                   _dev(out, "out"), _stream(stream)))
+        return out[0] if p.dim() == 1 else out
+
+    def solve(self, b, mode=32, tol=1e-8, max_iters=1000, restart=0, inner_tol=1e-4,
+              max_refinements=20, stream=None, raise_on_fail=True):
+        """x with A x = b (vsie_solve); returns (x, SolveInfo)."""
+        import torch
+        if b.dim() != 1:
+            raise ValueError("vsie_solve takes one right-hand side")
+        x = torch.empty_like(b)
+        o = _SolveOpts(int(mode), float(tol), int(max_iters), int(restart), float(inner_tol),
+                       int(max_refinements))
+        info = _SolveInfo()
+        st = _lib.vsie_solve(self._h, _dev(b, "b"), _dev(x, "x"), ctypes.byref(o),
+                             ctypes.byref(info), _stream(stream))
+        if raise_on_fail:
+            _check(st)
+        return x, SolveInfo(st, info.iterations, info.refinements, info.rel_residual,
+                            info.fp64_applies, info.fp32_applies)

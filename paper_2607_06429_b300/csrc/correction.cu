@@ -1,0 +1,481 @@
+// Near-field and self correction matrix Delta (FP64, built on the device) and its
+// application y += m x + Delta x (Eq. mass_function for m, Sec. 2.3.4 for the self terms).
+//
+// The far-field kernels evaluate every (collocation point, source point) pair with the
+// far rule.  Delta replaces, pair by pair, that far-rule value with an accurate one:
+//   * a tetrahedron on its own centroid: -(beta - k0^2 alpha)_e S(a_e), the single layer
+//     integrated over the ball of equal volume, S(a) = [e^{ika}(1 - ika) - 1]/k^2; the
+//     adjoint double layer of that ball vanishes by symmetry (Sec. 2.3.4);
+//   * a tetrahedron whose centroid lies within near_radius of the target (centroid far
+//     rule only): the degree-2 four-point rule;
+//   * a triangle whose centroid lies within tri_near_radius of the target: the double
+//     layer split as G = G_0 + (G - G_0), the Laplace part integrated exactly through the
+//     signed solid angle (Van Oosterom & Strackee), the bounded remainder by the
+//     three-point rule; a triangle on its own centroid takes the principal value 0.
+// Entry = accurate value - far-rule value.  Two value arrays are kept: val64 subtracts
+// the far-rule value from the FP64 coordinates (used with the FP64 far sum), val32 from
+// the FP32-rounded coordinates the FP32 far sum sees, so that near-singular pairs cancel
+// to FP32 arithmetic error rather than to coordinate-rounding error.
+//
+// Neighbour search: uniform cell grids (cell >= radius) over tetrahedron and triangle
+// centroids, sorted by cell with thrust; each target scans its 27 neighbouring cells.
+
+#include <cuda_runtime.h>
+#include <thrust/binary_search.h>
+#include <thrust/device_ptr.h>
+#include <thrust/execution_policy.h>
+#include <thrust/iterator/counting_iterator.h>
+#include <thrust/scan.h>
+#include <thrust/sequence.h>
+#include <thrust/sort.h>
+
+#include <cmath>
+
+#include "vsie_internal.h"
+
+namespace vsie {
+
+struct CellGrid {
+  double lo[3];
+  double inv;   // 1 / cell size
+  int nc[3];
+  int64_t ncell;
+  const int32_t* order = nullptr;   // element ids sorted by cell
+  const int64_t* start = nullptr;   // ncell + 1
+};
+
+__device__ __forceinline__ int cell_coord(double p, double lo, double inv, int nc) {
+  int c = (int)floor((p - lo) * inv);
+  return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+__global__ void cell_id_kernel(const double4_32a* __restrict__ pts, int64_t n, CellGrid g,
+                               int64_t* __restrict__ key, int32_t* __restrict__ idx) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double4_32a p = pts[i];
+  const int cx = cell_coord(p.x, g.lo[0], g.inv, g.nc[0]);
+  const int cy = cell_coord(p.y, g.lo[1], g.inv, g.nc[1]);
+  const int cz = cell_coord(p.z, g.lo[2], g.inv, g.nc[2]);
+  key[i] = ((int64_t)cx * g.nc[1] + cy) * g.nc[2] + cz;
+  idx[i] = (int32_t)i;
+}
+
+// ----------------------------------------------------------------- FP64 pair values
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// C(x, y) = G [-s + (ikr - 1)(d . v)/r^2], d = x - y, zero at r = 0.
+__device__ double2 pair64(double dx, double dy, double dz, double s, double vx, double vy,
+                          double vz, double k) {
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  if (!(r2 > 0.0)) return make_double2(0.0, 0.0);
+  const double r = sqrt(r2);
+  double sn, cs;
+  sincos(k * r, &sn, &cs);
+  const double g = 1.0 / (kFourPi * r);
+  const double dv = (dx * vx + dy * vy + dz * vz) / r2;
+  // (-s - dv) + i (k r dv)
+  const double2 m = make_double2(-s - dv, k * r * dv);
+  return cmul(make_double2(g * cs, g * sn), m);
+}
+
+// sum over the tetrahedron's four-point rule (weights w/4)
+__device__ double2 tet4(double x, double y, double z, const double4_32a* __restrict__ pts, double s4,
+                        double4_32a g4, double k, bool round32) {
+  double2 acc = make_double2(0.0, 0.0);
+  for (int q = 0; q < 4; ++q) {
+    double4_32a p = pts[q];
+    double xx = x, yy = y, zz = z;
+    if (round32) {
+      p.x = (double)(float)p.x; p.y = (double)(float)p.y; p.z = (double)(float)p.z;
+      xx = (double)(float)x; yy = (double)(float)y; zz = (double)(float)z;
+    }
+    const double2 c = pair64(xx - p.x, yy - p.y, zz - p.z, s4, g4.x, g4.y, g4.z, k);
+    acc.x += c.x;
+    acc.y += c.y;
+  }
+  return acc;
+}
+
+// int_t dG/dn_y dS for a target near the flat triangle t (see file comment)
+__device__ double2 dl_near(double x, double y, double z, const double4_32a* __restrict__ V,
+                           const double4_32a* __restrict__ Q, double4_32a nrm, double k) {
+  const double ax = V[0].x - x, ay = V[0].y - y, az = V[0].z - z;
+  const double bx = V[1].x - x, by = V[1].y - y, bz = V[1].z - z;
+  const double cx = V[2].x - x, cy = V[2].y - y, cz = V[2].z - z;
+  const double la = sqrt(ax * ax + ay * ay + az * az);
+  const double lb = sqrt(bx * bx + by * by + bz * bz);
+  const double lc = sqrt(cx * cx + cy * cy + cz * cz);
+  const double num = ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx);
+  const double den = la * lb * lc + (ax * bx + ay * by + az * bz) * lc +
+                     (ax * cx + ay * cy + az * cz) * lb + (bx * cx + by * cy + bz * cz) * la;
+  const double omega = 2.0 * atan2(num, den);
+  double2 acc = make_double2(-omega / kFourPi, 0.0);
+  const double w = nrm.w / 3.0;
+  for (int q = 0; q < 3; ++q) {
+    const double dx = x - Q[q].x, dy = y - Q[q].y, dz = z - Q[q].z;
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (!(r2 > 0.0)) continue;
+    const double r = sqrt(r2);
+    double sn, cs;
+    sincos(k * r, &sn, &cs);
+    // g'(r) = (i k r e^{ikr} - e^{ikr} + 1) / (4 pi r^2)
+    const double nr = -k * r * sn - cs + 1.0;
+    const double ni = k * r * cs - sn;
+    const double inv = 1.0 / (kFourPi * r2);
+    const double dn = (dx * nrm.x + dy * nrm.y + dz * nrm.z) / r;
+    acc.x += -nr * inv * dn * w;
+    acc.y += -ni * inv * dn * w;
+  }
+  return acc;
+}
+
+struct CorrInputs {
+  const double4_32a* tgt;       // n
+  const double4_32a* tet_cen;   // n_tet
+  const double4_32a* tet_pts;   // 4 n_tet
+  const double* tet_s;
+  const double4_32a* tet_ga;
+  const double* tet_vol;
+  const double4_32a* tri_vtx;   // 3 n_tri
+  const double4_32a* tri_pts;   // 3 n_tri
+  const double4_32a* tri_cen;   // n_tri
+  const double4_32a* tri_nrm;   // (n, area)
+  const double* tri_omega;
+  int64_t n_tet, n_tri, n;
+  int far_points;
+  double R2v, R2t;          // squared radii (0 = inactive)
+  double k;
+  CellGrid gv, gt;
+};
+
+// Visit the correction entries of row i: vol near set (or self only), then tri near set.
+// fill == false: count only.
+__global__ void corr_rows_kernel(CorrInputs in, const int64_t* __restrict__ row_ptr,
+                                 int64_t* __restrict__ counts, int32_t* __restrict__ col,
+                                 double2* __restrict__ v64, double2* __restrict__ v32, int fill) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= in.n) return;
+  const double4_32a X = in.tgt[i];
+  const double k = in.k;
+  int64_t pos = fill ? row_ptr[i] : 0;
+  int64_t cnt = 0;
+  auto emit = [&](int32_t c, double2 a64, double2 a32) {
+    if (fill) {
+      col[pos] = c;
+      v64[pos] = a64;
+      v32[pos] = a32;
+      ++pos;
+    }
+    ++cnt;
+  };
+  auto vol_entry = [&](int64_t e) {
+    const double vol = in.tet_vol[e];
+    const double s = in.tet_s[e];
+    const double4_32a ga = in.tet_ga[e];
+    double2 acc, f64 = make_double2(0, 0), f32 = make_double2(0, 0);
+    const double s4 = s * vol * 0.25;
+    const double4_32a g4 = make_double4_32a(ga.x * vol * 0.25, ga.y * vol * 0.25, ga.z * vol * 0.25, 0);
+    if (e == i) {
+      // self: single layer over the equal-volume ball, adjoint double layer 0
+      const double a = cbrt(3.0 * vol / kFourPi);
+      double sn, cs;
+      sincos(k * a, &sn, &cs);
+      // e^{ika}(1 - ika) - 1
+      const double re = cs + k * a * sn - 1.0, im = sn - k * a * cs;
+      acc = make_double2(-s * re / (k * k), -s * im / (k * k));
+      if (in.far_points == 4) {
+        f64 = tet4(X.x, X.y, X.z, in.tet_pts + 4 * e, s4, g4, k, false);
+        f32 = tet4(X.x, X.y, X.z, in.tet_pts + 4 * e, s4, g4, k, true);
+      }
+    } else {
+      acc = tet4(X.x, X.y, X.z, in.tet_pts + 4 * e, s4, g4, k, false);
+      const double4_32a c = in.tet_cen[e];
+      f64 = pair64(X.x - c.x, X.y - c.y, X.z - c.z, s * vol, ga.x * vol, ga.y * vol, ga.z * vol, k);
+      const double xr = (double)(float)X.x, yr = (double)(float)X.y, zr = (double)(float)X.z;
+      f32 = pair64(xr - (double)(float)c.x, yr - (double)(float)c.y, zr - (double)(float)c.z, s * vol,
+                   ga.x * vol, ga.y * vol, ga.z * vol, k);
+    }
+    emit((int32_t)e, make_double2(acc.x - f64.x, acc.y - f64.y),
+         make_double2(acc.x - f32.x, acc.y - f32.y));
+  };
+  auto tri_entry = [&](int64_t t) {
+    const double om = in.tri_omega[t];
+    const double4_32a nr = in.tri_nrm[t];
+    const double4_32a* Q = in.tri_pts + 3 * t;
+    const double w = nr.w / 3.0;
+    const double vx = -om * w * nr.x, vy = -om * w * nr.y, vz = -om * w * nr.z;
+    double2 acc = make_double2(0, 0), f64 = make_double2(0, 0), f32 = make_double2(0, 0);
+    const bool self = (i == in.n_tet + t);
+    if (!self) {
+      const double2 d = dl_near(X.x, X.y, X.z, in.tri_vtx + 3 * t, Q, nr, k);
+      acc = make_double2(om * d.x, om * d.y);
+    }
+    const double xr = (double)(float)X.x, yr = (double)(float)X.y, zr = (double)(float)X.z;
+    for (int q = 0; q < 3; ++q) {
+      const double2 c64 = pair64(X.x - Q[q].x, X.y - Q[q].y, X.z - Q[q].z, 0.0, vx, vy, vz, k);
+      const double2 c32 = pair64(xr - (double)(float)Q[q].x, yr - (double)(float)Q[q].y,
+                                 zr - (double)(float)Q[q].z, 0.0, vx, vy, vz, k);
+      f64.x += c64.x;
+      f64.y += c64.y;
+      f32.x += c32.x;
+      f32.y += c32.y;
+    }
+    emit((int32_t)(in.n_tet + t), make_double2(acc.x - f64.x, acc.y - f64.y),
+         make_double2(acc.x - f32.x, acc.y - f32.y));
+  };
+
+  // volume part
+  if (in.R2v > 0.0) {
+    const CellGrid& g = in.gv;
+    const int cx = cell_coord(X.x, g.lo[0], g.inv, g.nc[0]);
+    const int cy = cell_coord(X.y, g.lo[1], g.inv, g.nc[1]);
+    const int cz = cell_coord(X.z, g.lo[2], g.inv, g.nc[2]);
+    for (int ax = max(cx - 1, 0); ax <= min(cx + 1, g.nc[0] - 1); ++ax)
+      for (int ay = max(cy - 1, 0); ay <= min(cy + 1, g.nc[1] - 1); ++ay)
+        for (int az = max(cz - 1, 0); az <= min(cz + 1, g.nc[2] - 1); ++az) {
+          const int64_t cell = ((int64_t)ax * g.nc[1] + ay) * g.nc[2] + az;
+          for (int64_t p = g.start[cell]; p < g.start[cell + 1]; ++p) {
+            const int32_t e = g.order[p];
+            const double4_32a c = in.tet_cen[e];
+            const double dx = X.x - c.x, dy = X.y - c.y, dz = X.z - c.z;
+            if (dx * dx + dy * dy + dz * dz < in.R2v || e == i) vol_entry(e);
+          }
+        }
+  } else if (i < in.n_tet) {
+    vol_entry(i);
+  }
+  // interface part
+  if (in.R2t > 0.0) {
+    const CellGrid& g = in.gt;
+    const int cx = cell_coord(X.x, g.lo[0], g.inv, g.nc[0]);
+    const int cy = cell_coord(X.y, g.lo[1], g.inv, g.nc[1]);
+    const int cz = cell_coord(X.z, g.lo[2], g.inv, g.nc[2]);
+    for (int ax = max(cx - 1, 0); ax <= min(cx + 1, g.nc[0] - 1); ++ax)
+      for (int ay = max(cy - 1, 0); ay <= min(cy + 1, g.nc[1] - 1); ++ay)
+        for (int az = max(cz - 1, 0); az <= min(cz + 1, g.nc[2] - 1); ++az) {
+          const int64_t cell = ((int64_t)ax * g.nc[1] + ay) * g.nc[2] + az;
+          for (int64_t p = g.start[cell]; p < g.start[cell + 1]; ++p) {
+            const int32_t t = g.order[p];
+            const double4_32a c = in.tri_cen[t];
+            const double dx = X.x - c.x, dy = X.y - c.y, dz = X.z - c.z;
+            if (dx * dx + dy * dy + dz * dz < in.R2t || i == in.n_tet + t) tri_entry(t);
+          }
+        }
+  }
+  if (!fill) counts[i] = cnt;
+}
+
+// ----------------------------------------------------------------- application
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// y_i += m_i x_i + sum_k Delta_ik x_col(k); one warp per row, fixed summation order.
+__global__ void corr_apply_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                  const double2* __restrict__ val, const double* __restrict__ mass,
+                                  const double2* __restrict__ x, double2* __restrict__ y, int64_t n) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double ar = 0.0, ai = 0.0;
+  for (int64_t p = rp[row] + lane; p < rp[row + 1]; p += 32) {
+    const double2 v = val[p];
+    const double2 q = x[col[p]];
+    ar += v.x * q.x - v.y * q.y;
+    ai += v.x * q.y + v.y * q.x;
+  }
+  ar = warp_sum(ar);
+  ai = warp_sum(ai);
+  if (lane == 0) {
+    const double m = mass[row];
+    const double2 q = x[row];
+    const double2 o = y[row];
+    y[row] = make_double2(o.x + m * q.x + ar, o.y + m * q.y + ai);
+  }
+}
+
+// x_e += m_e lam_e (the mass is real)
+__global__ void mass_adjoint_kernel(const double* __restrict__ mass, const double2* __restrict__ lam,
+                                    double2* __restrict__ x, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double m = mass[i];
+  const double2 l = lam[i];
+  const double2 o = x[i];
+  x[i] = make_double2(o.x + m * l.x, o.y + m * l.y);
+}
+
+// x_col += conj(Delta_ik) lam_i (scatter with FP64 atomics)
+__global__ void corr_adjoint_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                    const double2* __restrict__ val, const double2* __restrict__ lam,
+                                    double2* __restrict__ x, int64_t n) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double2 l = lam[row];
+  for (int64_t p = rp[row] + lane; p < rp[row + 1]; p += 32) {
+    const double2 v = val[p];
+    double* dst = reinterpret_cast<double*>(x + col[p]);
+    atomicAdd(dst, v.x * l.x + v.y * l.y);
+    atomicAdd(dst + 1, v.x * l.y - v.y * l.x);
+  }
+}
+
+vsie_status correction_apply(vsie_handle* h, const double2* x, double2* y, int precision,
+                             cudaStream_t st) {
+  const int64_t n = h->n;
+  const double2* val = precision == 32 ? h->C.val32 : h->C.val64;
+  const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
+  corr_apply_kernel<<<blocks, 256, 0, st>>>(h->C.row_ptr, h->C.col, val, h->mass, x, y, n);
+  VSIE_CUDA(cudaGetLastError());
+  return VSIE_OK;
+}
+
+vsie_status correction_adjoint(vsie_handle* h, const double2* lam, double2* x, int precision,
+                               cudaStream_t st) {
+  const int64_t n = h->n;
+  const double2* val = precision == 32 ? h->C.val32 : h->C.val64;
+  mass_adjoint_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(h->mass, lam, x, n);
+  corr_adjoint_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(h->C.row_ptr, h->C.col, val,
+                                                                          lam, x, n);
+  VSIE_CUDA(cudaGetLastError());
+  return VSIE_OK;
+}
+
+// ----------------------------------------------------------------- construction
+
+static vsie_status make_grid(vsie_handle* h, const double4_32a* pts, int64_t np, double radius,
+                             const double lo[3], const double hi[3], CellGrid* g,
+                             std::vector<void*>* temps) {
+  double cs = radius;
+  for (;;) {
+    int64_t total = 1;
+    for (int d = 0; d < 3; ++d) {
+      g->lo[d] = lo[d];
+      g->nc[d] = (int)std::floor((hi[d] - lo[d]) / cs) + 1;
+      total *= g->nc[d];
+    }
+    if (total <= (int64_t)1 << 24) {
+      g->ncell = total;
+      break;
+    }
+    cs *= 1.5;  // a coarser grid still finds every neighbour within one cell
+  }
+  g->inv = 1.0 / cs;
+  int64_t* key;
+  int32_t* order;
+  int64_t* start;
+  VSIE_CUDA(cudaMalloc(&key, sizeof(int64_t) * (np > 0 ? np : 1)));
+  temps->push_back(key);
+  VSIE_CUDA(cudaMalloc(&order, sizeof(int32_t) * (np > 0 ? np : 1)));
+  temps->push_back(order);
+  VSIE_CUDA(cudaMalloc(&start, sizeof(int64_t) * (g->ncell + 1)));
+  temps->push_back(start);
+  if (np > 0) {
+    cell_id_kernel<<<(unsigned)((np + 255) / 256), 256>>>(pts, np, *g, key, order);
+    VSIE_CUDA(cudaGetLastError());
+    thrust::stable_sort_by_key(thrust::device, thrust::device_ptr<int64_t>(key),
+                               thrust::device_ptr<int64_t>(key + np),
+                               thrust::device_ptr<int32_t>(order));
+  }
+  thrust::lower_bound(thrust::device, thrust::device_ptr<int64_t>(key),
+                      thrust::device_ptr<int64_t>(key + np), thrust::counting_iterator<int64_t>(0),
+                      thrust::counting_iterator<int64_t>(g->ncell + 1),
+                      thrust::device_ptr<int64_t>(start));
+  VSIE_CUDA(cudaGetLastError());
+  g->order = order;
+  g->start = start;
+  (void)h;
+  return VSIE_OK;
+}
+
+vsie_status build_correction(vsie_handle* h, const double4_32a* d_tet_cen, const double4_32a* d_tet_pts,
+                             const double* d_tet_s, const double4_32a* d_tet_ga, const double* d_tet_vol,
+                             const double4_32a* d_tri_vtx, const double4_32a* d_tri_pts,
+                             const double4_32a* d_tri_cen, const double4_32a* d_tri_nrm,
+                             const double* d_tri_omega, const double lo[3], const double hi[3]) {
+  CorrInputs in;
+  in.tgt = h->tgt64;
+  in.tet_cen = d_tet_cen;
+  in.tet_pts = d_tet_pts;
+  in.tet_s = d_tet_s;
+  in.tet_ga = d_tet_ga;
+  in.tet_vol = d_tet_vol;
+  in.tri_vtx = d_tri_vtx;
+  in.tri_pts = d_tri_pts;
+  in.tri_cen = d_tri_cen;
+  in.tri_nrm = d_tri_nrm;
+  in.tri_omega = d_tri_omega;
+  in.n_tet = h->n_tet;
+  in.n_tri = h->n_tri;
+  in.n = h->n;
+  in.far_points = h->far_points;
+  in.k = h->k0;
+  const bool vol_near = h->far_points == 1 && h->near_radius > 0.0 && h->n_tet > 0;
+  const bool tri_near = h->tri_near_radius > 0.0 && h->n_tri > 0;
+  in.R2v = vol_near ? h->near_radius * h->near_radius : 0.0;
+  in.R2t = tri_near ? h->tri_near_radius * h->tri_near_radius : 0.0;
+
+  std::vector<void*> temps;
+  auto cleanup = [&]() {
+    for (void* p : temps) cudaFree(p);
+  };
+  vsie_status s = VSIE_OK;
+  if (vol_near) s = make_grid(h, d_tet_cen, h->n_tet, h->near_radius, lo, hi, &in.gv, &temps);
+  if (s == VSIE_OK && tri_near)
+    s = make_grid(h, d_tri_cen, h->n_tri, h->tri_near_radius, lo, hi, &in.gt, &temps);
+  if (s != VSIE_OK) {
+    cleanup();
+    return s;
+  }
+  const int64_t n = h->n;
+  s = dalloc_t(h, &h->C.row_ptr, (size_t)n + 1);
+  if (s != VSIE_OK) {
+    cleanup();
+    return s;
+  }
+  const unsigned blocks = (unsigned)((n + 127) / 128);
+  cudaError_t e = cudaMemset(h->C.row_ptr, 0, sizeof(int64_t) * ((size_t)n + 1));
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "cudaMemset(row_ptr)", __FILE__, __LINE__);
+  }
+  corr_rows_kernel<<<blocks, 128>>>(in, nullptr, h->C.row_ptr, nullptr, nullptr, nullptr, 0);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "corr_rows_kernel(count)", __FILE__, __LINE__);
+  }
+  // counts -> exclusive prefix sum in place (row_ptr[n] = nnz)
+  thrust::exclusive_scan(thrust::device, thrust::device_ptr<int64_t>(h->C.row_ptr),
+                         thrust::device_ptr<int64_t>(h->C.row_ptr + n + 1),
+                         thrust::device_ptr<int64_t>(h->C.row_ptr));
+  int64_t nnz = 0;
+  e = cudaMemcpy(&nnz, h->C.row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "cudaMemcpy(nnz)", __FILE__, __LINE__);
+  }
+  h->C.nnz = nnz;
+  if ((s = dalloc_t(h, &h->C.col, (size_t)nnz)) != VSIE_OK ||
+      (s = dalloc_t(h, &h->C.val64, (size_t)nnz)) != VSIE_OK ||
+      (s = dalloc_t(h, &h->C.val32, (size_t)nnz)) != VSIE_OK) {
+    cleanup();
+    return s;
+  }
+  corr_rows_kernel<<<blocks, 128>>>(in, h->C.row_ptr, nullptr, h->C.col, h->C.val64, h->C.val32, 1);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "corr_rows_kernel(fill)", __FILE__, __LINE__);
+  return VSIE_OK;
+}
+
+}  // namespace vsie

@@ -1,0 +1,140 @@
+// Incident plane waves (Eq. planewave) and the far-field pattern of the scattered field
+// (Eq. vsie used as a representation formula in Omega_0, Sec. 2.3.1), both in FP64.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "vsie_internal.h"
+
+namespace vsie {
+
+// b[i + n d] = exp(i k0 x_i . dir_d)
+__global__ void plane_wave_kernel(const double4_32a* __restrict__ tgt, int64_t n, const double4_32a* __restrict__ dirs,
+                                  int ndir, double k0, double2* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int d = blockIdx.y;
+  if (i >= n || d >= ndir) return;
+  const double4_32a x = tgt[i], u = dirs[d];
+  double sn, cs;
+  sincos(k0 * (x.x * u.x + x.y * u.y + x.z * u.z), &sn, &cs);
+  b[(int64_t)d * n + i] = make_double2(cs, sn);
+}
+
+// out[d + ndir r] = (1/4pi) sum_j e^{-ik xhat.y_j} (s_j - ik xhat.v_j) p_e(j)
+__global__ void far_field_kernel(const double4_32a* __restrict__ gps, const int32_t* __restrict__ gown, int64_t ng,
+                                 const double4_32a* __restrict__ fps, const double4_32a* __restrict__ fv,
+                                 const int32_t* __restrict__ fown, int64_t nf, const double2* __restrict__ p,
+                                 int64_t n, const double4_32a* __restrict__ dirs, int ndir, double k,
+                                 double2* __restrict__ out) {
+  __shared__ double red[2][8];
+  const int d = blockIdx.x, r = blockIdx.y;
+  const double4_32a u = dirs[d];
+  const double2* pr = p + (int64_t)r * n;
+  double ar = 0.0, ai = 0.0;
+  for (int64_t j = threadIdx.x; j < ng + nf; j += blockDim.x) {
+    double4_32a y;
+    double vx = 0, vy = 0, vz = 0;
+    int32_t e;
+    if (j < ng) {
+      y = gps[j];
+      e = gown[j];
+    } else {
+      y = fps[j - ng];
+      const double4_32a v = fv[j - ng];
+      vx = v.x; vy = v.y; vz = v.z;
+      e = fown[j - ng];
+    }
+    double sn, cs;
+    sincos(-k * (u.x * y.x + u.y * y.y + u.z * y.z), &sn, &cs);
+    const double amr = y.w, ami = -k * (u.x * vx + u.y * vy + u.z * vz);
+    const double tr = cs * amr - sn * ami, ti = cs * ami + sn * amr;
+    const double2 q = pr[e];
+    ar += tr * q.x - ti * q.y;
+    ai += tr * q.y + ti * q.x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ar += __shfl_down_sync(0xffffffffu, ar, o);
+    ai += __shfl_down_sync(0xffffffffu, ai, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = ar;
+    red[1][wid] = ai;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sr = 0, si = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      sr += red[0][w];
+      si += red[1][w];
+    }
+    out[(int64_t)r * ndir + d] = make_double2(sr / kFourPi, si / kFourPi);
+  }
+}
+
+static vsie_status upload_dirs(const double* h_dirs, int ndir, double4_32a** d_dirs, cudaStream_t st) {
+  std::vector<double4_32a> u(ndir);
+  for (int d = 0; d < ndir; ++d) {
+    const double x = h_dirs[3 * d], y = h_dirs[3 * d + 1], z = h_dirs[3 * d + 2];
+    const double nrm = std::sqrt(x * x + y * y + z * z);
+    if (!(nrm > 0.0) || !std::isfinite(nrm)) {
+      set_error("direction vectors must be nonzero and finite");
+      return VSIE_ERR_ARG;
+    }
+    u[d] = make_double4_32a(x / nrm, y / nrm, z / nrm, 0.0);
+  }
+  VSIE_CUDA(cudaMalloc(d_dirs, sizeof(double4_32a) * ndir));
+  cudaError_t e = cudaMemcpyAsync(*d_dirs, u.data(), sizeof(double4_32a) * ndir, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(*d_dirs);
+    return cuda_fail(e, "upload directions", __FILE__, __LINE__);
+  }
+  return VSIE_OK;
+}
+
+}  // namespace vsie
+
+using namespace vsie;
+
+extern "C" vsie_status vsie_plane_wave_rhs(vsie_handle* h, const double* h_dirs, int32_t ndir, void* d_b,
+                                           void* stream) {
+  clear_error();
+  if (!h || !h_dirs || !d_b || ndir < 1 || ndir > 65535) {
+    set_error("vsie_plane_wave_rhs: invalid argument");
+    return VSIE_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double4_32a* dirs;
+  VSIE_TRY(upload_dirs(h_dirs, ndir, &dirs, st));
+  dim3 grid((unsigned)((h->n + 255) / 256), (unsigned)ndir);
+  plane_wave_kernel<<<grid, 256, 0, st>>>(h->tgt64, h->n, dirs, ndir, h->k0, (double2*)d_b);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dirs);
+  if (e != cudaSuccess) return cuda_fail(e, "plane_wave_kernel", __FILE__, __LINE__);
+  return VSIE_OK;
+}
+
+extern "C" vsie_status vsie_far_field(vsie_handle* h, const void* d_p, int32_t nrhs, const double* h_dirs,
+                                      int32_t ndir, void* d_out, void* stream) {
+  clear_error();
+  if (!h || !d_p || !h_dirs || !d_out || ndir < 1 || nrhs < 1 || nrhs > 65535) {
+    set_error("vsie_far_field: invalid argument");
+    return VSIE_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double4_32a* dirs;
+  VSIE_TRY(upload_dirs(h_dirs, ndir, &dirs, st));
+  dim3 grid((unsigned)ndir, (unsigned)nrhs);
+  far_field_kernel<<<grid, 256, 0, st>>>(h->G.pos_s, h->G.owner, h->G.n, h->F.pos_s, h->F.vvec,
+                                         h->F.owner, h->F.n, (const double2*)d_p, h->n, dirs, ndir,
+                                         h->k0, (double2*)d_out);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dirs);
+  if (e != cudaSuccess) return cuda_fail(e, "far_field_kernel", __FILE__, __LINE__);
+  return VSIE_OK;
+}

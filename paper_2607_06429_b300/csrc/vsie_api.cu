@@ -1,0 +1,499 @@
+// libvsie: handle lifetime, discretisation (create time) and the apply entry points.
+//
+// Create-time arithmetic follows the paper's definitions: alpha, beta (Eqs. alpha, beta),
+// the mass function (Eq. mass_function), the weight (beta - k0^2 alpha) of the volume
+// single layer, grad(alpha) of the volume adjoint double layer and the interface jump
+// omega (alpha_1 on Gamma_1, alpha_2 - alpha_1 on Gamma_2) of the double layer, all from
+// Eq. (vsie); P0 collocation at centroids (Sec. 2.3.4).  Per-element geometry is O(n)
+// host work; the near-field/self correction matrix is built on the device.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vsie_internal.h"
+
+namespace vsie {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+void clear_error() { g_err.clear(); }
+
+vsie_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "CUDA error %d (%s) in %s at %s:%d", (int)e,
+           cudaGetErrorString(e), what, file, line);
+  set_error(buf);
+  cudaGetLastError();  // clear a non-sticky error
+  return e == cudaErrorMemoryAllocation ? VSIE_ERR_OOM : VSIE_ERR_CUDA;
+}
+
+vsie_status dalloc(vsie_handle* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "device allocation of %zu bytes failed: %s", bytes,
+             cudaGetErrorString(e));
+    set_error(buf);
+    cudaGetLastError();
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? VSIE_ERR_OOM : VSIE_ERR_CUDA;
+  }
+  h->allocs.push_back(*p);
+  return VSIE_OK;
+}
+
+template <class T>
+static vsie_status upload(vsie_handle* h, T** d, const std::vector<T>& v) {
+  VSIE_TRY(dalloc_t(h, d, v.size()));
+  if (!v.empty()) VSIE_CUDA(cudaMemcpy(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return VSIE_OK;
+}
+
+static inline bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+// Degree-2 four-point rule on a tetrahedron: barycentric (a, b, b, b) and permutations,
+// a = (5 + 3 sqrt5)/20, b = (5 - sqrt5)/20, weight |e|/4 each.
+static void tet_points(const double* P /*4x3*/, double* out /*4x3*/) {
+  const double s5 = std::sqrt(5.0);
+  const double a = (5.0 + 3.0 * s5) / 20.0, b = (5.0 - s5) / 20.0;
+  for (int q = 0; q < 4; ++q)
+    for (int d = 0; d < 3; ++d) {
+      double acc = 0.0;
+      for (int v = 0; v < 4; ++v) acc += (v == q ? a : b) * P[3 * v + d];
+      out[3 * q + d] = acc;
+    }
+}
+
+// Degree-2 three-point interior rule on a triangle: barycentric (2/3, 1/6, 1/6).
+static void tri_points(const double* P /*3x3*/, double* out /*3x3*/) {
+  for (int q = 0; q < 3; ++q)
+    for (int d = 0; d < 3; ++d) {
+      double acc = 0.0;
+      for (int v = 0; v < 3; ++v) acc += (v == q ? 2.0 / 3.0 : 1.0 / 6.0) * P[3 * v + d];
+      out[3 * q + d] = acc;
+    }
+}
+
+}  // namespace vsie
+
+using namespace vsie;
+
+extern "C" const char* vsie_last_error(void) { return g_err.c_str(); }
+
+extern "C" void vsie_destroy(vsie_handle* h) {
+  if (!h) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(h->device);
+  for (void* p : h->allocs) cudaFree(p);
+  cudaSetDevice(prev);
+  delete h;
+}
+
+extern "C" vsie_status vsie_sizes(const vsie_handle* h, int64_t* n, int64_t* n_far,
+                                  int64_t* nnz) {
+  if (!h) {
+    set_error("vsie_sizes: null handle");
+    return VSIE_ERR_ARG;
+  }
+  if (n) *n = h->n;
+  if (n_far) *n_far = h->G.n + h->F.n;
+  if (nnz) *nnz = h->C.nnz;
+  return VSIE_OK;
+}
+
+static vsie_status create_impl(const vsie_mesh* mesh, const vsie_material* mat, double k0,
+                               const vsie_options* opt, vsie_handle* h) {
+  const int64_t nv = mesh->n_vert, nt = mesh->n_tet, ns = mesh->n_tri;
+  h->n_tet = nt;
+  h->n_tri = ns;
+  h->n = nt + ns;
+  h->k0 = k0;
+  h->rho0 = mat->rho0;
+  h->c0 = mat->c0;
+  h->far_points = opt ? opt->tet_far_points : 1;
+  h->near_radius = opt ? opt->near_radius : 0.0;
+  h->tri_near_radius = opt ? opt->tri_near_radius : 0.0;
+  h->tile_override = opt ? opt->tile_override : 0;
+  if (h->far_points != 1 && h->far_points != 4) {
+    set_error("vsie_create: tet_far_points must be 1 or 4");
+    return VSIE_ERR_ARG;
+  }
+  if (!(h->near_radius >= 0.0) || !(h->tri_near_radius >= 0.0)) {
+    set_error("vsie_create: negative near radius");
+    return VSIE_ERR_ARG;
+  }
+  const double rho0 = mat->rho0, c0 = mat->c0;
+  const double omega = k0 * c0;  // k0 = omega / c0
+  const int FP = h->far_points;
+
+  // ---------------------------------------------------------------- volume elements
+  std::vector<double4_32a> tet_cen(nt), tet_pts(4 * nt), tet_ga(nt);
+  std::vector<double> tet_vol(nt), tet_s(nt), mass(h->n);
+  for (int64_t e = 0; e < nt; ++e) {
+    double P[12];
+    for (int v = 0; v < 4; ++v) {
+      int32_t id = mesh->tet[4 * e + v];
+      if (id < 0 || id >= nv) {
+        set_error("vsie_create: tetrahedron " + std::to_string(e) + " has a vertex index out of range");
+        return VSIE_ERR_MESH;
+      }
+      for (int d = 0; d < 3; ++d) P[3 * v + d] = mesh->vert[3 * id + d];
+    }
+    const double d1[3] = {P[3] - P[0], P[4] - P[1], P[5] - P[2]};
+    const double d2[3] = {P[6] - P[0], P[7] - P[1], P[8] - P[2]};
+    const double d3[3] = {P[9] - P[0], P[10] - P[1], P[11] - P[2]};
+    const double det = d1[0] * (d2[1] * d3[2] - d2[2] * d3[1]) -
+                       d1[1] * (d2[0] * d3[2] - d2[2] * d3[0]) +
+                       d1[2] * (d2[0] * d3[1] - d2[1] * d3[0]);
+    const double vol = std::fabs(det) / 6.0;
+    if (!(vol > 0.0) || !std::isfinite(vol)) {
+      set_error("vsie_create: tetrahedron " + std::to_string(e) + " has zero volume");
+      return VSIE_ERR_MESH;
+    }
+    const double rho = mat->rho[e], c = mat->c[e];
+    if (!finite_pos(rho) || !finite_pos(c)) {
+      set_error("vsie_create: non-positive or non-finite material on tetrahedron " + std::to_string(e));
+      return VSIE_ERR_MESH;
+    }
+    const double alpha = rho0 / rho - 1.0;                                   // Eq. (alpha)
+    const double beta = (rho0 / rho) * (omega / c) * (omega / c) - (omega / c0) * (omega / c0);  // Eq. (beta)
+    tet_vol[e] = vol;
+    tet_s[e] = beta - k0 * k0 * alpha;
+    mass[e] = rho0 / rho;                                                   // Eq. (mass_function)
+    tet_cen[e] = make_double4_32a(0.25 * (P[0] + P[3] + P[6] + P[9]), 0.25 * (P[1] + P[4] + P[7] + P[10]),
+                              0.25 * (P[2] + P[5] + P[8] + P[11]), 0.0);
+    double Q[12];
+    tet_points(P, Q);
+    for (int q = 0; q < 4; ++q) tet_pts[4 * e + q] = make_double4_32a(Q[3 * q], Q[3 * q + 1], Q[3 * q + 2], 0.0);
+    if (mat->grad_alpha) {
+      const double* g = mat->grad_alpha + 3 * e;
+      if (!std::isfinite(g[0]) || !std::isfinite(g[1]) || !std::isfinite(g[2])) {
+        set_error("vsie_create: non-finite grad_alpha");
+        return VSIE_ERR_NAN;
+      }
+      tet_ga[e] = make_double4_32a(g[0], g[1], g[2], 0.0);
+    } else {
+      tet_ga[e] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    }
+  }
+
+  // ---------------------------------------------------------------- interface elements
+  std::vector<double4_32a> tri_vtx(3 * ns), tri_nrm(ns), tri_cen(ns), tri_pts(3 * ns);
+  std::vector<double> tri_omega(ns);
+  for (int64_t t = 0; t < ns; ++t) {
+    double P[9];
+    for (int v = 0; v < 3; ++v) {
+      int32_t id = mesh->tri[3 * t + v];
+      if (id < 0 || id >= nv) {
+        set_error("vsie_create: triangle " + std::to_string(t) + " has a vertex index out of range");
+        return VSIE_ERR_MESH;
+      }
+      for (int d = 0; d < 3; ++d) P[3 * v + d] = mesh->vert[3 * id + d];
+      tri_vtx[3 * t + v] = make_double4_32a(P[3 * v], P[3 * v + 1], P[3 * v + 2], 0.0);
+    }
+    const double e1[3] = {P[3] - P[0], P[4] - P[1], P[5] - P[2]};
+    const double e2[3] = {P[6] - P[0], P[7] - P[1], P[8] - P[2]};
+    double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                    e1[0] * e2[1] - e1[1] * e2[0]};
+    const double nn = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    if (!(nn > 0.0) || !std::isfinite(nn)) {
+      set_error("vsie_create: triangle " + std::to_string(t) + " has zero area");
+      return VSIE_ERR_MESH;
+    }
+    const double area = 0.5 * nn;
+    tri_nrm[t] = make_double4_32a(cr[0] / nn, cr[1] / nn, cr[2] / nn, area);
+    tri_cen[t] = make_double4_32a((P[0] + P[3] + P[6]) / 3.0, (P[1] + P[4] + P[7]) / 3.0,
+                              (P[2] + P[5] + P[8]) / 3.0, 0.0);
+    double Q[9];
+    tri_points(P, Q);
+    for (int q = 0; q < 3; ++q) tri_pts[3 * t + q] = make_double4_32a(Q[3 * q], Q[3 * q + 1], Q[3 * q + 2], 0.0);
+    const double rin = mat->tri_rho_in[t], rout = mat->tri_rho_out[t];
+    if (!finite_pos(rin) || !finite_pos(rout)) {
+      set_error("vsie_create: non-positive interface density on triangle " + std::to_string(t));
+      return VSIE_ERR_MESH;
+    }
+    // omega = alpha_in - alpha_out  (alpha_1 on Gamma_1, alpha_2 - alpha_1 on Gamma_2)
+    tri_omega[t] = rho0 / rin - rho0 / rout;
+    // m = (rho0/rho_in + rho0/rho_out)/2 (Eq. mass_function on Gamma_1 and Gamma_2)
+    mass[nt + t] = 0.5 * (rho0 / rin + rho0 / rout);
+  }
+
+  // ---------------------------------------------------------------- far-field sources
+  std::vector<double4_32a> g_ps, f_ps, f_v;
+  std::vector<int32_t> g_own, f_own, g_first, g_elem, f_first, f_elem;
+  for (int64_t e = 0; e < nt; ++e) {
+    const bool has_v = tet_ga[e].x != 0.0 || tet_ga[e].y != 0.0 || tet_ga[e].z != 0.0;
+    auto& ps = has_v ? f_ps : g_ps;
+    auto& own = has_v ? f_own : g_own;
+    auto& first = has_v ? f_first : g_first;
+    auto& el = has_v ? f_elem : g_elem;
+    first.push_back((int32_t)ps.size());
+    el.push_back((int32_t)e);
+    if (FP == 1) {
+      const double w = tet_vol[e];
+      ps.push_back(make_double4_32a(tet_cen[e].x, tet_cen[e].y, tet_cen[e].z, tet_s[e] * w));
+      own.push_back((int32_t)e);
+      if (has_v) f_v.push_back(make_double4_32a(tet_ga[e].x * w, tet_ga[e].y * w, tet_ga[e].z * w, 0.0));
+    } else {
+      const double w = 0.25 * tet_vol[e];
+      for (int q = 0; q < 4; ++q) {
+        const double4_32a y = tet_pts[4 * e + q];
+        ps.push_back(make_double4_32a(y.x, y.y, y.z, tet_s[e] * w));
+        own.push_back((int32_t)e);
+        if (has_v) f_v.push_back(make_double4_32a(tet_ga[e].x * w, tet_ga[e].y * w, tet_ga[e].z * w, 0.0));
+      }
+    }
+  }
+  for (int64_t t = 0; t < ns; ++t) {
+    f_first.push_back((int32_t)f_ps.size());
+    f_elem.push_back((int32_t)(nt + t));
+    const double w = tri_nrm[t].w / 3.0;
+    const double sc = -tri_omega[t] * w;  // v = -omega n w  (dG/dn_y = -grad_x G . n)
+    for (int q = 0; q < 3; ++q) {
+      const double4_32a y = tri_pts[3 * t + q];
+      f_ps.push_back(make_double4_32a(y.x, y.y, y.z, 0.0));
+      f_v.push_back(make_double4_32a(sc * tri_nrm[t].x, sc * tri_nrm[t].y, sc * tri_nrm[t].z, 0.0));
+      f_own.push_back((int32_t)(nt + t));
+    }
+  }
+  g_first.push_back((int32_t)g_ps.size());
+  f_first.push_back((int32_t)f_ps.size());
+
+  // ---------------------------------------------------------------- targets
+  std::vector<double4_32a> tgt(h->n);
+  std::vector<float4> tgt32(h->n);
+  for (int64_t e = 0; e < nt; ++e) tgt[e] = tet_cen[e];
+  for (int64_t t = 0; t < ns; ++t) tgt[nt + t] = tri_cen[t];
+  for (int64_t i = 0; i < h->n; ++i)
+    tgt32[i] = make_float4((float)tgt[i].x, (float)tgt[i].y, (float)tgt[i].z, 0.0f);
+
+  VSIE_TRY(upload(h, &h->tgt64, tgt));
+  VSIE_TRY(upload(h, &h->tgt32, tgt32));
+  VSIE_TRY(upload(h, &h->mass, mass));
+
+  auto setup_class = [&](Sources& S, const std::vector<double4_32a>& ps, const std::vector<double4_32a>* vv,
+                         const std::vector<int32_t>& own, const std::vector<int32_t>& first,
+                         const std::vector<int32_t>& el, int recs32) -> vsie_status {
+    S.n = (int64_t)ps.size();
+    S.n_elem = (int64_t)el.size();
+    VSIE_TRY(upload(h, &S.pos_s, ps));
+    if (vv) VSIE_TRY(upload(h, &S.vvec, *vv));
+    VSIE_TRY(upload(h, &S.owner, own));
+    VSIE_TRY(upload(h, &S.elem_first, first));
+    VSIE_TRY(upload(h, &S.elem_list, el));
+    VSIE_TRY(dalloc_t(h, &S.r32a, (size_t)recs32 * S.n));
+    VSIE_TRY(dalloc_t(h, &S.r64a, (size_t)recs32 * S.n));
+    if (recs32 == 1) {
+      VSIE_TRY(dalloc_t(h, &S.r32b, (size_t)S.n));
+      VSIE_TRY(dalloc_t(h, &S.r64b, (size_t)S.n));
+    }
+    return VSIE_OK;
+  };
+  VSIE_TRY(setup_class(h->G, g_ps, nullptr, g_own, g_first, g_elem, 1));
+  VSIE_TRY(setup_class(h->F, f_ps, &f_v, f_own, f_first, f_elem, 3));
+
+  // ---------------------------------------------------------------- correction matrix
+  double4_32a *d_tet_cen, *d_tet_pts, *d_tet_ga, *d_tri_vtx, *d_tri_nrm, *d_tri_pts, *d_tri_cen;
+  double *d_tet_s, *d_tet_vol, *d_tri_omega;
+  VSIE_TRY(upload(h, &d_tet_cen, tet_cen));
+  VSIE_TRY(upload(h, &d_tet_pts, tet_pts));
+  VSIE_TRY(upload(h, &d_tet_ga, tet_ga));
+  VSIE_TRY(upload(h, &d_tet_s, tet_s));
+  VSIE_TRY(upload(h, &d_tet_vol, tet_vol));
+  VSIE_TRY(upload(h, &d_tri_vtx, tri_vtx));
+  VSIE_TRY(upload(h, &d_tri_nrm, tri_nrm));
+  VSIE_TRY(upload(h, &d_tri_omega, tri_omega));
+  VSIE_TRY(upload(h, &d_tri_pts, tri_pts));
+  VSIE_TRY(upload(h, &d_tri_cen, tri_cen));
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t i = 0; i < h->n; ++i) {
+    const double p[3] = {tgt[i].x, tgt[i].y, tgt[i].z};
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::fmin(lo[d], p[d]);
+      hi[d] = std::fmax(hi[d], p[d]);
+    }
+  }
+  VSIE_TRY(build_correction(h, d_tet_cen, d_tet_pts, d_tet_s, d_tet_ga, d_tet_vol, d_tri_vtx,
+                            d_tri_pts, d_tri_cen, d_tri_nrm, d_tri_omega, lo, hi));
+  VSIE_CUDA(cudaDeviceSynchronize());
+  // create-time geometry is no longer needed
+  for (void* p : {(void*)d_tet_cen, (void*)d_tet_pts, (void*)d_tet_ga, (void*)d_tet_s,
+                  (void*)d_tet_vol, (void*)d_tri_vtx, (void*)d_tri_nrm, (void*)d_tri_omega,
+                  (void*)d_tri_pts, (void*)d_tri_cen}) {
+    for (size_t i = 0; i < h->allocs.size(); ++i)
+      if (h->allocs[i] == p) {
+        h->allocs.erase(h->allocs.begin() + i);
+        break;
+      }
+    cudaFree(p);
+  }
+  return VSIE_OK;
+}
+
+extern "C" vsie_status vsie_create(const vsie_mesh* mesh, const vsie_material* mat, double k0,
+                                   const vsie_options* opt, vsie_handle** out) {
+  clear_error();
+  if (!out) {
+    set_error("vsie_create: null output pointer");
+    return VSIE_ERR_ARG;
+  }
+  *out = nullptr;
+  if (!mesh || !mat || !mesh->vert || (mesh->n_tet > 0 && !mesh->tet) ||
+      (mesh->n_tri > 0 && (!mesh->tri || !mat->tri_rho_in || !mat->tri_rho_out)) ||
+      (mesh->n_tet > 0 && (!mat->rho || !mat->c))) {
+    set_error("vsie_create: null mesh or material array");
+    return VSIE_ERR_ARG;
+  }
+  if (mesh->n_vert <= 0 || mesh->n_tet < 0 || mesh->n_tri < 0 || mesh->n_tet + mesh->n_tri <= 0 ||
+      mesh->n_tet + mesh->n_tri > (int64_t)INT32_MAX / 4) {
+    set_error("vsie_create: mesh sizes out of range");
+    return VSIE_ERR_ARG;
+  }
+  if (!(k0 > 0.0) || !std::isfinite(k0) || !finite_pos(mat->rho0) || !finite_pos(mat->c0)) {
+    set_error("vsie_create: k0, rho0 and c0 must be positive and finite");
+    return VSIE_ERR_ARG;
+  }
+  vsie_handle* h = new vsie_handle();
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "cudaGetDevice", __FILE__, __LINE__);
+  }
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  vsie_status s = create_impl(mesh, mat, k0, opt, h);
+  if (s != VSIE_OK) {
+    std::string msg = vsie_last_error();
+    vsie_destroy(h);
+    set_error(msg);
+    return s;
+  }
+  *out = h;
+  return VSIE_OK;
+}
+
+namespace vsie {
+vsie_status apply_one(vsie_handle* h, const double2* x, double2* y, int precision,
+                      cudaStream_t st) {
+  VSIE_TRY(far_apply(h, x, y, precision, st));
+  VSIE_TRY(correction_apply(h, x, y, precision, st));
+  return VSIE_OK;
+}
+}  // namespace vsie
+
+static vsie_status check_apply_args(vsie_handle* h, const void* x, const void* y, int32_t nrhs,
+                                    int32_t precision, const char* who) {
+  if (!h || !x || !y) {
+    set_error(std::string(who) + ": null handle or vector");
+    return VSIE_ERR_ARG;
+  }
+  if (nrhs < 1) {
+    set_error(std::string(who) + ": nrhs must be >= 1");
+    return VSIE_ERR_ARG;
+  }
+  if (precision != 32 && precision != 64) {
+    set_error(std::string(who) + ": precision must be 32 or 64");
+    return VSIE_ERR_ARG;
+  }
+  if (x == y) {
+    set_error(std::string(who) + ": input and output must not alias");
+    return VSIE_ERR_ARG;
+  }
+  return VSIE_OK;
+}
+
+extern "C" vsie_status vsie_apply(vsie_handle* h, const void* d_x, void* d_y, int32_t nrhs,
+                                  int32_t precision, void* stream) {
+  clear_error();
+  VSIE_TRY(check_apply_args(h, d_x, d_y, nrhs, precision, "vsie_apply"));
+  cudaStream_t st = (cudaStream_t)stream;
+  const double2* x = (const double2*)d_x;
+  double2* y = (double2*)d_y;
+  for (int r = 0; r < nrhs; ++r)
+    VSIE_TRY(apply_one(h, x + (size_t)r * h->n, y + (size_t)r * h->n, precision, st));
+  VSIE_CUDA(cudaGetLastError());
+  return VSIE_OK;
+}
+
+extern "C" vsie_status vsie_apply_host(vsie_handle* h, const double* h_x, double* h_y,
+                                       int32_t nrhs, int32_t precision, void* stream) {
+  clear_error();
+  VSIE_TRY(check_apply_args(h, h_x, h_y, nrhs, precision, "vsie_apply_host"));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->host_cols < nrhs) {
+    VSIE_TRY(dalloc_t(h, &h->host_x, (size_t)h->n * nrhs));
+    VSIE_TRY(dalloc_t(h, &h->host_y, (size_t)h->n * nrhs));
+    h->host_cols = nrhs;
+  }
+  const size_t bytes = sizeof(double2) * (size_t)h->n * nrhs;
+  VSIE_CUDA(cudaMemcpyAsync(h->host_x, h_x, bytes, cudaMemcpyHostToDevice, st));
+  for (int r = 0; r < nrhs; ++r)
+    VSIE_TRY(apply_one(h, h->host_x + (size_t)r * h->n, h->host_y + (size_t)r * h->n, precision, st));
+  VSIE_CUDA(cudaMemcpyAsync(h_y, h->host_y, bytes, cudaMemcpyDeviceToHost, st));
+  VSIE_CUDA(cudaStreamSynchronize(st));
+  return VSIE_OK;
+}
+
+extern "C" vsie_status vsie_adjoint_apply(vsie_handle* h, const void* d_y, void* d_x,
+                                          int32_t nrhs, int32_t precision, void* stream) {
+  clear_error();
+  VSIE_TRY(check_apply_args(h, d_y, d_x, nrhs, precision, "vsie_adjoint_apply"));
+  cudaStream_t st = (cudaStream_t)stream;
+  const double2* lam = (const double2*)d_y;
+  double2* x = (double2*)d_x;
+  for (int r = 0; r < nrhs; ++r) {
+    VSIE_TRY(far_adjoint(h, lam + (size_t)r * h->n, x + (size_t)r * h->n, precision, st));
+    VSIE_TRY(correction_adjoint(h, lam + (size_t)r * h->n, x + (size_t)r * h->n, precision, st));
+  }
+  VSIE_CUDA(cudaGetLastError());
+  return VSIE_OK;
+}
+
+extern "C" vsie_status vsie_apply_timed(vsie_handle* h, const void* d_x, void* d_y,
+                                        int32_t precision, void* stream, double* kernel_ms,
+                                        int32_t* launches) {
+  clear_error();
+  VSIE_TRY(check_apply_args(h, d_x, d_y, 1, precision, "vsie_apply_timed"));
+  if (!kernel_ms) {
+    set_error("vsie_apply_timed: null kernel_ms");
+    return VSIE_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const double2* x = (const double2*)d_x;
+  double2* y = (double2*)d_y;
+  cudaEvent_t ev[5];
+  for (int i = 0; i < 5; ++i) VSIE_CUDA(cudaEventCreate(&ev[i]));
+  int n_launch = 0;
+  vsie_status s = VSIE_OK;
+  auto run = [&]() -> vsie_status {
+    VSIE_CUDA(cudaEventRecord(ev[0], st));
+    VSIE_TRY(far_prescale(h, x, precision, st, &n_launch));
+    VSIE_CUDA(cudaEventRecord(ev[1], st));
+    VSIE_TRY(far_sum_g(h, y, precision, st, &n_launch));
+    VSIE_CUDA(cudaEventRecord(ev[2], st));
+    VSIE_TRY(far_sum_f(h, y, precision, st, &n_launch));
+    VSIE_CUDA(cudaEventRecord(ev[3], st));
+    VSIE_TRY(correction_apply(h, x, y, precision, st));
+    ++n_launch;
+    VSIE_CUDA(cudaEventRecord(ev[4], st));
+    VSIE_CUDA(cudaEventSynchronize(ev[4]));
+    for (int i = 0; i < 4; ++i) {
+      float ms = 0.0f;
+      VSIE_CUDA(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+      kernel_ms[i] = ms;
+    }
+    return VSIE_OK;
+  };
+  s = run();
+  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+  if (launches) *launches = n_launch;
+  return s;
+}

@@ -1,0 +1,63 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds/loads, exports every
+entry point declared in include/vsie.h, and rejects invalid arguments before touching
+the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2607_06429_b300 import binding as B
+from paper_2607_06429_b300 import build as BUILD
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(vsie_[a-z_0-9]+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    BUILD.build()
+    return B.load_library()
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert {"vsie_create", "vsie_apply", "vsie_solve", "vsie_adjoint_apply"} <= declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(B.EXPORTS) == declared
+
+
+def test_create_rejects_null_and_bad_sizes(lib):
+    h = ctypes.c_void_p()
+    assert lib.vsie_create(None, None, 1.0, None, ctypes.byref(h)) == 1
+    assert b"null" in lib.vsie_last_error()
+    vert = np.zeros(12)
+    tet = np.array([0, 1, 2, 3], dtype=np.int32)
+    mesh = B._Mesh(4, vert.ctypes.data_as(ctypes.c_void_p), 1, tet.ctypes.data_as(ctypes.c_void_p), 0, None)
+    rho = np.ones(1)
+    mat = B._Material(1.0, 1.0, rho.ctypes.data_as(ctypes.c_void_p), rho.ctypes.data_as(ctypes.c_void_p),
+                      None, None, None)
+    # non-positive wavenumber is rejected before any device work
+    assert lib.vsie_create(ctypes.byref(mesh), ctypes.byref(mat), -1.0, None, ctypes.byref(h)) == 1
+    assert b"k0" in lib.vsie_last_error()
+    assert not h.value
+
+
+def test_calls_reject_null_handle(lib):
+    assert lib.vsie_apply(None, None, None, 1, 32, None) == 1
+    assert lib.vsie_adjoint_apply(None, None, None, 1, 32, None) == 1
+    assert lib.vsie_sizes(None, None, None, None) == 1
+    assert lib.vsie_solve(None, None, None, None, None, None) == 1
+    assert lib.vsie_plane_wave_rhs(None, None, 0, None, None) == 1
+    assert lib.vsie_far_field(None, None, 1, None, 1, None, None) == 1
