@@ -123,6 +123,25 @@ vsie_status vsie_apply_host(vsie_handle* h, const double* h_x, double* h_y, int3
 vsie_status vsie_apply_timed(vsie_handle* h, const void* d_x, void* d_y, int32_t precision,
                              void* stream, double* kernel_ms, int32_t* launches);
 
+/* y = A x like vsie_apply, for callers that may not allocate device memory once set-up
+ * is over: a host application that hands all device memory to its own pool at start-up
+ * and accounts for every later byte, or a latency-critical loop that must not pay the
+ * implicit device synchronisation of cudaMalloc.  (The paper has no counterpart; this is
+ * an interface concern of the library.)  vsie_apply may grow a device buffer on first use
+ * for source-split partial sums; this variant keeps them in a fixed device array of
+ * 2,097,152 complex128 elements (32 MiB) compiled into the library, which every GPU that
+ * loads the library holds until the process exits.  Calls allocate nothing and free
+ * nothing.  The first call on a device looks up that array's device address (with the
+ * handle's device made current for the lookup); make that first call before any stream
+ * capture.  All calls share the one array and its contents persist between calls (every
+ * element a call reads it has written first), so calls that overlap on the GPU -- on
+ * different streams or different handles -- race and must be serialised by the caller.
+ * Same arguments, layouts and precisions as vsie_apply.  Errors: VSIE_ERR_ARG when the
+ * operator's launch shape needs more scratch than the array holds (the message gives
+ * both sizes; vsie_apply still works), and as vsie_apply otherwise. */
+vsie_status vsie_apply_noalloc(vsie_handle* h, const void* d_x, void* d_y, int32_t nrhs,
+                               int32_t precision, void* stream);
+
 /* x = A^H y (conjugate transpose), same layouts and precisions as vsie_apply. */
 vsie_status vsie_adjoint_apply(vsie_handle* h, const void* d_y, void* d_x, int32_t nrhs,
                                int32_t precision, void* stream);

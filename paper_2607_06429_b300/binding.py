@@ -24,7 +24,7 @@ STATUS = {
 VSIE_ERR_NOT_CONVERGED = 5
 
 EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_apply_host",
-           "vsie_apply_timed",
+           "vsie_apply_timed", "vsie_apply_noalloc",
            "vsie_adjoint_apply", "vsie_plane_wave_rhs", "vsie_far_field", "vsie_solve",
            "vsie_last_error")
 
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH):
     lib.vsie_sizes.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
     lib.vsie_apply.argtypes = [P, P, P, I32, I32, P]
     lib.vsie_apply_host.argtypes = [P, P, P, I32, I32, P]
+    lib.vsie_apply_noalloc.argtypes = [P, P, P, I32, I32, P]
     lib.vsie_adjoint_apply.argtypes = [P, P, P, I32, I32, P]
     lib.vsie_apply_timed.argtypes = [P, P, P, I32, P, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(I32)]
@@ -205,6 +206,14 @@ class Operator:
             y = torch.empty_like(x)
         _check(_lib.vsie_apply(self._h, _dev(x, "x"), _dev(y, "y"), nrhs, int(precision),
                                _stream(stream)))
+        return y
+
+    def apply_noalloc(self, x, y, precision=32, stream=None):
+        """y = A x without any device allocation in the call (vsie_apply_noalloc); the
+        caller provides y."""
+        nrhs = self._nrhs(x)
+        _check(_lib.vsie_apply_noalloc(self._h, _dev(x, "x"), _dev(y, "y"), nrhs,
+                                       int(precision), _stream(stream)))
         return y
 
     def apply_timed(self, x, y, precision=32, stream=None):

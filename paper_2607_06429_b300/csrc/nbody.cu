@@ -20,6 +20,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "vsie_internal.h"
 
 namespace vsie {
@@ -533,6 +535,75 @@ vsie_status far_apply(vsie_handle* h, const double2* x, double2* y, int precisio
   VSIE_TRY(far_prescale(h, x, precision, st, nullptr));
   VSIE_TRY(far_sum_g(h, y, precision, st, nullptr));
   VSIE_TRY(far_sum_f(h, y, precision, st, nullptr));
+  return VSIE_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Far-field sums whose source-split partials go to caller-provided scratch instead of
+// the handle's lazily grown buffer (used by the allocation-free apply).
+
+size_t far_split_elems(const vsie_handle* h) {
+  size_t need = 0;
+  const Sources* cls[2] = {&h->G, &h->F};
+  for (const Sources* S : cls) {
+    if (!S->n || !h->n) continue;
+    const Launch L = plan(h, h->n, S->n, kT);
+    if (L.nsplit > 1) need = std::max(need, (size_t)L.nsplit * (size_t)h->n);
+  }
+  return need;
+}
+
+template <class R>
+static void launch_g_into(const vsie_handle* h, const typename Vec4<R>::type* tgt, int64_t nt,
+                          const typename Vec4<R>::type* sa, const R* sb, int64_t ns, double2* out,
+                          int mode, double2* scratch, cudaStream_t st) {
+  const R kk = (R)(h->k0 / (2.0 * kPi));
+  const Launch L = plan(h, nt, ns, kT);
+  if (L.nsplit == 1) {
+    far_g_kernel<R, kT><<<L.grid, kBlock, 0, st>>>(tgt, nt, sa, sb, ns, L.chunk, kk, out, mode);
+  } else {
+    far_g_kernel<R, kT><<<L.grid, kBlock, 0, st>>>(tgt, nt, sa, sb, ns, L.chunk, kk, scratch, 0);
+    reduce_split_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(scratch, L.nsplit, nt, out, mode);
+  }
+}
+
+template <class R>
+static void launch_f_into(const vsie_handle* h, const typename Vec4<R>::type* tgt, int64_t nt,
+                          const typename Vec4<R>::type* src, int64_t ns, double2* out, int mode,
+                          double2* scratch, cudaStream_t st) {
+  const R k = (R)h->k0, kk = (R)(h->k0 / (2.0 * kPi));
+  const Launch L = plan(h, nt, ns, kT);
+  if (L.nsplit == 1) {
+    far_f_kernel<R, kT><<<L.grid, kBlock, 0, st>>>(tgt, nt, src, ns, L.chunk, k, kk, out, mode);
+  } else {
+    far_f_kernel<R, kT><<<L.grid, kBlock, 0, st>>>(tgt, nt, src, ns, L.chunk, k, kk, scratch, 0);
+    reduce_split_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(scratch, L.nsplit, nt, out, mode);
+  }
+}
+
+vsie_status far_sums_into(vsie_handle* h, double2* y, int precision, double2* scratch,
+                          cudaStream_t st) {
+  Sources& G = h->G;
+  Sources& F = h->F;
+  const int64_t n = h->n;
+  if (!G.n && !F.n) {
+    VSIE_CUDA(cudaMemsetAsync(y, 0, sizeof(double2) * n, st));
+    return VSIE_OK;
+  }
+  if (G.n) {
+    if (precision == 32)
+      launch_g_into<float>(h, h->tgt32, n, G.r32a, G.r32b, G.n, y, 0, scratch, st);
+    else
+      launch_g_into<double>(h, h->tgt64, n, G.r64a, G.r64b, G.n, y, 0, scratch, st);
+  }
+  if (F.n) {
+    const int mode = G.n ? 1 : 0;
+    if (precision == 32)
+      launch_f_into<float>(h, h->tgt32, n, F.r32a, F.n, y, mode, scratch, st);
+    else
+      launch_f_into<double>(h, h->tgt64, n, F.r64a, F.n, y, mode, scratch, st);
+  }
+  VSIE_CUDA(cudaGetLastError());
   return VSIE_OK;
 }
 

@@ -133,6 +133,11 @@ vsie_status far_prescale(vsie_handle* h, const double2* x, int precision, cudaSt
                          int* launches);
 vsie_status far_sum_g(vsie_handle* h, double2* y, int precision, cudaStream_t st, int* launches);
 vsie_status far_sum_f(vsie_handle* h, double2* y, int precision, cudaStream_t st, int* launches);
+// Both far-field sums with source-split partials in caller-provided scratch; the scratch
+// must hold far_split_elems(h) double2 values (nothing is allocated).
+size_t far_split_elems(const vsie_handle* h);
+vsie_status far_sums_into(vsie_handle* h, double2* y, int precision, double2* scratch,
+                          cudaStream_t st);
 // x_e = sum_{j in e} sum_i conj(C_ij) lam_i (overwrites x).
 vsie_status far_adjoint(vsie_handle* h, const double2* lam, double2* x, int precision,
                         cudaStream_t st);
