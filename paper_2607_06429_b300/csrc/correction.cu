@@ -14,7 +14,7 @@
 //     three-point rule; a triangle on its own centroid takes the principal value 0.
 // Entry = accurate value - far-rule value.  Two value arrays are kept: val64 subtracts
 // the far-rule value from the FP64 coordinates (used with the FP64 far sum), val32 from
-// the FP32-rounded coordinates the FP32 far sum sees, so that near-singular pairs cancel
+// the FP32 coordinates the FP32 far sum sees (float(kappa x)), so that near-singular pairs cancel
 // to FP32 arithmetic error rather than to coordinate-rounding error.
 //
 // Neighbour search: uniform cell grids (cell >= radius) over tetrahedron and triangle
@@ -82,16 +82,20 @@ __device__ double2 pair64(double dx, double dy, double dz, double s, double vx, 
   return cmul(make_double2(g * cs, g * sn), m);
 }
 
+// The coordinate the FP32 far-field kernels see: x stored as float(kappa x), mapped back.
+__device__ __forceinline__ double r32(double x, double kap) { return (double)(float)(kap * x) / kap; }
+
 // sum over the tetrahedron's four-point rule (weights w/4)
 __device__ double2 tet4(double x, double y, double z, const double4_32a* __restrict__ pts, double s4,
                         double4_32a g4, double k, bool round32) {
+  const double kap = k / (2.0 * kPi);
   double2 acc = make_double2(0.0, 0.0);
   for (int q = 0; q < 4; ++q) {
     double4_32a p = pts[q];
     double xx = x, yy = y, zz = z;
     if (round32) {
-      p.x = (double)(float)p.x; p.y = (double)(float)p.y; p.z = (double)(float)p.z;
-      xx = (double)(float)x; yy = (double)(float)y; zz = (double)(float)z;
+      p.x = r32(p.x, kap); p.y = r32(p.y, kap); p.z = r32(p.z, kap);
+      xx = r32(x, kap); yy = r32(y, kap); zz = r32(z, kap);
     }
     const double2 c = pair64(xx - p.x, yy - p.y, zz - p.z, s4, g4.x, g4.y, g4.z, k);
     acc.x += c.x;
@@ -195,9 +199,9 @@ __global__ void corr_rows_kernel(CorrInputs in, const int64_t* __restrict__ row_
       acc = tet4(X.x, X.y, X.z, in.tet_pts + 4 * e, s4, g4, k, false);
       const double4_32a c = in.tet_cen[e];
       f64 = pair64(X.x - c.x, X.y - c.y, X.z - c.z, s * vol, ga.x * vol, ga.y * vol, ga.z * vol, k);
-      const double xr = (double)(float)X.x, yr = (double)(float)X.y, zr = (double)(float)X.z;
-      f32 = pair64(xr - (double)(float)c.x, yr - (double)(float)c.y, zr - (double)(float)c.z, s * vol,
-                   ga.x * vol, ga.y * vol, ga.z * vol, k);
+      const double kap = k / (2.0 * kPi);
+      f32 = pair64(r32(X.x, kap) - r32(c.x, kap), r32(X.y, kap) - r32(c.y, kap),
+                   r32(X.z, kap) - r32(c.z, kap), s * vol, ga.x * vol, ga.y * vol, ga.z * vol, k);
     }
     emit((int32_t)e, make_double2(acc.x - f64.x, acc.y - f64.y),
          make_double2(acc.x - f32.x, acc.y - f32.y));
@@ -214,11 +218,12 @@ __global__ void corr_rows_kernel(CorrInputs in, const int64_t* __restrict__ row_
       const double2 d = dl_near(X.x, X.y, X.z, in.tri_vtx + 3 * t, Q, nr, k);
       acc = make_double2(om * d.x, om * d.y);
     }
-    const double xr = (double)(float)X.x, yr = (double)(float)X.y, zr = (double)(float)X.z;
+    const double kap = k / (2.0 * kPi);
+    const double xr = r32(X.x, kap), yr = r32(X.y, kap), zr = r32(X.z, kap);
     for (int q = 0; q < 3; ++q) {
       const double2 c64 = pair64(X.x - Q[q].x, X.y - Q[q].y, X.z - Q[q].z, 0.0, vx, vy, vz, k);
-      const double2 c32 = pair64(xr - (double)(float)Q[q].x, yr - (double)(float)Q[q].y,
-                                 zr - (double)(float)Q[q].z, 0.0, vx, vy, vz, k);
+      const double2 c32 = pair64(xr - r32(Q[q].x, kap), yr - r32(Q[q].y, kap), zr - r32(Q[q].z, kap),
+                                 0.0, vx, vy, vz, k);
       f64.x += c64.x;
       f64.y += c64.y;
       f32.x += c32.x;

@@ -23,9 +23,14 @@ __global__ void plane_wave_kernel(const double4_32a* __restrict__ tgt, int64_t n
 }
 
 // out[d + ndir r] = (1/4pi) sum_j e^{-ik xhat.y_j} (s_j - ik xhat.v_j) p_e(j)
-__global__ void far_field_kernel(const double4_32a* __restrict__ gps, const int32_t* __restrict__ gown, int64_t ng,
-                                 const double4_32a* __restrict__ fps, const double4_32a* __restrict__ fv,
-                                 const int32_t* __restrict__ fown, int64_t nf, const double2* __restrict__ p,
+struct FarClass {
+  const double4_32a* ps;
+  const double4_32a* v;  // null for the G class (v = 0)
+  const int32_t* own;
+  int64_t n;
+};
+
+__global__ void far_field_kernel(FarClass c0, FarClass c1, FarClass c2, const double2* __restrict__ p,
                                  int64_t n, const double4_32a* __restrict__ dirs, int ndir, double k,
                                  double2* __restrict__ out) {
   __shared__ double red[2][8];
@@ -33,19 +38,17 @@ __global__ void far_field_kernel(const double4_32a* __restrict__ gps, const int3
   const double4_32a u = dirs[d];
   const double2* pr = p + (int64_t)r * n;
   double ar = 0.0, ai = 0.0;
-  for (int64_t j = threadIdx.x; j < ng + nf; j += blockDim.x) {
-    double4_32a y;
+  const int64_t total = c0.n + c1.n + c2.n;
+  for (int64_t jj = threadIdx.x; jj < total; jj += blockDim.x) {
+    const FarClass& c = jj < c0.n ? c0 : (jj < c0.n + c1.n ? c1 : c2);
+    const int64_t j = jj < c0.n ? jj : (jj < c0.n + c1.n ? jj - c0.n : jj - c0.n - c1.n);
+    const double4_32a y = c.ps[j];
     double vx = 0, vy = 0, vz = 0;
-    int32_t e;
-    if (j < ng) {
-      y = gps[j];
-      e = gown[j];
-    } else {
-      y = fps[j - ng];
-      const double4_32a v = fv[j - ng];
+    if (c.v) {
+      const double4_32a v = c.v[j];
       vx = v.x; vy = v.y; vz = v.z;
-      e = fown[j - ng];
     }
+    const int32_t e = c.own[j];
     double sn, cs;
     sincos(-k * (u.x * y.x + u.y * y.y + u.z * y.z), &sn, &cs);
     const double amr = y.w, ami = -k * (u.x * vx + u.y * vy + u.z * vz);
@@ -129,9 +132,11 @@ extern "C" vsie_status vsie_far_field(vsie_handle* h, const void* d_p, int32_t n
   double4_32a* dirs;
   VSIE_TRY(upload_dirs(h_dirs, ndir, &dirs, st));
   dim3 grid((unsigned)ndir, (unsigned)nrhs);
-  far_field_kernel<<<grid, 256, 0, st>>>(h->G.pos_s, h->G.owner, h->G.n, h->F.pos_s, h->F.vvec,
-                                         h->F.owner, h->F.n, (const double2*)d_p, h->n, dirs, ndir,
-                                         h->k0, (double2*)d_out);
+  const FarClass g{h->G.pos_s, nullptr, h->G.owner, h->G.n};
+  const FarClass kc{h->K.pos_s, h->K.vvec, h->K.owner, h->K.n};
+  const FarClass f{h->F.pos_s, h->F.vvec, h->F.owner, h->F.n};
+  far_field_kernel<<<grid, 256, 0, st>>>(g, kc, f, (const double2*)d_p, h->n, dirs, ndir, h->k0,
+                                         (double2*)d_out);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(dirs);

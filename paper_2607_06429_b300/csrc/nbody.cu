@@ -8,15 +8,26 @@
 // since dG/dn_y = -grad_x G . n).  With charges q = -s p_e/(4 pi), u = v p_e/(4 pi):
 //     y_i = sum_j (e^{ikr}/r) [ q_j + (i k r - 1) (d . u_j) / r^2 ],   r = 0 -> 0.
 //
-// Kernel design (B300, sm_103a): the sum is bound by the FP32 and MUFU pipes, not by
-// memory.  Each thread owns T targets in registers; a block stages 128 source records
-// into shared memory per tile (one coalesced 16-byte load per thread) and every thread
-// reads them back as warp-wide broadcasts.  e^{ikr} uses an explicit range reduction
-// t = r k/(2 pi), f = t - rint(t), so the hardware sine/cosine only ever sees |2 pi f| <= pi.
-// Accumulation is compensated by blocking: each tile's 128 terms are summed in FP32 and
-// the tile sums are added in FP64.  A second grid dimension splits the sources when the
-// target count alone cannot fill the 148 SMs; partial sums then go to a scratch array and
-// are reduced in a fixed order (deterministic).
+// Source classes (one kernel each, so no pair pays for terms it does not have):
+//   G  volume points with v = 0:          y += (e^{ikr}/r) q
+//   K  interface points (s = 0, v = sigma n):  y += e^{ikr} (ikr - 1)(d.n) c / r^3
+//   F  volume points with grad(alpha) != 0:    the general form above
+//
+// Units: positions are stored pre-multiplied by kappa = k/(2 pi), so that
+// t = |x~ - y~| = k r/(2 pi) is the phase in revolutions and 1/r = kappa/|x~ - y~|;
+// the kappa powers are folded into the charges by the prescale kernels.  e^{ikr} is
+// evaluated from f = t - round(t) in [-1/2, 1/2] (round by the 1.5*2^23 shifter, two
+// adds on the FP32 pipe) so the hardware sine/cosine only sees |2 pi f| <= pi.
+//
+// Scheduling (B300, 148 SMs): a persistent grid of exactly the resident block count.
+// The work is the list of (target tile of 512, source chunk of 1024) items in
+// target-major order; block b takes the contiguous item range [b N/C, (b+1) N/C), so all
+// blocks get the same number of pairs (+-1 chunk) and there is no tail wave.  A target
+// tile that spans several blocks leaves its pieces in per-block slots, and a fix-up kernel
+// adds them in block order (deterministic).  Within an item each thread owns 4 targets
+// in registers; 128 source records at a time are staged in shared memory and read back
+// as warp-wide broadcasts.  FP32 accumulation is compensated: each 128-source tile is
+// summed in FP32 and folded into an FP32 (hi, lo) pair with an exact TwoSum.
 
 #include <cuda_runtime.h>
 
@@ -26,7 +37,11 @@
 
 namespace vsie {
 
-constexpr int kBlock = 128;
+constexpr int kBlock = 128;                 // threads per block, sources per smem tile
+constexpr int kT = 4;                       // targets per thread
+constexpr int kTile = kBlock * kT;          // targets per work item
+constexpr int kChunk = 8 * kBlock;          // sources per work item
+constexpr double kTwoPi = 2.0 * kPi;
 
 template <class R>
 struct Vec4;
@@ -39,354 +54,544 @@ struct Vec4<double> {
   using type = double4_32a;
 };
 
-// rinv = 1/r (0 at r = 0); (cs, sn) = (cos kr, sin kr).  kk = k/(2 pi).
-__device__ __forceinline__ void phase(float r2, float kk, float& rinv, float& cs, float& sn) {
+// ----------------------------------------------------------------- phase helpers
+
+// rinv = 1/|d~| (0 at d~ = 0), t = |d~| (revolutions), (cs, sn) = (cos, sin)(2 pi t)
+__device__ __forceinline__ void phase(float r2, float& rinv, float& t, float& cs, float& sn) {
   rinv = (r2 > 0.0f) ? rsqrtf(r2) : 0.0f;
-  const float t = r2 * rinv * kk;
-  const float f = t - rintf(t);
+  t = r2 * rinv;
+  const float shifter = 12582912.0f;  // 1.5 * 2^23: (t + s) - s rounds t to an integer
+  const float rt = __fsub_rn(__fadd_rn(t, shifter), shifter);
+  const float f = __fsub_rn(t, rt);
   __sincosf(f * 6.28318530717958647692f, &sn, &cs);
 }
-__device__ __forceinline__ void phase(double r2, double kk, double& rinv, double& cs, double& sn) {
+__device__ __forceinline__ void phase(double r2, double& rinv, double& t, double& cs, double& sn) {
   rinv = (r2 > 0.0) ? rsqrt(r2) : 0.0;
-  const double t = r2 * rinv * kk;
+  t = r2 * rinv;
   const double f = t - rint(t);
   sincospi(2.0 * f, &sn, &cs);
 }
 
-// ---------------------------------------------------------------------------------
-// G class: y_i += sum_j (e^{ikr}/r) q_j.  Source records: a = (x, y, z, q.re), b = q.im.
-template <class R, int T>
-__global__ void __launch_bounds__(kBlock) far_g_kernel(
-    const typename Vec4<R>::type* __restrict__ tgt, int64_t nt,
-    const typename Vec4<R>::type* __restrict__ sa, const R* __restrict__ sb, int64_t ns,
-    int64_t chunk, R kk, double2* __restrict__ out, int mode) {
-  using V = typename Vec4<R>::type;
-  __shared__ V s_a[kBlock];
-  __shared__ R s_b[kBlock];
-  const int tid = threadIdx.x;
-  const int64_t base = (int64_t)blockIdx.x * kBlock * T + tid;
-  const int64_t j_begin = (int64_t)blockIdx.y * chunk;
-  const int64_t j_end = min(ns, j_begin + chunk);
-  R xt[T], yt[T], zt[T];
-  double tr[T], ti[T];
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int64_t i = base + (int64_t)t * kBlock;
-    V p = (i < nt) ? tgt[i] : V{};
-    xt[t] = p.x;
-    yt[t] = p.y;
-    zt[t] = p.z;
-    tr[t] = 0.0;
-    ti[t] = 0.0;
+// ----------------------------------------------------------------- accumulators
+
+template <class R>
+struct Acc;
+template <>
+struct Acc<float> {
+  float hr, lr, hi, li;
+  __device__ __forceinline__ void zero() { hr = lr = hi = li = 0.0f; }
+  __device__ __forceinline__ static void two_sum(float& h, float& l, float a) {
+    const float s = __fadd_rn(h, a);
+    const float bp = __fsub_rn(s, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(a, bp));
+    h = s;
+    l = __fadd_rn(l, e);
   }
-  for (int64_t j0 = j_begin; j0 < j_end; j0 += kBlock) {
-    const int64_t j = j0 + tid;
-    if (j < j_end) {
-      s_a[tid] = sa[j];
-      s_b[tid] = sb[j];
+  __device__ __forceinline__ void fold(float ar, float ai) {
+    two_sum(hr, lr, ar);
+    two_sum(hi, li, ai);
+  }
+  __device__ __forceinline__ double2 value() const {
+    return make_double2((double)hr + (double)lr, (double)hi + (double)li);
+  }
+};
+template <>
+struct Acc<double> {
+  double r, i;
+  __device__ __forceinline__ void zero() { r = i = 0.0; }
+  __device__ __forceinline__ void fold(double ar, double ai) {
+    r += ar;
+    i += ai;
+  }
+  __device__ __forceinline__ double2 value() const { return make_double2(r, i); }
+};
+
+// ----------------------------------------------------------------- pair policies
+
+// G: records a = (x~, y~, z~, q~.re), b = q~.im;  y += e^{2 pi i t} rinv q~
+template <class R>
+struct PolG {
+  using V = typename Vec4<R>::type;
+  struct Smem {
+    V a[kBlock];
+    R b[kBlock];
+  };
+  struct Src {
+    V a;
+    R b;
+  };
+  struct Tgt {
+    R x, y, z;
+  };
+  const V* __restrict__ tgt;  // target positions (scaled, or unscaled if tscale != 1)
+  R tscale;
+  const V* __restrict__ sa;
+  const R* __restrict__ sb;
+
+  __device__ __forceinline__ void load_target(int64_t i, bool ok, Tgt& t) const {
+    if (ok) {
+      const V p = tgt[i];
+      t.x = p.x * tscale;
+      t.y = p.y * tscale;
+      t.z = p.z * tscale;
     } else {
-      s_a[tid] = V{};  // zero charge: contributes exactly 0 wherever it sits
-      s_b[tid] = R(0);
+      t.x = t.y = t.z = R(0);
     }
-    __syncthreads();
-    R ar[T], ai[T];
+  }
+  __device__ __forceinline__ void stage(Smem& sm, int64_t j, bool ok, int tid) const {
+    if (ok) {
+      sm.a[tid] = sa[j];
+      sm.b[tid] = sb[j];
+    } else {
+      sm.a[tid] = V{};  // zero charge contributes exactly 0 wherever it sits
+      sm.b[tid] = R(0);
+    }
+  }
+  __device__ __forceinline__ Src get(const Smem& sm, int jj) const { return Src{sm.a[jj], sm.b[jj]}; }
+  __device__ __forceinline__ void pair(const Src& s, const Tgt& t, R& ar, R& ai) const {
+    const R dx = t.x - s.a.x, dy = t.y - s.a.y, dz = t.z - s.a.z;
+    const R r2 = dx * dx + dy * dy + dz * dz;
+    R rinv, tt, cs, sn;
+    phase(r2, rinv, tt, cs, sn);
+    const R er = cs * rinv, ei = sn * rinv;
+    ar += er * s.a.w - ei * s.b;
+    ai += er * s.b + ei * s.a.w;
+  }
+};
+
+// K: records a = (x~, y~, z~, c~.re), b = (c~.im, nx, ny, nz);
+//    y += e^{2 pi i t} (2 pi i t - 1) (d~ . n) rinv^3 c~
+template <class R>
+struct PolK {
+  using V = typename Vec4<R>::type;
+  struct Smem {
+    V a[kBlock];
+    V b[kBlock];
+  };
+  struct Src {
+    V a, b;
+  };
+  using Tgt = typename PolG<R>::Tgt;
+  const V* __restrict__ tgt;
+  R tscale;
+  const V* __restrict__ src;  // 2 records per source
+
+  __device__ __forceinline__ void load_target(int64_t i, bool ok, Tgt& t) const {
+    if (ok) {
+      const V p = tgt[i];
+      t.x = p.x * tscale;
+      t.y = p.y * tscale;
+      t.z = p.z * tscale;
+    } else {
+      t.x = t.y = t.z = R(0);
+    }
+  }
+  __device__ __forceinline__ void stage(Smem& sm, int64_t j, bool ok, int tid) const {
+    if (ok) {
+      sm.a[tid] = src[2 * j];
+      sm.b[tid] = src[2 * j + 1];
+    } else {
+      sm.a[tid] = V{};
+      sm.b[tid] = V{};
+    }
+  }
+  __device__ __forceinline__ Src get(const Smem& sm, int jj) const { return Src{sm.a[jj], sm.b[jj]}; }
+  __device__ __forceinline__ void pair(const Src& s, const Tgt& t, R& ar, R& ai) const {
+    const R dx = t.x - s.a.x, dy = t.y - s.a.y, dz = t.z - s.a.z;
+    const R r2 = dx * dx + dy * dy + dz * dz;
+    R rinv, tt, cs, sn;
+    phase(r2, rinv, tt, cs, sn);
+    const R dn = dx * s.b.y + dy * s.b.z + dz * s.b.w;
+    const R g3 = rinv * rinv * rinv * dn;
+    const R gr = cs * g3, gi = sn * g3;
+    const R kr = tt * R(6.28318530717958647692);
+    const R hr = -gr - kr * gi, hi = kr * gr - gi;
+    ar += hr * s.a.w - hi * s.b.x;
+    ai += hr * s.b.x + hi * s.a.w;
+  }
+};
+
+// F: records a = (x~, y~, z~, q~.re), b = (q~.im, ux.re, ux.im, uy.re), c = (uy.im, uz.re, uz.im, 0)
+//    y += e^{2 pi i t} rinv [q~ + (2 pi i t - 1)(d~ . u~) rinv^2]
+template <class R>
+struct PolF {
+  using V = typename Vec4<R>::type;
+  struct Smem {
+    V a[kBlock];
+    V b[kBlock];
+    V c[kBlock];
+  };
+  struct Src {
+    V a, b, c;
+  };
+  using Tgt = typename PolG<R>::Tgt;
+  const V* __restrict__ tgt;
+  R tscale;
+  const V* __restrict__ src;  // 3 records per source
+
+  __device__ __forceinline__ void load_target(int64_t i, bool ok, Tgt& t) const {
+    if (ok) {
+      const V p = tgt[i];
+      t.x = p.x * tscale;
+      t.y = p.y * tscale;
+      t.z = p.z * tscale;
+    } else {
+      t.x = t.y = t.z = R(0);
+    }
+  }
+  __device__ __forceinline__ void stage(Smem& sm, int64_t j, bool ok, int tid) const {
+    if (ok) {
+      sm.a[tid] = src[3 * j];
+      sm.b[tid] = src[3 * j + 1];
+      sm.c[tid] = src[3 * j + 2];
+    } else {
+      sm.a[tid] = V{};
+      sm.b[tid] = V{};
+      sm.c[tid] = V{};
+    }
+  }
+  __device__ __forceinline__ Src get(const Smem& sm, int jj) const {
+    return Src{sm.a[jj], sm.b[jj], sm.c[jj]};
+  }
+  __device__ __forceinline__ void pair(const Src& s, const Tgt& t, R& ar, R& ai) const {
+    const R dx = t.x - s.a.x, dy = t.y - s.a.y, dz = t.z - s.a.z;
+    const R r2 = dx * dx + dy * dy + dz * dz;
+    R rinv, tt, cs, sn;
+    phase(r2, rinv, tt, cs, sn);
+    const R dur = dx * s.b.y + dy * s.b.w + dz * s.c.y;
+    const R dui = dx * s.b.z + dy * s.c.x + dz * s.c.z;
+    const R rinv2 = rinv * rinv;
+    const R fi = (tt * R(6.28318530717958647692)) * rinv2;  // (2 pi i t - 1) rinv^2
+    const R inr = s.a.w - rinv2 * dur - fi * dui;
+    const R ini = s.b.x - rinv2 * dui + fi * dur;
+    const R er = cs * rinv, ei = sn * rinv;
+    ar += er * inr - ei * ini;
+    ai += er * ini + ei * inr;
+  }
+};
+
+// Adjoint F: targets are source points j with (y~, s) and v~ = kappa v; sources are
+// collocation records a = (x~, c~.re), b = c~.im with c~ = kappa conj(lam)/(4 pi):
+//   w_j += e^{2 pi i t} rinv c~ [-s + (2 pi i t - 1)((x~_i - y~_j) . v~) rinv^2]
+template <class R>
+struct PolAF {
+  using V = typename Vec4<R>::type;
+  using Smem = typename PolG<R>::Smem;
+  using Src = typename PolG<R>::Src;
+  struct Tgt {
+    R x, y, z, s, vx, vy, vz;
+  };
+  const V* __restrict__ tps;  // (y~, s) scaled positions
+  const V* __restrict__ tv;   // v~
+  const V* __restrict__ sa;
+  const R* __restrict__ sb;
+
+  __device__ __forceinline__ void load_target(int64_t i, bool ok, Tgt& t) const {
+    if (ok) {
+      const V p = tps[i], v = tv[i];
+      t.x = p.x;
+      t.y = p.y;
+      t.z = p.z;
+      t.s = p.w;
+      t.vx = v.x;
+      t.vy = v.y;
+      t.vz = v.z;
+    } else {
+      t.x = t.y = t.z = t.s = t.vx = t.vy = t.vz = R(0);
+    }
+  }
+  __device__ __forceinline__ void stage(Smem& sm, int64_t j, bool ok, int tid) const {
+    if (ok) {
+      sm.a[tid] = sa[j];
+      sm.b[tid] = sb[j];
+    } else {
+      sm.a[tid] = V{};
+      sm.b[tid] = R(0);
+    }
+  }
+  __device__ __forceinline__ Src get(const Smem& sm, int jj) const { return Src{sm.a[jj], sm.b[jj]}; }
+  __device__ __forceinline__ void pair(const Src& s, const Tgt& t, R& ar, R& ai) const {
+    const R dx = s.a.x - t.x, dy = s.a.y - t.y, dz = s.a.z - t.z;  // x_i - y_j
+    const R r2 = dx * dx + dy * dy + dz * dz;
+    R rinv, tt, cs, sn;
+    phase(r2, rinv, tt, cs, sn);
+    const R dv = dx * t.vx + dy * t.vy + dz * t.vz;
+    const R rinv2 = rinv * rinv;
+    const R mr = -t.s - rinv2 * dv;
+    const R mi = (tt * R(6.28318530717958647692)) * rinv2 * dv;
+    const R er = cs * rinv, ei = sn * rinv;
+    const R gr = er * s.a.w - ei * s.b, gi = er * s.b + ei * s.a.w;
+    ar += gr * mr - gi * mi;
+    ai += gr * mi + gi * mr;
+  }
+};
+
+// ----------------------------------------------------------------- persistent driver
+
+struct StreamK {
+  int64_t nt, ns;
+  int64_t ntile, nchunk, nitems;
+  int64_t grid;
+};
+
+__host__ __device__ __forceinline__ int64_t sk_begin(const StreamK& s, int64_t b) {
+  return (b * s.nitems) / s.grid;
+}
+
+template <class R, class P>
+__global__ void __launch_bounds__(kBlock) nbody_kernel(P p, StreamK sk, double2* __restrict__ out,
+                                                       double2* __restrict__ slots, int mode) {
+  __shared__ typename P::Smem sm;
+  const int tid = threadIdx.x;
+  const int64_t b = blockIdx.x;
+  const int64_t k0 = sk_begin(sk, b), k1 = sk_begin(sk, b + 1);
+  int64_t k = k0;
+  while (k < k1) {
+    const int64_t tile = k / sk.nchunk;
+    const int64_t c0 = k - tile * sk.nchunk;
+    const int64_t c1 = min(sk.nchunk, c0 + (k1 - k));
+    typename P::Tgt tg[kT];
+    Acc<R> acc[kT];
 #pragma unroll
-    for (int t = 0; t < T; ++t) ar[t] = ai[t] = R(0);
+    for (int t = 0; t < kT; ++t) {
+      const int64_t i = tile * kTile + (int64_t)t * kBlock + tid;
+      p.load_target(i, i < sk.nt, tg[t]);
+      acc[t].zero();
+    }
+    const int64_t j_begin = c0 * kChunk;
+    const int64_t j_end = min(sk.ns, c1 * kChunk);
+    for (int64_t j0 = j_begin; j0 < j_end; j0 += kBlock) {
+      const int64_t j = j0 + tid;
+      p.stage(sm, j, j < j_end, tid);
+      __syncthreads();
+      R ar[kT], ai[kT];
+#pragma unroll
+      for (int t = 0; t < kT; ++t) ar[t] = ai[t] = R(0);
 #pragma unroll 4
-    for (int jj = 0; jj < kBlock; ++jj) {
-      const V s = s_a[jj];
-      const R qi = s_b[jj];
+      for (int jj = 0; jj < kBlock; ++jj) {
+        const typename P::Src s = p.get(sm, jj);
 #pragma unroll
-      for (int t = 0; t < T; ++t) {
-        const R dx = xt[t] - s.x, dy = yt[t] - s.y, dz = zt[t] - s.z;
-        const R r2 = dx * dx + dy * dy + dz * dz;
-        R rinv, cs, sn;
-        phase(r2, kk, rinv, cs, sn);
-        const R er = cs * rinv, ei = sn * rinv;
-        ar[t] += er * s.w - ei * qi;
-        ai[t] += er * qi + ei * s.w;
+        for (int t = 0; t < kT; ++t) p.pair(s, tg[t], ar[t], ai[t]);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < kT; ++t) acc[t].fold(ar[t], ai[t]);
+    }
+    const bool complete = (c0 == 0 && c1 == sk.nchunk);
+    const int64_t slot = (k == k0) ? 2 * b : 2 * b + 1;
+#pragma unroll
+    for (int t = 0; t < kT; ++t) {
+      const int64_t i = tile * kTile + (int64_t)t * kBlock + tid;
+      if (i < sk.nt) {
+        const double2 v = acc[t].value();
+        if (complete) {
+          if (mode) {
+            const double2 o = out[i];
+            out[i] = make_double2(o.x + v.x, o.y + v.y);
+          } else {
+            out[i] = v;
+          }
+        } else {
+          slots[slot * kTile + (int64_t)t * kBlock + tid] = v;
+        }
       }
     }
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-      tr[t] += (double)ar[t];
-      ti[t] += (double)ai[t];
-    }
-  }
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int64_t i = base + (int64_t)t * kBlock;
-    if (i < nt) {
-      double2* o = out + (int64_t)blockIdx.y * nt + i;
-      if (mode) {
-        double2 v = *o;
-        *o = make_double2(v.x + tr[t], v.y + ti[t]);
-      } else {
-        *o = make_double2(tr[t], ti[t]);
-      }
-    }
+    k = tile * sk.nchunk + c1;
   }
 }
 
-// ---------------------------------------------------------------------------------
-// F class: y_i += sum_j (e^{ikr}/r) [q_j + (ikr - 1)(d . u_j)/r^2].
-// Records (3 per source): (x, y, z, q.re) (q.im, ux.re, ux.im, uy.re) (uy.im, uz.re, uz.im, 0)
-template <class R, int T>
-__global__ void __launch_bounds__(kBlock) far_f_kernel(
-    const typename Vec4<R>::type* __restrict__ tgt, int64_t nt,
-    const typename Vec4<R>::type* __restrict__ src, int64_t ns, int64_t chunk, R k, R kk,
-    double2* __restrict__ out, int mode) {
-  using V = typename Vec4<R>::type;
-  __shared__ V s_r[3 * kBlock];
-  const int tid = threadIdx.x;
-  const int64_t base = (int64_t)blockIdx.x * kBlock * T + tid;
-  const int64_t j_begin = (int64_t)blockIdx.y * chunk;
-  const int64_t j_end = min(ns, j_begin + chunk);
-  R xt[T], yt[T], zt[T];
-  double tr[T], ti[T];
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int64_t i = base + (int64_t)t * kBlock;
-    V p = (i < nt) ? tgt[i] : V{};
-    xt[t] = p.x;
-    yt[t] = p.y;
-    zt[t] = p.z;
-    tr[t] = 0.0;
-    ti[t] = 0.0;
+__device__ __forceinline__ int64_t sk_block_of(const StreamK& s, int64_t k) {
+  int64_t b = (k * s.grid) / s.nitems;
+  while (b + 1 < s.grid && sk_begin(s, b + 1) <= k) ++b;
+  while (b > 0 && sk_begin(s, b) > k) --b;
+  return b;
+}
+
+// Adds the pieces of target tiles that span several blocks, in block order.
+__global__ void __launch_bounds__(kTile) fixup_kernel(StreamK sk, const double2* __restrict__ slots,
+                                                      double2* __restrict__ out, int mode) {
+  const int64_t tile = blockIdx.x;
+  const int64_t kf = tile * sk.nchunk, kl = kf + sk.nchunk - 1;
+  const int64_t bs = sk_block_of(sk, kf), be = sk_block_of(sk, kl);
+  if (bs == be) return;  // the whole tile was summed (and written) by one block
+  const int idx = threadIdx.x;
+  const int64_t i = tile * kTile + idx;
+  if (i >= sk.nt) return;
+  double sr = 0.0, si = 0.0;
+  for (int64_t b = bs; b <= be; ++b) {
+    if (sk_begin(sk, b) == sk_begin(sk, b + 1)) continue;  // empty range
+    const int64_t slot = (b == bs && sk_begin(sk, b) != kf) ? 2 * b + 1 : 2 * b;
+    const double2 v = slots[slot * kTile + idx];
+    sr += v.x;
+    si += v.y;
   }
-  for (int64_t j0 = j_begin; j0 < j_end; j0 += kBlock) {
-    // 3*kBlock records, loaded as 3 coalesced passes
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int64_t idx = 3 * j0 + (int64_t)c * kBlock + tid;
-      s_r[c * kBlock + tid] = (idx < 3 * j_end) ? src[idx] : V{};
-    }
-    __syncthreads();
-    R ar[T], ai[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) ar[t] = ai[t] = R(0);
-#pragma unroll 2
-    for (int jj = 0; jj < kBlock; ++jj) {
-      const V a = s_r[3 * jj], b = s_r[3 * jj + 1], c = s_r[3 * jj + 2];
-#pragma unroll
-      for (int t = 0; t < T; ++t) {
-        const R dx = xt[t] - a.x, dy = yt[t] - a.y, dz = zt[t] - a.z;
-        const R r2 = dx * dx + dy * dy + dz * dz;
-        R rinv, cs, sn;
-        phase(r2, kk, rinv, cs, sn);
-        const R dur = dx * b.y + dy * b.w + dz * c.y;
-        const R dui = dx * b.z + dy * c.x + dz * c.z;
-        const R rinv2 = rinv * rinv;
-        const R fi = (r2 * rinv * k) * rinv2;  // (ikr - 1)/r^2 = -rinv2 + i kr rinv2
-        const R inr = a.w - rinv2 * dur - fi * dui;
-        const R ini = b.x - rinv2 * dui + fi * dur;
-        const R er = cs * rinv, ei = sn * rinv;
-        ar[t] += er * inr - ei * ini;
-        ai[t] += er * ini + ei * inr;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-      tr[t] += (double)ar[t];
-      ti[t] += (double)ai[t];
-    }
-  }
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int64_t i = base + (int64_t)t * kBlock;
-    if (i < nt) {
-      double2* o = out + (int64_t)blockIdx.y * nt + i;
-      if (mode) {
-        double2 v = *o;
-        *o = make_double2(v.x + tr[t], v.y + ti[t]);
-      } else {
-        *o = make_double2(tr[t], ti[t]);
-      }
-    }
+  if (mode) {
+    const double2 o = out[i];
+    out[i] = make_double2(o.x + sr, o.y + si);
+  } else {
+    out[i] = make_double2(sr, si);
   }
 }
 
-// ---------------------------------------------------------------------------------
-// Adjoint, F class: for every source point j (here the "target", with weights s_j, v_j)
-//   w_j = sum_i (e^{ikr}/r) [-s_j + (ikr - 1)((x_i - y_j) . v_j)/r^2] c_i,
-// with c_i = conj(lam_i)/(4 pi) at the collocation points; then
-// sum_i conj(C_ij) lam_i = conj(w_j).  Collocation records: a = (x, y, z, c.re), b = c.im.
-template <class R, int T>
-__global__ void __launch_bounds__(kBlock) adj_f_kernel(
-    const typename Vec4<R>::type* __restrict__ tps, const typename Vec4<R>::type* __restrict__ tv,
-    int64_t nt, const typename Vec4<R>::type* __restrict__ sa, const R* __restrict__ sb,
-    int64_t ns, int64_t chunk, R k, R kk, double2* __restrict__ out, int mode) {
-  using V = typename Vec4<R>::type;
-  __shared__ V s_a[kBlock];
-  __shared__ R s_b[kBlock];
-  const int tid = threadIdx.x;
-  const int64_t base = (int64_t)blockIdx.x * kBlock * T + tid;
-  const int64_t j_begin = (int64_t)blockIdx.y * chunk;
-  const int64_t j_end = min(ns, j_begin + chunk);
-  V pt[T], vt[T];
-  double tr[T], ti[T];
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int64_t i = base + (int64_t)t * kBlock;
-    pt[t] = (i < nt) ? tps[i] : V{};
-    vt[t] = (i < nt) ? tv[i] : V{};
-    tr[t] = 0.0;
-    ti[t] = 0.0;
+// ----------------------------------------------------------------- launch planning
+
+template <class R, class P>
+static int resident_blocks(const vsie_handle* h) {
+  static int cached = 0;  // per instantiation; identical on every B300
+  if (!cached) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nbody_kernel<R, P>, kBlock, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    cached = per_sm;
   }
-  for (int64_t j0 = j_begin; j0 < j_end; j0 += kBlock) {
-    const int64_t j = j0 + tid;
-    if (j < j_end) {
-      s_a[tid] = sa[j];
-      s_b[tid] = sb[j];
-    } else {
-      s_a[tid] = V{};
-      s_b[tid] = R(0);
-    }
-    __syncthreads();
-    R ar[T], ai[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) ar[t] = ai[t] = R(0);
-#pragma unroll 2
-    for (int jj = 0; jj < kBlock; ++jj) {
-      const V s = s_a[jj];
-      const R ci = s_b[jj];
-#pragma unroll
-      for (int t = 0; t < T; ++t) {
-        const R dx = s.x - pt[t].x, dy = s.y - pt[t].y, dz = s.z - pt[t].z;  // x_i - y_j
-        const R r2 = dx * dx + dy * dy + dz * dz;
-        R rinv, cs, sn;
-        phase(r2, kk, rinv, cs, sn);
-        const R dv = dx * vt[t].x + dy * vt[t].y + dz * vt[t].z;
-        const R rinv2 = rinv * rinv;
-        const R mr = -pt[t].w - rinv2 * dv;        // -s + (ikr - 1) dv / r^2
-        const R mi = (r2 * rinv * k) * rinv2 * dv;
-        const R er = cs * rinv, ei = sn * rinv;
-        const R gr = er * s.w - ei * ci, gi = er * ci + ei * s.w;  // (e^{ikr}/r) c_i
-        ar[t] += gr * mr - gi * mi;
-        ai[t] += gr * mi + gi * mr;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-      tr[t] += (double)ar[t];
-      ti[t] += (double)ai[t];
-    }
-  }
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int64_t i = base + (int64_t)t * kBlock;
-    if (i < nt) {
-      double2* o = out + (int64_t)blockIdx.y * nt + i;
-      if (mode) {
-        double2 v = *o;
-        *o = make_double2(v.x + tr[t], v.y + ti[t]);
-      } else {
-        *o = make_double2(tr[t], ti[t]);
-      }
-    }
-  }
+  return cached * (h->num_sms > 0 ? h->num_sms : 148);
 }
 
-// ---------------------------------------------------------------------------------
-// Charge prescale (per apply): q = -s p_e/(4 pi), u = v p_e/(4 pi).
+template <class R, class P>
+static StreamK plan_sk(const vsie_handle* h, int64_t nt, int64_t ns) {
+  StreamK s;
+  s.nt = nt;
+  s.ns = ns;
+  s.ntile = (nt + kTile - 1) / kTile;
+  s.nchunk = (ns + kChunk - 1) / kChunk;
+  s.nitems = s.ntile * s.nchunk;
+  int64_t C = resident_blocks<R, P>(h);
+  if (h->tile_override > 0) C = h->tile_override;
+  s.grid = std::max<int64_t>(1, std::min<int64_t>(C, s.nitems));
+  return s;
+}
+
+static size_t slot_elems(const StreamK& s) { return (size_t)(2 * s.grid) * kTile; }
+
+template <class R, class P>
+static vsie_status run_nbody(const P& p, const StreamK& sk, double2* out, int mode, double2* slots,
+                             cudaStream_t st, int* launches) {
+  if (sk.nt == 0 || sk.ns == 0) return VSIE_OK;
+  nbody_kernel<R, P><<<(unsigned)sk.grid, kBlock, 0, st>>>(p, sk, out, slots, mode);
+  fixup_kernel<<<(unsigned)sk.ntile, kTile, 0, st>>>(sk, slots, out, mode);
+  if (launches) *launches += 2;
+  VSIE_CUDA(cudaGetLastError());
+  return VSIE_OK;
+}
+
+// Slot scratch of the handle, grown on demand.
+static vsie_status handle_slots(vsie_handle* h, size_t elems, double2** out) {
+  if (h->split_elems < elems) {
+    double2* p = nullptr;
+    VSIE_TRY(dalloc_t(h, &p, elems));
+    h->split = p;
+    h->split_elems = elems;
+  }
+  *out = h->split;
+  return VSIE_OK;
+}
+
+// ----------------------------------------------------------------- prescale kernels
+
+// G: a = kappa (y, q.re), b = kappa q.im,  q = -s p/(4 pi)
 __global__ void prescale_g_kernel(const double4_32a* __restrict__ ps, const int32_t* __restrict__ own,
-                                  const double2* __restrict__ p, int64_t n, int prec,
+                                  const double2* __restrict__ p, int64_t n, double kap, int prec,
                                   float4* __restrict__ a32, float* __restrict__ b32,
                                   double4_32a* __restrict__ a64, double* __restrict__ b64) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const double4_32a y = ps[j];
   const double2 pe = p[own[j]];
-  const double sc = -y.w / kFourPi;
+  const double sc = -kap * y.w / kFourPi;
   const double qr = sc * pe.x, qi = sc * pe.y;
   if (prec == 32) {
-    a32[j] = make_float4((float)y.x, (float)y.y, (float)y.z, (float)qr);
+    a32[j] = make_float4((float)(kap * y.x), (float)(kap * y.y), (float)(kap * y.z), (float)qr);
     b32[j] = (float)qi;
   } else {
-    a64[j] = make_double4_32a(y.x, y.y, y.z, qr);
+    a64[j] = make_double4_32a(kap * y.x, kap * y.y, kap * y.z, qr);
     b64[j] = qi;
   }
 }
 
+// K: a = (kappa y, c~.re), b = (c~.im, n), c~ = kappa^2 sigma p/(4 pi), v = sigma n
+__global__ void prescale_k_kernel(const double4_32a* __restrict__ ps, const double4_32a* __restrict__ nrm,
+                                  const int32_t* __restrict__ own, const double2* __restrict__ p, int64_t n,
+                                  double kap, int prec, float4* __restrict__ a32,
+                                  double4_32a* __restrict__ a64) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double4_32a y = ps[j];
+  const double4_32a nn = nrm[j];
+  const double2 pe = p[own[j]];
+  const double sc = kap * kap * nn.w / kFourPi;
+  const double cr = sc * pe.x, ci = sc * pe.y;
+  if (prec == 32) {
+    a32[2 * j] = make_float4((float)(kap * y.x), (float)(kap * y.y), (float)(kap * y.z), (float)cr);
+    a32[2 * j + 1] = make_float4((float)ci, (float)nn.x, (float)nn.y, (float)nn.z);
+  } else {
+    a64[2 * j] = make_double4_32a(kap * y.x, kap * y.y, kap * y.z, cr);
+    a64[2 * j + 1] = make_double4_32a(ci, nn.x, nn.y, nn.z);
+  }
+}
+
+// F: a = (kappa y, kappa q.re), b = (kappa q.im, kappa^2 u...), c = (...)
 __global__ void prescale_f_kernel(const double4_32a* __restrict__ ps, const double4_32a* __restrict__ vv,
                                   const int32_t* __restrict__ own, const double2* __restrict__ p,
-                                  int64_t n, int prec, float4* __restrict__ a32,
+                                  int64_t n, double kap, int prec, float4* __restrict__ a32,
                                   double4_32a* __restrict__ a64) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const double4_32a y = ps[j];
   const double4_32a v = vv[j];
   const double2 pe = p[own[j]];
-  const double sc = -y.w / kFourPi, vs = 1.0 / kFourPi;
+  const double sc = -kap * y.w / kFourPi, vs = kap * kap / kFourPi;
   const double qr = sc * pe.x, qi = sc * pe.y;
   const double uxr = vs * v.x * pe.x, uxi = vs * v.x * pe.y;
   const double uyr = vs * v.y * pe.x, uyi = vs * v.y * pe.y;
   const double uzr = vs * v.z * pe.x, uzi = vs * v.z * pe.y;
   if (prec == 32) {
-    a32[3 * j] = make_float4((float)y.x, (float)y.y, (float)y.z, (float)qr);
+    a32[3 * j] = make_float4((float)(kap * y.x), (float)(kap * y.y), (float)(kap * y.z), (float)qr);
     a32[3 * j + 1] = make_float4((float)qi, (float)uxr, (float)uxi, (float)uyr);
     a32[3 * j + 2] = make_float4((float)uyi, (float)uzr, (float)uzi, 0.0f);
   } else {
-    a64[3 * j] = make_double4_32a(y.x, y.y, y.z, qr);
+    a64[3 * j] = make_double4_32a(kap * y.x, kap * y.y, kap * y.z, qr);
     a64[3 * j + 1] = make_double4_32a(qi, uxr, uxi, uyr);
     a64[3 * j + 2] = make_double4_32a(uyi, uzr, uzi, 0.0);
   }
 }
 
-// collocation records for the adjoint: c = conj(lam)/(4 pi) at x_i
+// collocation records for the adjoint: c~ = kappa conj(lam)/(4 pi) at kappa x
 __global__ void prescale_colloc_kernel(const double4_32a* __restrict__ tgt, const double2* __restrict__ lam,
-                                       int64_t n, int prec, float4* __restrict__ a32,
+                                       int64_t n, double kap, int prec, float4* __restrict__ a32,
                                        float* __restrict__ b32, double4_32a* __restrict__ a64,
                                        double* __restrict__ b64) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double4_32a x = tgt[i];
-  const double cr = lam[i].x / kFourPi, ci = -lam[i].y / kFourPi;
+  const double cr = kap * lam[i].x / kFourPi, ci = -kap * lam[i].y / kFourPi;
   if (prec == 32) {
-    a32[i] = make_float4((float)x.x, (float)x.y, (float)x.z, (float)cr);
+    a32[i] = make_float4((float)(kap * x.x), (float)(kap * x.y), (float)(kap * x.z), (float)cr);
     b32[i] = (float)ci;
   } else {
-    a64[i] = make_double4_32a(x.x, x.y, x.z, cr);
+    a64[i] = make_double4_32a(kap * x.x, kap * x.y, kap * x.z, cr);
     b64[i] = ci;
   }
 }
 
-// static per-point target records for the adjoint: (x, y, z, s) and (vx, vy, vz, 0)
+// static per-point target records for the adjoint: (kappa y, s) and (kappa v, 0)
 __global__ void point_records_kernel(const double4_32a* __restrict__ ps, const double4_32a* __restrict__ vv,
-                                     int64_t n, float4* __restrict__ p32, float4* __restrict__ v32) {
+                                     int64_t n, double kap, float4* __restrict__ p32,
+                                     float4* __restrict__ v32, double4_32a* __restrict__ p64,
+                                     double4_32a* __restrict__ v64) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const double4_32a y = ps[j];
-  p32[j] = make_float4((float)y.x, (float)y.y, (float)y.z, (float)y.w);
+  p32[j] = make_float4((float)(kap * y.x), (float)(kap * y.y), (float)(kap * y.z), (float)y.w);
+  p64[j] = make_double4_32a(kap * y.x, kap * y.y, kap * y.z, y.w);
   if (vv) {
     const double4_32a v = vv[j];
-    v32[j] = make_float4((float)v.x, (float)v.y, (float)v.z, 0.0f);
+    v32[j] = make_float4((float)(kap * v.x), (float)(kap * v.y), (float)(kap * v.z), 0.0f);
+    v64[j] = make_double4_32a(kap * v.x, kap * v.y, kap * v.z, 0.0);
   }
 }
 
-// sum of split partials (fixed order), stored or added into out
-__global__ void reduce_split_kernel(const double2* __restrict__ part, int nsplit, int64_t n,
-                                    double2* __restrict__ out, int mode) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double sr = 0.0, si = 0.0;
-  for (int s = 0; s < nsplit; ++s) {
-    const double2 v = part[(int64_t)s * n + i];
-    sr += v.x;
-    si += v.y;
-  }
-  if (mode) {
-    const double2 v = out[i];
-    out[i] = make_double2(v.x + sr, v.y + si);
-  } else {
-    out[i] = make_double2(sr, si);
-  }
-}
-
-// x_e = sum_{j in e} conj(scale_j * w_j), scale_j = -s_j for the G class (w = a_j), 1 for F
+// x_e = conj(sum_{j in e} scale_j w_j), scale_j = -s_j for the G class (w = a_j), 1 otherwise
 __global__ void gather_adjoint_kernel(const double2* __restrict__ w, const double4_32a* __restrict__ ps,
                                       int use_s, const int32_t* __restrict__ first,
                                       const int32_t* __restrict__ elem, int64_t n_elem,
@@ -402,102 +607,28 @@ __global__ void gather_adjoint_kernel(const double2* __restrict__ w, const doubl
   x[elem[e]] = make_double2(sr, -si);
 }
 
-// ---------------------------------------------------------------------------------
-struct Launch {
-  dim3 grid;
-  int64_t chunk;
-  int nsplit;
-};
-
-static Launch plan(const vsie_handle* h, int64_t nt, int64_t ns, int T) {
-  Launch L;
-  const int64_t bx = (nt + (int64_t)kBlock * T - 1) / ((int64_t)kBlock * T);
-  const int64_t want = (int64_t)(h->num_sms > 0 ? h->num_sms : 148) * 8;
-  int64_t nsplit = (bx >= want) ? 1 : (want + bx - 1) / bx;
-  const int64_t max_split = (ns + kBlock - 1) / kBlock;
-  if (nsplit > max_split) nsplit = max_split;
-  if (nsplit < 1) nsplit = 1;
-  if (h->tile_override > 0) nsplit = h->tile_override < 65535 ? h->tile_override : 65535;
-  int64_t chunk = (ns + nsplit - 1) / nsplit;
-  chunk = ((chunk + kBlock - 1) / kBlock) * kBlock;
-  if (chunk < kBlock) chunk = kBlock;
-  nsplit = (int)((ns + chunk - 1) / chunk);
-  if (nsplit < 1) nsplit = 1;
-  L.grid = dim3((unsigned)bx, (unsigned)nsplit, 1);
-  L.chunk = chunk;
-  L.nsplit = (int)nsplit;
-  return L;
-}
-
-}  // namespace vsie
-
-namespace vsie {
-
-// Split-partial scratch, grown on demand and owned by the handle.
-static vsie_status split_scratch(vsie_handle* h, size_t elems, double2** out) {
-  if (h->split_elems < elems) {
-    double2* p = nullptr;
-    VSIE_TRY(dalloc_t(h, &p, elems));
-    h->split = p;
-    h->split_elems = elems;
-  }
-  *out = h->split;
-  return VSIE_OK;
-}
-
-constexpr int kT = 4;
-
-template <class R>
-static vsie_status launch_g(vsie_handle* h, const typename Vec4<R>::type* tgt, int64_t nt,
-                            const typename Vec4<R>::type* sa, const R* sb, int64_t ns, double2* out,
-                            int mode, cudaStream_t st) {
-  if (ns == 0 || nt == 0) return VSIE_OK;
-  const R kk = (R)(h->k0 / (2.0 * kPi));
-  Launch L = plan(h, nt, ns, kT);
-  if (L.nsplit == 1) {
-    far_g_kernel<R, kT><<<L.grid, kBlock, 0, st>>>(tgt, nt, sa, sb, ns, L.chunk, kk, out, mode);
-  } else {
-    double2* part;
-    VSIE_TRY(split_scratch(h, (size_t)L.nsplit * nt, &part));
-    far_g_kernel<R, kT><<<L.grid, kBlock, 0, st>>>(tgt, nt, sa, sb, ns, L.chunk, kk, part, 0);
-    reduce_split_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(part, L.nsplit, nt, out, mode);
-  }
-  VSIE_CUDA(cudaGetLastError());
-  return VSIE_OK;
-}
-
-template <class R>
-static vsie_status launch_f(vsie_handle* h, const typename Vec4<R>::type* tgt, int64_t nt,
-                            const typename Vec4<R>::type* src, int64_t ns, double2* out, int mode,
-                            cudaStream_t st) {
-  if (ns == 0 || nt == 0) return VSIE_OK;
-  const R k = (R)h->k0, kk = (R)(h->k0 / (2.0 * kPi));
-  Launch L = plan(h, nt, ns, kT);
-  if (L.nsplit == 1) {
-    far_f_kernel<R, kT><<<L.grid, kBlock, 0, st>>>(tgt, nt, src, ns, L.chunk, k, kk, out, mode);
-  } else {
-    double2* part;
-    VSIE_TRY(split_scratch(h, (size_t)L.nsplit * nt, &part));
-    far_f_kernel<R, kT><<<L.grid, kBlock, 0, st>>>(tgt, nt, src, ns, L.chunk, k, kk, part, 0);
-    reduce_split_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(part, L.nsplit, nt, out, mode);
-  }
-  VSIE_CUDA(cudaGetLastError());
-  return VSIE_OK;
-}
-
 static inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+// ----------------------------------------------------------------- forward apply
 
 vsie_status far_prescale(vsie_handle* h, const double2* x, int precision, cudaStream_t st,
                          int* launches) {
+  const double kap = h->k0 / kTwoPi;
   Sources& G = h->G;
   Sources& F = h->F;
+  Sources& K = h->K;
   if (G.n) {
-    prescale_g_kernel<<<nblk(G.n), 256, 0, st>>>(G.pos_s, G.owner, x, G.n, precision, G.r32a,
+    prescale_g_kernel<<<nblk(G.n), 256, 0, st>>>(G.pos_s, G.owner, x, G.n, kap, precision, G.r32a,
                                                  G.r32b, G.r64a, G.r64b);
     if (launches) ++*launches;
   }
+  if (K.n) {
+    prescale_k_kernel<<<nblk(K.n), 256, 0, st>>>(K.pos_s, K.aux, K.owner, x, K.n, kap, precision,
+                                                 K.r32a, K.r64a);
+    if (launches) ++*launches;
+  }
   if (F.n) {
-    prescale_f_kernel<<<nblk(F.n), 256, 0, st>>>(F.pos_s, F.vvec, F.owner, x, F.n, precision,
+    prescale_f_kernel<<<nblk(F.n), 256, 0, st>>>(F.pos_s, F.vvec, F.owner, x, F.n, kap, precision,
                                                  F.r32a, F.r64a);
     if (launches) ++*launches;
   }
@@ -505,158 +636,159 @@ vsie_status far_prescale(vsie_handle* h, const double2* x, int precision, cudaSt
   return VSIE_OK;
 }
 
-static int launches_of(const vsie_handle* h, int64_t nt, int64_t ns) {
-  if (ns == 0 || nt == 0) return 0;
-  return plan(h, nt, ns, kT).nsplit > 1 ? 2 : 1;
-}
+// Plans of the three forward sums (stored/added in the order G, K, F).
+struct ForwardPlans {
+  StreamK g, k, f;
+  size_t slots;
+};
 
-vsie_status far_sum_g(vsie_handle* h, double2* y, int precision, cudaStream_t st, int* launches) {
-  Sources& G = h->G;
-  if (!G.n) return VSIE_OK;
-  if (launches) *launches += launches_of(h, h->n, G.n);
-  if (precision == 32) return launch_g<float>(h, h->tgt32, h->n, G.r32a, G.r32b, G.n, y, 0, st);
-  return launch_g<double>(h, h->tgt64, h->n, G.r64a, G.r64b, G.n, y, 0, st);
-}
-
-vsie_status far_sum_f(vsie_handle* h, double2* y, int precision, cudaStream_t st, int* launches) {
-  Sources& F = h->F;
-  const int mode = h->G.n ? 1 : 0;
-  if (!F.n) {
-    if (!h->G.n) VSIE_CUDA(cudaMemsetAsync(y, 0, sizeof(double2) * h->n, st));
-    return VSIE_OK;
+static ForwardPlans forward_plans(const vsie_handle* h, int precision) {
+  ForwardPlans P;
+  const int64_t n = h->n;
+  if (precision == 32) {
+    P.g = plan_sk<float, PolG<float>>(h, n, h->G.n);
+    P.k = plan_sk<float, PolK<float>>(h, n, h->K.n);
+    P.f = plan_sk<float, PolF<float>>(h, n, h->F.n);
+  } else {
+    P.g = plan_sk<double, PolG<double>>(h, n, h->G.n);
+    P.k = plan_sk<double, PolK<double>>(h, n, h->K.n);
+    P.f = plan_sk<double, PolF<double>>(h, n, h->F.n);
   }
-  if (launches) *launches += launches_of(h, h->n, F.n);
-  if (precision == 32) return launch_f<float>(h, h->tgt32, h->n, F.r32a, F.n, y, mode, st);
-  return launch_f<double>(h, h->tgt64, h->n, F.r64a, F.n, y, mode, st);
+  P.slots = std::max(slot_elems(P.g), std::max(slot_elems(P.k), slot_elems(P.f)));
+  return P;
+}
+
+template <class R>
+static vsie_status forward_sums(vsie_handle* h, double2* y, const ForwardPlans& P, double2* slots,
+                                cudaStream_t st, int phase_mask, int* launches) {
+  using V = typename Vec4<R>::type;
+  const bool fp32 = sizeof(R) == 4;
+  const V* tgt = fp32 ? reinterpret_cast<const V*>(h->tgt32) : reinterpret_cast<const V*>(h->tgt64);
+  const R tscale = fp32 ? R(1) : (R)(h->k0 / kTwoPi);  // FP32 targets are stored scaled
+  int mode = 0;
+  if (h->G.n) {
+    if (phase_mask & 1) {
+      PolG<R> p{tgt, tscale, reinterpret_cast<const V*>(fp32 ? (const void*)h->G.r32a : (const void*)h->G.r64a),
+                reinterpret_cast<const R*>(fp32 ? (const void*)h->G.r32b : (const void*)h->G.r64b)};
+      VSIE_TRY((run_nbody<R, PolG<R>>(p, P.g, y, mode, slots, st, launches)));
+    }
+    mode = 1;
+  }
+  if (h->K.n) {
+    if (phase_mask & 2) {
+      PolK<R> p{tgt, tscale, reinterpret_cast<const V*>(fp32 ? (const void*)h->K.r32a : (const void*)h->K.r64a)};
+      VSIE_TRY((run_nbody<R, PolK<R>>(p, P.k, y, mode, slots, st, launches)));
+    }
+    mode = 1;
+  }
+  if (h->F.n) {
+    if (phase_mask & 2) {
+      PolF<R> p{tgt, tscale, reinterpret_cast<const V*>(fp32 ? (const void*)h->F.r32a : (const void*)h->F.r64a)};
+      VSIE_TRY((run_nbody<R, PolF<R>>(p, P.f, y, mode, slots, st, launches)));
+    }
+    mode = 1;
+  }
+  if (!mode && (phase_mask & 1)) VSIE_CUDA(cudaMemsetAsync(y, 0, sizeof(double2) * h->n, st));
+  return VSIE_OK;
+}
+
+static vsie_status forward(vsie_handle* h, double2* y, int precision, double2* slots_given,
+                           cudaStream_t st, int phase_mask, int* launches) {
+  const ForwardPlans P = forward_plans(h, precision);
+  double2* slots = slots_given;
+  if (!slots) VSIE_TRY(handle_slots(h, P.slots, &slots));
+  if (precision == 32) return forward_sums<float>(h, y, P, slots, st, phase_mask, launches);
+  return forward_sums<double>(h, y, P, slots, st, phase_mask, launches);
+}
+
+// phase 1: the volume (G) sum; phase 2: interface (K) and heterogeneous-volume (F) sums
+vsie_status far_sum_g(vsie_handle* h, double2* y, int precision, cudaStream_t st, int* launches) {
+  return forward(h, y, precision, nullptr, st, 1, launches);
+}
+vsie_status far_sum_f(vsie_handle* h, double2* y, int precision, cudaStream_t st, int* launches) {
+  return forward(h, y, precision, nullptr, st, 2, launches);
 }
 
 vsie_status far_apply(vsie_handle* h, const double2* x, double2* y, int precision,
                       cudaStream_t st) {
   VSIE_TRY(far_prescale(h, x, precision, st, nullptr));
-  VSIE_TRY(far_sum_g(h, y, precision, st, nullptr));
-  VSIE_TRY(far_sum_f(h, y, precision, st, nullptr));
-  return VSIE_OK;
+  return forward(h, y, precision, nullptr, st, 3, nullptr);
 }
-
-// ---------------------------------------------------------------------------------
-// Far-field sums whose source-split partials go to caller-provided scratch instead of
-// the handle's lazily grown buffer (used by the allocation-free apply).
 
 size_t far_split_elems(const vsie_handle* h) {
-  size_t need = 0;
-  const Sources* cls[2] = {&h->G, &h->F};
-  for (const Sources* S : cls) {
-    if (!S->n || !h->n) continue;
-    const Launch L = plan(h, h->n, S->n, kT);
-    if (L.nsplit > 1) need = std::max(need, (size_t)L.nsplit * (size_t)h->n);
-  }
-  return need;
-}
-
-template <class R>
-static void launch_g_into(const vsie_handle* h, const typename Vec4<R>::type* tgt, int64_t nt,
-                          const typename Vec4<R>::type* sa, const R* sb, int64_t ns, double2* out,
-                          int mode, double2* scratch, cudaStream_t st) {
-  const R kk = (R)(h->k0 / (2.0 * kPi));
-  const Launch L = plan(h, nt, ns, kT);
-  if (L.nsplit == 1) {
-    far_g_kernel<R, kT><<<L.grid, kBlock, 0, st>>>(tgt, nt, sa, sb, ns, L.chunk, kk, out, mode);
-  } else {
-    far_g_kernel<R, kT><<<L.grid, kBlock, 0, st>>>(tgt, nt, sa, sb, ns, L.chunk, kk, scratch, 0);
-    reduce_split_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(scratch, L.nsplit, nt, out, mode);
-  }
-}
-
-template <class R>
-static void launch_f_into(const vsie_handle* h, const typename Vec4<R>::type* tgt, int64_t nt,
-                          const typename Vec4<R>::type* src, int64_t ns, double2* out, int mode,
-                          double2* scratch, cudaStream_t st) {
-  const R k = (R)h->k0, kk = (R)(h->k0 / (2.0 * kPi));
-  const Launch L = plan(h, nt, ns, kT);
-  if (L.nsplit == 1) {
-    far_f_kernel<R, kT><<<L.grid, kBlock, 0, st>>>(tgt, nt, src, ns, L.chunk, k, kk, out, mode);
-  } else {
-    far_f_kernel<R, kT><<<L.grid, kBlock, 0, st>>>(tgt, nt, src, ns, L.chunk, k, kk, scratch, 0);
-    reduce_split_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(scratch, L.nsplit, nt, out, mode);
-  }
+  return std::max(forward_plans(h, 32).slots, forward_plans(h, 64).slots);
 }
 
 vsie_status far_sums_into(vsie_handle* h, double2* y, int precision, double2* scratch,
                           cudaStream_t st) {
-  Sources& G = h->G;
-  Sources& F = h->F;
-  const int64_t n = h->n;
-  if (!G.n && !F.n) {
-    VSIE_CUDA(cudaMemsetAsync(y, 0, sizeof(double2) * n, st));
-    return VSIE_OK;
-  }
-  if (G.n) {
-    if (precision == 32)
-      launch_g_into<float>(h, h->tgt32, n, G.r32a, G.r32b, G.n, y, 0, scratch, st);
-    else
-      launch_g_into<double>(h, h->tgt64, n, G.r64a, G.r64b, G.n, y, 0, scratch, st);
-  }
-  if (F.n) {
-    const int mode = G.n ? 1 : 0;
-    if (precision == 32)
-      launch_f_into<float>(h, h->tgt32, n, F.r32a, F.n, y, mode, scratch, st);
-    else
-      launch_f_into<double>(h, h->tgt64, n, F.r64a, F.n, y, mode, scratch, st);
-  }
-  VSIE_CUDA(cudaGetLastError());
-  return VSIE_OK;
+  return forward(h, y, precision, scratch, st, 3, nullptr);
 }
+
+// ----------------------------------------------------------------- adjoint apply
 
 vsie_status far_adjoint(vsie_handle* h, const double2* lam, double2* x, int precision,
                         cudaStream_t st) {
-  Sources& G = h->G;
-  Sources& F = h->F;
   const int64_t n = h->n;
+  const double kap = h->k0 / kTwoPi;
   AdjRecords* A = &h->adj;
+  Sources* cls[3] = {&h->G, &h->K, &h->F};
   if (!A->w) {
-    VSIE_TRY(dalloc_t(h, &A->g_p32, (size_t)G.n));
-    VSIE_TRY(dalloc_t(h, &A->f_p32, (size_t)F.n));
-    VSIE_TRY(dalloc_t(h, &A->f_v32, (size_t)F.n));
+    int64_t maxn = 1;
+    for (Sources* S : cls) maxn = std::max<int64_t>(maxn, S->n);
+    for (Sources* S : cls) {
+      VSIE_TRY(dalloc_t(h, &S->adj_p32, (size_t)S->n));
+      VSIE_TRY(dalloc_t(h, &S->adj_v32, (size_t)S->n));
+      VSIE_TRY(dalloc_t(h, &S->adj_p64, (size_t)S->n));
+      VSIE_TRY(dalloc_t(h, &S->adj_v64, (size_t)S->n));
+      if (S->n)
+        point_records_kernel<<<nblk(S->n), 256, 0, st>>>(S->pos_s, S->vvec, S->n, kap, S->adj_p32,
+                                                          S->adj_v32, S->adj_p64, S->adj_v64);
+    }
     VSIE_TRY(dalloc_t(h, &A->c_a32, (size_t)n));
     VSIE_TRY(dalloc_t(h, &A->c_b32, (size_t)n));
     VSIE_TRY(dalloc_t(h, &A->c_a64, (size_t)n));
     VSIE_TRY(dalloc_t(h, &A->c_b64, (size_t)n));
-    VSIE_TRY(dalloc_t(h, &A->w, (size_t)(G.n > F.n ? G.n : F.n)));
-    if (G.n) point_records_kernel<<<nblk(G.n), 256, 0, st>>>(G.pos_s, nullptr, G.n, A->g_p32, nullptr);
-    if (F.n) point_records_kernel<<<nblk(F.n), 256, 0, st>>>(F.pos_s, F.vvec, F.n, A->f_p32, A->f_v32);
+    VSIE_TRY(dalloc_t(h, &A->w, (size_t)maxn));
     VSIE_CUDA(cudaGetLastError());
   }
-  prescale_colloc_kernel<<<nblk(n), 256, 0, st>>>(h->tgt64, lam, n, precision, A->c_a32, A->c_b32,
+  prescale_colloc_kernel<<<nblk(n), 256, 0, st>>>(h->tgt64, lam, n, kap, precision, A->c_a32, A->c_b32,
                                                   A->c_a64, A->c_b64);
   VSIE_CUDA(cudaGetLastError());
-  const double k = h->k0, kk = h->k0 / (2.0 * kPi);
-  // G class: w_j = sum_i (e^{ikr}/r) c_i, then x_e = conj(sum_j -s_j w_j)
-  if (G.n) {
-    if (precision == 32)
-      VSIE_TRY(launch_g<float>(h, A->g_p32, G.n, A->c_a32, A->c_b32, n, A->w, 0, st));
-    else
-      VSIE_TRY(launch_g<double>(h, G.pos_s, G.n, A->c_a64, A->c_b64, n, A->w, 0, st));
-    gather_adjoint_kernel<<<nblk(G.n_elem), 256, 0, st>>>(A->w, G.pos_s, 1, G.elem_first,
-                                                          G.elem_list, G.n_elem, x);
-  }
-  if (F.n) {
-    Launch L = plan(h, F.n, n, kT);
-    double2* dst = A->w;
-    double2* part = nullptr;
-    if (L.nsplit > 1) {
-      VSIE_TRY(split_scratch(h, (size_t)L.nsplit * F.n, &part));
-      dst = part;
+  for (int c = 0; c < 3; ++c) {
+    Sources& S = *cls[c];
+    if (!S.n) continue;
+    double2* slots = nullptr;
+    if (c == 0) {
+      // G: w_j = sum_i (e^{ikr}/r) c_i, x_e = conj(sum_j -s_j w_j)
+      if (precision == 32) {
+        const StreamK sk = plan_sk<float, PolG<float>>(h, S.n, n);
+        VSIE_TRY(handle_slots(h, slot_elems(sk), &slots));
+        PolG<float> p{S.adj_p32, 1.0f, A->c_a32, A->c_b32};
+        VSIE_TRY((run_nbody<float, PolG<float>>(p, sk, A->w, 0, slots, st, nullptr)));
+      } else {
+        const StreamK sk = plan_sk<double, PolG<double>>(h, S.n, n);
+        VSIE_TRY(handle_slots(h, slot_elems(sk), &slots));
+        PolG<double> p{S.adj_p64, 1.0, A->c_a64, A->c_b64};
+        VSIE_TRY((run_nbody<double, PolG<double>>(p, sk, A->w, 0, slots, st, nullptr)));
+      }
+      gather_adjoint_kernel<<<nblk(S.n_elem), 256, 0, st>>>(A->w, S.pos_s, 1, S.elem_first, S.elem_list,
+                                                            S.n_elem, x);
+    } else {
+      // K and F: w_j = sum_i (e^{ikr}/r)[-s_j + (ikr - 1)((x_i - y_j).v_j)/r^2] c_i
+      if (precision == 32) {
+        const StreamK sk = plan_sk<float, PolAF<float>>(h, S.n, n);
+        VSIE_TRY(handle_slots(h, slot_elems(sk), &slots));
+        PolAF<float> p{S.adj_p32, S.adj_v32, A->c_a32, A->c_b32};
+        VSIE_TRY((run_nbody<float, PolAF<float>>(p, sk, A->w, 0, slots, st, nullptr)));
+      } else {
+        const StreamK sk = plan_sk<double, PolAF<double>>(h, S.n, n);
+        VSIE_TRY(handle_slots(h, slot_elems(sk), &slots));
+        PolAF<double> p{S.adj_p64, S.adj_v64, A->c_a64, A->c_b64};
+        VSIE_TRY((run_nbody<double, PolAF<double>>(p, sk, A->w, 0, slots, st, nullptr)));
+      }
+      gather_adjoint_kernel<<<nblk(S.n_elem), 256, 0, st>>>(A->w, S.pos_s, 0, S.elem_first, S.elem_list,
+                                                            S.n_elem, x);
     }
-    if (precision == 32)
-      adj_f_kernel<float, kT><<<L.grid, kBlock, 0, st>>>(A->f_p32, A->f_v32, F.n, A->c_a32, A->c_b32, n,
-                                                         L.chunk, (float)k, (float)kk, dst, 0);
-    else
-      adj_f_kernel<double, kT><<<L.grid, kBlock, 0, st>>>(F.pos_s, F.vvec, F.n, A->c_a64, A->c_b64, n,
-                                                          L.chunk, k, kk, dst, 0);
-    if (L.nsplit > 1)
-      reduce_split_kernel<<<nblk(F.n), 256, 0, st>>>(part, L.nsplit, F.n, A->w, 0);
-    gather_adjoint_kernel<<<nblk(F.n_elem), 256, 0, st>>>(A->w, F.pos_s, 0, F.elem_first,
-                                                          F.elem_list, F.n_elem, x);
   }
   VSIE_CUDA(cudaGetLastError());
   return VSIE_OK;

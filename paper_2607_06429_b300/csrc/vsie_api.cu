@@ -105,7 +105,7 @@ extern "C" vsie_status vsie_sizes(const vsie_handle* h, int64_t* n, int64_t* n_f
     return VSIE_ERR_ARG;
   }
   if (n) *n = h->n;
-  if (n_far) *n_far = h->G.n + h->F.n;
+  if (n_far) *n_far = h->G.n + h->K.n + h->F.n;
   if (nnz) *nnz = h->C.nnz;
   return VSIE_OK;
 }
@@ -228,8 +228,10 @@ static vsie_status create_impl(const vsie_mesh* mesh, const vsie_material* mat, 
   }
 
   // ---------------------------------------------------------------- far-field sources
-  std::vector<double4_32a> g_ps, f_ps, f_v;
-  std::vector<int32_t> g_own, f_own, g_first, g_elem, f_first, f_elem;
+  // G: volume points with grad(alpha) = 0; F: volume points with grad(alpha) != 0;
+  // K: interface points (v = sigma n, sigma = -omega w since dG/dn_y = -grad_x G . n).
+  std::vector<double4_32a> g_ps, f_ps, f_v, k_ps, k_v, k_aux;
+  std::vector<int32_t> g_own, f_own, k_own, g_first, g_elem, f_first, f_elem, k_first, k_elem;
   for (int64_t e = 0; e < nt; ++e) {
     const bool has_v = tet_ga[e].x != 0.0 || tet_ga[e].y != 0.0 || tet_ga[e].z != 0.0;
     auto& ps = has_v ? f_ps : g_ps;
@@ -238,68 +240,68 @@ static vsie_status create_impl(const vsie_mesh* mesh, const vsie_material* mat, 
     auto& el = has_v ? f_elem : g_elem;
     first.push_back((int32_t)ps.size());
     el.push_back((int32_t)e);
-    if (FP == 1) {
-      const double w = tet_vol[e];
-      ps.push_back(make_double4_32a(tet_cen[e].x, tet_cen[e].y, tet_cen[e].z, tet_s[e] * w));
+    const int npts = FP == 1 ? 1 : 4;
+    const double w = tet_vol[e] / npts;
+    for (int q = 0; q < npts; ++q) {
+      const double4_32a y = FP == 1 ? tet_cen[e] : tet_pts[4 * e + q];
+      ps.push_back(make_double4_32a(y.x, y.y, y.z, tet_s[e] * w));
       own.push_back((int32_t)e);
       if (has_v) f_v.push_back(make_double4_32a(tet_ga[e].x * w, tet_ga[e].y * w, tet_ga[e].z * w, 0.0));
-    } else {
-      const double w = 0.25 * tet_vol[e];
-      for (int q = 0; q < 4; ++q) {
-        const double4_32a y = tet_pts[4 * e + q];
-        ps.push_back(make_double4_32a(y.x, y.y, y.z, tet_s[e] * w));
-        own.push_back((int32_t)e);
-        if (has_v) f_v.push_back(make_double4_32a(tet_ga[e].x * w, tet_ga[e].y * w, tet_ga[e].z * w, 0.0));
-      }
     }
   }
   for (int64_t t = 0; t < ns; ++t) {
-    f_first.push_back((int32_t)f_ps.size());
-    f_elem.push_back((int32_t)(nt + t));
+    k_first.push_back((int32_t)k_ps.size());
+    k_elem.push_back((int32_t)(nt + t));
     const double w = tri_nrm[t].w / 3.0;
-    const double sc = -tri_omega[t] * w;  // v = -omega n w  (dG/dn_y = -grad_x G . n)
+    const double sigma = -tri_omega[t] * w;
     for (int q = 0; q < 3; ++q) {
       const double4_32a y = tri_pts[3 * t + q];
-      f_ps.push_back(make_double4_32a(y.x, y.y, y.z, 0.0));
-      f_v.push_back(make_double4_32a(sc * tri_nrm[t].x, sc * tri_nrm[t].y, sc * tri_nrm[t].z, 0.0));
-      f_own.push_back((int32_t)(nt + t));
+      k_ps.push_back(make_double4_32a(y.x, y.y, y.z, 0.0));
+      k_v.push_back(make_double4_32a(sigma * tri_nrm[t].x, sigma * tri_nrm[t].y, sigma * tri_nrm[t].z, 0.0));
+      k_aux.push_back(make_double4_32a(tri_nrm[t].x, tri_nrm[t].y, tri_nrm[t].z, sigma));
+      k_own.push_back((int32_t)(nt + t));
     }
   }
   g_first.push_back((int32_t)g_ps.size());
   f_first.push_back((int32_t)f_ps.size());
+  k_first.push_back((int32_t)k_ps.size());
 
   // ---------------------------------------------------------------- targets
   std::vector<double4_32a> tgt(h->n);
   std::vector<float4> tgt32(h->n);
   for (int64_t e = 0; e < nt; ++e) tgt[e] = tet_cen[e];
   for (int64_t t = 0; t < ns; ++t) tgt[nt + t] = tri_cen[t];
+  const double kap = k0 / (2.0 * kPi);  // positions in units of the wavelength
   for (int64_t i = 0; i < h->n; ++i)
-    tgt32[i] = make_float4((float)tgt[i].x, (float)tgt[i].y, (float)tgt[i].z, 0.0f);
+    tgt32[i] = make_float4((float)(kap * tgt[i].x), (float)(kap * tgt[i].y), (float)(kap * tgt[i].z), 0.0f);
 
   VSIE_TRY(upload(h, &h->tgt64, tgt));
   VSIE_TRY(upload(h, &h->tgt32, tgt32));
   VSIE_TRY(upload(h, &h->mass, mass));
 
   auto setup_class = [&](Sources& S, const std::vector<double4_32a>& ps, const std::vector<double4_32a>* vv,
-                         const std::vector<int32_t>& own, const std::vector<int32_t>& first,
-                         const std::vector<int32_t>& el, int recs32) -> vsie_status {
+                         const std::vector<double4_32a>* aux, const std::vector<int32_t>& own,
+                         const std::vector<int32_t>& first, const std::vector<int32_t>& el,
+                         int recs) -> vsie_status {
     S.n = (int64_t)ps.size();
     S.n_elem = (int64_t)el.size();
     VSIE_TRY(upload(h, &S.pos_s, ps));
     if (vv) VSIE_TRY(upload(h, &S.vvec, *vv));
+    if (aux) VSIE_TRY(upload(h, &S.aux, *aux));
     VSIE_TRY(upload(h, &S.owner, own));
     VSIE_TRY(upload(h, &S.elem_first, first));
     VSIE_TRY(upload(h, &S.elem_list, el));
-    VSIE_TRY(dalloc_t(h, &S.r32a, (size_t)recs32 * S.n));
-    VSIE_TRY(dalloc_t(h, &S.r64a, (size_t)recs32 * S.n));
-    if (recs32 == 1) {
+    VSIE_TRY(dalloc_t(h, &S.r32a, (size_t)recs * S.n));
+    VSIE_TRY(dalloc_t(h, &S.r64a, (size_t)recs * S.n));
+    if (recs == 1) {
       VSIE_TRY(dalloc_t(h, &S.r32b, (size_t)S.n));
       VSIE_TRY(dalloc_t(h, &S.r64b, (size_t)S.n));
     }
     return VSIE_OK;
   };
-  VSIE_TRY(setup_class(h->G, g_ps, nullptr, g_own, g_first, g_elem, 1));
-  VSIE_TRY(setup_class(h->F, f_ps, &f_v, f_own, f_first, f_elem, 3));
+  VSIE_TRY(setup_class(h->G, g_ps, nullptr, nullptr, g_own, g_first, g_elem, 1));
+  VSIE_TRY(setup_class(h->K, k_ps, &k_v, &k_aux, k_own, k_first, k_elem, 2));
+  VSIE_TRY(setup_class(h->F, f_ps, &f_v, nullptr, f_own, f_first, f_elem, 3));
 
   // ---------------------------------------------------------------- correction matrix
   double4_32a *d_tet_cen, *d_tet_pts, *d_tet_ga, *d_tri_vtx, *d_tri_nrm, *d_tri_pts, *d_tri_cen;

@@ -33,28 +33,35 @@ vsie_status cuda_fail(cudaError_t e, const char* what, const char* file, int lin
     if (_s != VSIE_OK) return _s;          \
   } while (0)
 
-// Far-field source records.  Sources come in two classes:
-//   G: volume quadrature points whose density is locally constant (v = 0): weight s only;
-//   F: points with a vector weight v (interface points, and volume points with
-//      grad(alpha) != 0), which may also carry s.
-// Charges per apply: q = -s p/(4 pi) (complex), u = v p/(4 pi) (complex 3-vector).
-// FP32 records (written per apply by the prescale kernels):
-//   G: float4 (x, y, z, q.re) + float q.im
-//   F: 3 x float4 (x, y, z, q.re) (q.im, ux.re, ux.im, uy.re) (uy.im, uz.re, uz.im, 0)
-// FP64 records: the same layouts with double4_32a / double.
+// Far-field source points, in three classes (one kernel each):
+//   G: volume quadrature points whose density is locally constant (v = 0): weight s;
+//   K: interface quadrature points (s = 0, v = sigma n with sigma = -omega w);
+//   F: volume points with grad(alpha) != 0 (both s and v).
+// Static FP64 data: pos_s = (x, y, z, s), vvec = (vx, vy, vz, 0) (K and F), and for K
+// aux = (nx, ny, nz, sigma).  Per-apply records written by the prescale kernels, with
+// positions scaled by kappa = k0/(2 pi) and the kappa powers folded into the charges:
+//   G: (x, y, z, q.re) + q.im                       (r32a n, r32b n)
+//   K: (x, y, z, c.re) (c.im, nx, ny, nz)           (r32a 2n)
+//   F: (x, y, z, q.re) (q.im, ux.re, ux.im, uy.re) (uy.im, uz.re, uz.im, 0)  (r32a 3n)
+// and the same layouts in FP64 (r64a, r64b).
 struct Sources {
   int64_t n = 0;
-  double4_32a* pos_s = nullptr;   // (x, y, z, s) FP64, static
-  double4_32a* vvec = nullptr;    // (vx, vy, vz, 0) FP64, static (class F only)
-  int32_t* owner = nullptr;   // unknown index e(j)
-  int32_t* elem_first = nullptr;  // CSR-like point ranges per owning element (adjoint)
+  double4_32a* pos_s = nullptr;
+  double4_32a* vvec = nullptr;
+  double4_32a* aux = nullptr;
+  int32_t* owner = nullptr;       // unknown index e(j)
+  int32_t* elem_first = nullptr;  // point ranges per owning element (n_elem + 1)
   int32_t* elem_list = nullptr;   // owning unknown of each range
   int64_t n_elem = 0;
-  // per-apply records
-  float4* r32a = nullptr;     // G: n records; F: 3n records
-  float* r32b = nullptr;      // G: q.im
+  float4* r32a = nullptr;
+  float* r32b = nullptr;
   double4_32a* r64a = nullptr;
   double* r64b = nullptr;
+  // adjoint target records (built on first adjoint call): (kappa y, s), (kappa v, 0)
+  float4* adj_p32 = nullptr;
+  float4* adj_v32 = nullptr;
+  double4_32a* adj_p64 = nullptr;
+  double4_32a* adj_v64 = nullptr;
 };
 
 struct Correction {
@@ -65,17 +72,13 @@ struct Correction {
   double2* val32 = nullptr;    // accurate - far-rule value (FP32-rounded coordinates)
 };
 
-// Static point records and per-call buffers of the adjoint far-field sum (built on
-// first use).
+// Per-call buffers of the adjoint far-field sum (allocated on the first adjoint call).
 struct AdjRecords {
-  float4* g_p32 = nullptr;
-  float4* f_p32 = nullptr;
-  float4* f_v32 = nullptr;
-  float4* c_a32 = nullptr;
+  float4* c_a32 = nullptr;   // collocation records (kappa x, c.re), c = kappa conj(lam)/(4 pi)
   float* c_b32 = nullptr;
   double4_32a* c_a64 = nullptr;
   double* c_b64 = nullptr;
-  double2* w = nullptr;
+  double2* w = nullptr;      // per-source-point sums
 };
 
 }  // namespace vsie
@@ -90,17 +93,17 @@ struct vsie_handle {
   int tile_override = 0;
 
   double4_32a* tgt64 = nullptr;   // (x, y, z, 0) collocation points, FP64
-  float4* tgt32 = nullptr;    // FP32-rounded copies
+  float4* tgt32 = nullptr;    // FP32 copies of kappa * x (kappa = k0/(2 pi))
   double* mass = nullptr;     // mass function m at the collocation points
 
-  vsie::Sources G, F;
+  vsie::Sources G, K, F;
   vsie::Correction C;
 
   // library-owned scratch
   double2* host_x = nullptr;  // device staging of vsie_apply_host
   double2* host_y = nullptr;
   int64_t host_cols = 0;
-  double2* split = nullptr;   // source-split partial sums of the far-field kernels
+  double2* split = nullptr;   // per-block partial-tile slots of the far-field kernels
   size_t split_elems = 0;
   vsie::AdjRecords adj;
 
@@ -128,12 +131,13 @@ vsie_status build_correction(vsie_handle* h, const double4_32a* d_tet_cen,
 // Far-field sums: y (+)= sum_j C(x_i, y_j) p_e(j) over the far-field source points.
 vsie_status far_apply(vsie_handle* h, const double2* x, double2* y, int precision,
                       cudaStream_t st);
-// The three phases of far_apply (launch counters optional).
+// The phases of far_apply (launch counters optional): prescale; the volume (G) sum;
+// the interface (K) and heterogeneous-volume (F) sums.
 vsie_status far_prescale(vsie_handle* h, const double2* x, int precision, cudaStream_t st,
                          int* launches);
 vsie_status far_sum_g(vsie_handle* h, double2* y, int precision, cudaStream_t st, int* launches);
 vsie_status far_sum_f(vsie_handle* h, double2* y, int precision, cudaStream_t st, int* launches);
-// Both far-field sums with source-split partials in caller-provided scratch; the scratch
+// All far-field sums with the partial-tile slots in caller-provided scratch; the scratch
 // must hold far_split_elems(h) double2 values (nothing is allocated).
 size_t far_split_elems(const vsie_handle* h);
 vsie_status far_sums_into(vsie_handle* h, double2* y, int precision, double2* scratch,
