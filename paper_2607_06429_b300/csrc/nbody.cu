@@ -326,6 +326,211 @@ struct PolAF {
   }
 };
 
+// Block-level interface over a per-target policy: kT independent targets per thread.
+template <class R, class B>
+struct PerTarget : B {
+  using typename B::Src;
+  using typename B::Smem;
+  struct Tgts {
+    typename B::Tgt t[kT];
+  };
+  struct Part {
+    R ar[kT], ai[kT];
+  };
+  __device__ __forceinline__ void load_targets(int64_t i0, int64_t nt, Tgts& tg) const {
+#pragma unroll
+    for (int t = 0; t < kT; ++t) {
+      const int64_t i = i0 + (int64_t)t * kBlock;
+      B::load_target(i, i < nt, tg.t[t]);
+    }
+  }
+  __device__ __forceinline__ void zero(Part& q) const {
+#pragma unroll
+    for (int t = 0; t < kT; ++t) q.ar[t] = q.ai[t] = R(0);
+  }
+  __device__ __forceinline__ void accumulate(const Src& s, const Tgts& tg, Part& q) const {
+#pragma unroll
+    for (int t = 0; t < kT; ++t) B::pair(s, tg.t[t], q.ar[t], q.ai[t]);
+  }
+  __device__ __forceinline__ void unpack(const Part& q, R* ar, R* ai) const {
+#pragma unroll
+    for (int t = 0; t < kT; ++t) {
+      ar[t] = q.ar[t];
+      ai[t] = q.ai[t];
+    }
+  }
+};
+
+// ----------------------------------------------------------------- packed FP32 policies
+// Blackwell's paired FP32 instructions (two lanes' worth of add/mul/fma per issue slot)
+// evaluate two targets per instruction.  Targets (t0, t2) and (t1, t3) form the packed
+// pairs; source records are staged in shared memory already duplicated (and negated
+// where the formula subtracts), so every packed operand is a single 64-bit load.
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// e^{2 pi i t} for a packed pair, plus rinv = 1/|d~| (0 at coincidence) and t.
+__device__ __forceinline__ void phase2(float2 r2, float2& rinv, float2& t, float2& cs, float2& sn) {
+  rinv.x = (r2.x > 0.0f) ? rsqrtf(r2.x) : 0.0f;
+  rinv.y = (r2.y > 0.0f) ? rsqrtf(r2.y) : 0.0f;
+  t = __fmul2_rn(r2, rinv);
+  const float2 u = __fadd2_rn(t, f2(12582912.0f));       // t + 1.5*2^23
+  const float2 w = __fadd2_rn(u, f2(-12582912.0f));      // round(t)
+  const float2 f = __ffma2_rn(w, f2(-1.0f), t);          // t - round(t), exact
+  const float2 a = __fmul2_rn(f, f2(6.28318530717958647692f));
+  __sincosf(a.x, &sn.x, &cs.x);
+  __sincosf(a.y, &sn.y, &cs.y);
+}
+
+struct Tgts2 {
+  float2 x[kT / 2], y[kT / 2], z[kT / 2];  // packed pair p holds targets (p, p + kT/2)
+};
+
+__device__ __forceinline__ void load_targets2(const float4* __restrict__ tgt, int64_t i0, int64_t nt,
+                                              Tgts2& tg) {
+#pragma unroll
+  for (int p = 0; p < kT / 2; ++p) {
+    const int64_t ia = i0 + (int64_t)p * kBlock, ib = i0 + (int64_t)(p + kT / 2) * kBlock;
+    const float4 a = ia < nt ? tgt[ia] : make_float4(0, 0, 0, 0);
+    const float4 b = ib < nt ? tgt[ib] : make_float4(0, 0, 0, 0);
+    tg.x[p] = make_float2(a.x, b.x);
+    tg.y[p] = make_float2(a.y, b.y);
+    tg.z[p] = make_float2(a.z, b.z);
+  }
+}
+
+struct Part2 {
+  float2 ar[kT / 2], ai[kT / 2];
+};
+
+__device__ __forceinline__ void zero2(Part2& q) {
+#pragma unroll
+  for (int p = 0; p < kT / 2; ++p) q.ar[p] = q.ai[p] = make_float2(0.0f, 0.0f);
+}
+
+__device__ __forceinline__ void unpack2(const Part2& q, float* ar, float* ai) {
+#pragma unroll
+  for (int p = 0; p < kT / 2; ++p) {
+    ar[p] = q.ar[p].x;
+    ai[p] = q.ai[p].x;
+    ar[p + kT / 2] = q.ar[p].y;
+    ai[p + kT / 2] = q.ai[p].y;
+  }
+}
+
+// Volume sources (G class), y += e^{2 pi i t} rinv q~.
+// Smem per source: (-x, -x, -y, -y) (-z, -z, q.re, q.re) (q.im, q.im, -q.im, -q.im)
+struct PolG2 {
+  struct Smem {
+    float4 a[kBlock], b[kBlock], c[kBlock];
+  };
+  struct Src {
+    float4 a, b, c;
+  };
+  using Tgts = Tgts2;
+  using Part = Part2;
+  const float4* __restrict__ tgt;
+  const float4* __restrict__ sa;
+  const float* __restrict__ sb;
+
+  __device__ __forceinline__ void load_targets(int64_t i0, int64_t nt, Tgts& tg) const {
+    load_targets2(tgt, i0, nt, tg);
+  }
+  __device__ __forceinline__ void stage(Smem& sm, int64_t j, bool ok, int tid) const {
+    float4 r = ok ? sa[j] : make_float4(0, 0, 0, 0);
+    const float qi = ok ? sb[j] : 0.0f;
+    sm.a[tid] = make_float4(-r.x, -r.x, -r.y, -r.y);
+    sm.b[tid] = make_float4(-r.z, -r.z, r.w, r.w);
+    sm.c[tid] = make_float4(qi, qi, -qi, -qi);
+  }
+  __device__ __forceinline__ Src get(const Smem& sm, int jj) const { return Src{sm.a[jj], sm.b[jj], sm.c[jj]}; }
+  __device__ __forceinline__ void zero(Part& q) const { zero2(q); }
+  __device__ __forceinline__ void unpack(const Part& q, float* ar, float* ai) const { unpack2(q, ar, ai); }
+  __device__ __forceinline__ void accumulate(const Src& s, const Tgts& tg, Part& q) const {
+    const float2 nx = make_float2(s.a.x, s.a.y), ny = make_float2(s.a.z, s.a.w);
+    const float2 nz = make_float2(s.b.x, s.b.y), qr = make_float2(s.b.z, s.b.w);
+    const float2 qi = make_float2(s.c.x, s.c.y), nqi = make_float2(s.c.z, s.c.w);
+#pragma unroll
+    for (int p = 0; p < kT / 2; ++p) {
+      const float2 dx = __fadd2_rn(tg.x[p], nx), dy = __fadd2_rn(tg.y[p], ny), dz = __fadd2_rn(tg.z[p], nz);
+      float2 r2 = __fmul2_rn(dx, dx);
+      r2 = __ffma2_rn(dy, dy, r2);
+      r2 = __ffma2_rn(dz, dz, r2);
+      float2 rinv, t, cs, sn;
+      phase2(r2, rinv, t, cs, sn);
+      const float2 er = __fmul2_rn(cs, rinv), ei = __fmul2_rn(sn, rinv);
+      q.ar[p] = __ffma2_rn(er, qr, q.ar[p]);
+      q.ar[p] = __ffma2_rn(ei, nqi, q.ar[p]);
+      q.ai[p] = __ffma2_rn(er, qi, q.ai[p]);
+      q.ai[p] = __ffma2_rn(ei, qr, q.ai[p]);
+    }
+  }
+};
+
+// Interface sources (K class), y += e^{2 pi i t}(2 pi i t - 1)(d~ . n) rinv^3 c~.
+// With A = cos + kr sin and Q = kr cos - sin (kr = 2 pi t):
+//   re += -g3 (A c.re + Q c.im),  im += g3 (Q c.re - A c.im),  g3 = rinv^3 (d~ . n).
+// Smem per source: (-x,-x,-y,-y) (-z,-z,nx,nx) (ny,ny,nz,nz) (-c.re,-c.re,-c.im,-c.im) (c.re,c.re,0,0)
+struct PolK2 {
+  struct Smem {
+    float4 a[kBlock], b[kBlock], c[kBlock], d[kBlock], e[kBlock];
+  };
+  struct Src {
+    float4 a, b, c, d, e;
+  };
+  using Tgts = Tgts2;
+  using Part = Part2;
+  const float4* __restrict__ tgt;
+  const float4* __restrict__ src;  // 2 records per source: (x, y, z, c.re) (c.im, nx, ny, nz)
+
+  __device__ __forceinline__ void load_targets(int64_t i0, int64_t nt, Tgts& tg) const {
+    load_targets2(tgt, i0, nt, tg);
+  }
+  __device__ __forceinline__ void stage(Smem& sm, int64_t j, bool ok, int tid) const {
+    const float4 r = ok ? src[2 * j] : make_float4(0, 0, 0, 0);
+    const float4 v = ok ? src[2 * j + 1] : make_float4(0, 0, 0, 0);
+    sm.a[tid] = make_float4(-r.x, -r.x, -r.y, -r.y);
+    sm.b[tid] = make_float4(-r.z, -r.z, v.y, v.y);
+    sm.c[tid] = make_float4(v.z, v.z, v.w, v.w);
+    sm.d[tid] = make_float4(-r.w, -r.w, -v.x, -v.x);
+    sm.e[tid] = make_float4(r.w, r.w, 0.0f, 0.0f);
+  }
+  __device__ __forceinline__ Src get(const Smem& sm, int jj) const {
+    return Src{sm.a[jj], sm.b[jj], sm.c[jj], sm.d[jj], sm.e[jj]};
+  }
+  __device__ __forceinline__ void zero(Part& q) const { zero2(q); }
+  __device__ __forceinline__ void unpack(const Part& q, float* ar, float* ai) const { unpack2(q, ar, ai); }
+  __device__ __forceinline__ void accumulate(const Src& s, const Tgts& tg, Part& q) const {
+    const float2 nx = make_float2(s.a.x, s.a.y), ny = make_float2(s.a.z, s.a.w);
+    const float2 nz = make_float2(s.b.x, s.b.y), ux = make_float2(s.b.z, s.b.w);
+    const float2 uy = make_float2(s.c.x, s.c.y), uz = make_float2(s.c.z, s.c.w);
+    const float2 ncr = make_float2(s.d.x, s.d.y), nci = make_float2(s.d.z, s.d.w);
+    const float2 cr = make_float2(s.e.x, s.e.y);
+#pragma unroll
+    for (int p = 0; p < kT / 2; ++p) {
+      const float2 dx = __fadd2_rn(tg.x[p], nx), dy = __fadd2_rn(tg.y[p], ny), dz = __fadd2_rn(tg.z[p], nz);
+      float2 r2 = __fmul2_rn(dx, dx);
+      r2 = __ffma2_rn(dy, dy, r2);
+      r2 = __ffma2_rn(dz, dz, r2);
+      float2 rinv, t, cs, sn;
+      phase2(r2, rinv, t, cs, sn);
+      float2 dn = __fmul2_rn(dx, ux);
+      dn = __ffma2_rn(dy, uy, dn);
+      dn = __ffma2_rn(dz, uz, dn);
+      const float2 ri2 = __fmul2_rn(rinv, rinv);
+      const float2 g3 = __fmul2_rn(__fmul2_rn(ri2, rinv), dn);
+      const float2 kr = __fmul2_rn(t, f2(6.28318530717958647692f));
+      const float2 A = __ffma2_rn(kr, sn, cs);                        // cos + kr sin
+      const float2 Q = __ffma2_rn(kr, cs, __fmul2_rn(sn, f2(-1.0f)));  // kr cos - sin
+      const float2 gA = __fmul2_rn(g3, A), gQ = __fmul2_rn(g3, Q);
+      q.ar[p] = __ffma2_rn(gA, ncr, q.ar[p]);   // - gA c.re
+      q.ar[p] = __ffma2_rn(gQ, nci, q.ar[p]);   // - gQ c.im
+      q.ai[p] = __ffma2_rn(gQ, cr, q.ai[p]);    // + gQ c.re
+      q.ai[p] = __ffma2_rn(gA, nci, q.ai[p]);   // - gA c.im
+    }
+  }
+};
+
 // ----------------------------------------------------------------- persistent driver
 
 struct StreamK {
@@ -350,30 +555,24 @@ __global__ void __launch_bounds__(kBlock) nbody_kernel(P p, StreamK sk, double2*
     const int64_t tile = k / sk.nchunk;
     const int64_t c0 = k - tile * sk.nchunk;
     const int64_t c1 = min(sk.nchunk, c0 + (k1 - k));
-    typename P::Tgt tg[kT];
+    typename P::Tgts tg;
     Acc<R> acc[kT];
+    p.load_targets(tile * kTile + tid, sk.nt, tg);
 #pragma unroll
-    for (int t = 0; t < kT; ++t) {
-      const int64_t i = tile * kTile + (int64_t)t * kBlock + tid;
-      p.load_target(i, i < sk.nt, tg[t]);
-      acc[t].zero();
-    }
+    for (int t = 0; t < kT; ++t) acc[t].zero();
     const int64_t j_begin = c0 * kChunk;
     const int64_t j_end = min(sk.ns, c1 * kChunk);
     for (int64_t j0 = j_begin; j0 < j_end; j0 += kBlock) {
       const int64_t j = j0 + tid;
       p.stage(sm, j, j < j_end, tid);
       __syncthreads();
-      R ar[kT], ai[kT];
-#pragma unroll
-      for (int t = 0; t < kT; ++t) ar[t] = ai[t] = R(0);
+      typename P::Part part;
+      p.zero(part);
 #pragma unroll 4
-      for (int jj = 0; jj < kBlock; ++jj) {
-        const typename P::Src s = p.get(sm, jj);
-#pragma unroll
-        for (int t = 0; t < kT; ++t) p.pair(s, tg[t], ar[t], ai[t]);
-      }
+      for (int jj = 0; jj < kBlock; ++jj) p.accumulate(p.get(sm, jj), tg, part);
       __syncthreads();
+      R ar[kT], ai[kT];
+      p.unpack(part, ar, ai);
 #pragma unroll
       for (int t = 0; t < kT; ++t) acc[t].fold(ar[t], ai[t]);
     }
@@ -646,46 +845,86 @@ static ForwardPlans forward_plans(const vsie_handle* h, int precision) {
   ForwardPlans P;
   const int64_t n = h->n;
   if (precision == 32) {
-    P.g = plan_sk<float, PolG<float>>(h, n, h->G.n);
-    P.k = plan_sk<float, PolK<float>>(h, n, h->K.n);
-    P.f = plan_sk<float, PolF<float>>(h, n, h->F.n);
+    P.g = plan_sk<float, PolG2>(h, n, h->G.n);
+    P.k = plan_sk<float, PolK2>(h, n, h->K.n);
+    P.f = plan_sk<float, PerTarget<float, PolF<float>>>(h, n, h->F.n);
   } else {
-    P.g = plan_sk<double, PolG<double>>(h, n, h->G.n);
-    P.k = plan_sk<double, PolK<double>>(h, n, h->K.n);
-    P.f = plan_sk<double, PolF<double>>(h, n, h->F.n);
+    P.g = plan_sk<double, PerTarget<double, PolG<double>>>(h, n, h->G.n);
+    P.k = plan_sk<double, PerTarget<double, PolK<double>>>(h, n, h->K.n);
+    P.f = plan_sk<double, PerTarget<double, PolF<double>>>(h, n, h->F.n);
   }
   P.slots = std::max(slot_elems(P.g), std::max(slot_elems(P.k), slot_elems(P.f)));
   return P;
 }
 
 template <class R>
-static vsie_status forward_sums(vsie_handle* h, double2* y, const ForwardPlans& P, double2* slots,
-                                cudaStream_t st, int phase_mask, int* launches) {
+struct PolicySet {
+  using G = PerTarget<R, PolG<R>>;
+  using K = PerTarget<R, PolK<R>>;
+  using F = PerTarget<R, PolF<R>>;
+};
+template <>
+struct PolicySet<float> {
+  using G = PolG2;
+  using K = PolK2;
+  using F = PerTarget<float, PolF<float>>;
+};
+
+template <class R>
+static typename PolicySet<R>::G make_g(const vsie_handle* h);
+template <>
+PolG2 make_g<float>(const vsie_handle* h) {
+  return PolG2{h->tgt32, h->G.r32a, h->G.r32b};
+}
+template <>
+PerTarget<double, PolG<double>> make_g<double>(const vsie_handle* h) {
+  PerTarget<double, PolG<double>> p;
+  p.tgt = h->tgt64;
+  p.tscale = h->k0 / kTwoPi;
+  p.sa = h->G.r64a;
+  p.sb = h->G.r64b;
+  return p;
+}
+template <class R>
+static typename PolicySet<R>::K make_k(const vsie_handle* h);
+template <>
+PolK2 make_k<float>(const vsie_handle* h) {
+  return PolK2{h->tgt32, h->K.r32a};
+}
+template <>
+PerTarget<double, PolK<double>> make_k<double>(const vsie_handle* h) {
+  PerTarget<double, PolK<double>> p;
+  p.tgt = h->tgt64;
+  p.tscale = h->k0 / kTwoPi;
+  p.src = h->K.r64a;
+  return p;
+}
+template <class R>
+static PerTarget<R, PolF<R>> make_f(const vsie_handle* h) {
+  PerTarget<R, PolF<R>> p;
   using V = typename Vec4<R>::type;
   const bool fp32 = sizeof(R) == 4;
-  const V* tgt = fp32 ? reinterpret_cast<const V*>(h->tgt32) : reinterpret_cast<const V*>(h->tgt64);
-  const R tscale = fp32 ? R(1) : (R)(h->k0 / kTwoPi);  // FP32 targets are stored scaled
+  p.tgt = reinterpret_cast<const V*>(fp32 ? (const void*)h->tgt32 : (const void*)h->tgt64);
+  p.tscale = fp32 ? R(1) : (R)(h->k0 / kTwoPi);
+  p.src = reinterpret_cast<const V*>(fp32 ? (const void*)h->F.r32a : (const void*)h->F.r64a);
+  return p;
+}
+
+template <class R>
+static vsie_status forward_sums(vsie_handle* h, double2* y, const ForwardPlans& P, double2* slots,
+                                cudaStream_t st, int phase_mask, int* launches) {
+  using PS = PolicySet<R>;
   int mode = 0;
   if (h->G.n) {
-    if (phase_mask & 1) {
-      PolG<R> p{tgt, tscale, reinterpret_cast<const V*>(fp32 ? (const void*)h->G.r32a : (const void*)h->G.r64a),
-                reinterpret_cast<const R*>(fp32 ? (const void*)h->G.r32b : (const void*)h->G.r64b)};
-      VSIE_TRY((run_nbody<R, PolG<R>>(p, P.g, y, mode, slots, st, launches)));
-    }
+    if (phase_mask & 1) VSIE_TRY((run_nbody<R, typename PS::G>(make_g<R>(h), P.g, y, mode, slots, st, launches)));
     mode = 1;
   }
   if (h->K.n) {
-    if (phase_mask & 2) {
-      PolK<R> p{tgt, tscale, reinterpret_cast<const V*>(fp32 ? (const void*)h->K.r32a : (const void*)h->K.r64a)};
-      VSIE_TRY((run_nbody<R, PolK<R>>(p, P.k, y, mode, slots, st, launches)));
-    }
+    if (phase_mask & 2) VSIE_TRY((run_nbody<R, typename PS::K>(make_k<R>(h), P.k, y, mode, slots, st, launches)));
     mode = 1;
   }
   if (h->F.n) {
-    if (phase_mask & 2) {
-      PolF<R> p{tgt, tscale, reinterpret_cast<const V*>(fp32 ? (const void*)h->F.r32a : (const void*)h->F.r64a)};
-      VSIE_TRY((run_nbody<R, PolF<R>>(p, P.f, y, mode, slots, st, launches)));
-    }
+    if (phase_mask & 2) VSIE_TRY((run_nbody<R, typename PS::F>(make_f<R>(h), P.f, y, mode, slots, st, launches)));
     mode = 1;
   }
   if (!mode && (phase_mask & 1)) VSIE_CUDA(cudaMemsetAsync(y, 0, sizeof(double2) * h->n, st));
@@ -761,30 +1000,45 @@ vsie_status far_adjoint(vsie_handle* h, const double2* lam, double2* x, int prec
     if (c == 0) {
       // G: w_j = sum_i (e^{ikr}/r) c_i, x_e = conj(sum_j -s_j w_j)
       if (precision == 32) {
-        const StreamK sk = plan_sk<float, PolG<float>>(h, S.n, n);
+        const StreamK sk = plan_sk<float, PolG2>(h, S.n, n);
         VSIE_TRY(handle_slots(h, slot_elems(sk), &slots));
-        PolG<float> p{S.adj_p32, 1.0f, A->c_a32, A->c_b32};
-        VSIE_TRY((run_nbody<float, PolG<float>>(p, sk, A->w, 0, slots, st, nullptr)));
+        PolG2 p{S.adj_p32, A->c_a32, A->c_b32};
+        VSIE_TRY((run_nbody<float, PolG2>(p, sk, A->w, 0, slots, st, nullptr)));
       } else {
-        const StreamK sk = plan_sk<double, PolG<double>>(h, S.n, n);
+        using PG = PerTarget<double, PolG<double>>;
+        const StreamK sk = plan_sk<double, PG>(h, S.n, n);
         VSIE_TRY(handle_slots(h, slot_elems(sk), &slots));
-        PolG<double> p{S.adj_p64, 1.0, A->c_a64, A->c_b64};
-        VSIE_TRY((run_nbody<double, PolG<double>>(p, sk, A->w, 0, slots, st, nullptr)));
+        PG p;
+        p.tgt = S.adj_p64;
+        p.tscale = 1.0;
+        p.sa = A->c_a64;
+        p.sb = A->c_b64;
+        VSIE_TRY((run_nbody<double, PG>(p, sk, A->w, 0, slots, st, nullptr)));
       }
       gather_adjoint_kernel<<<nblk(S.n_elem), 256, 0, st>>>(A->w, S.pos_s, 1, S.elem_first, S.elem_list,
                                                             S.n_elem, x);
     } else {
       // K and F: w_j = sum_i (e^{ikr}/r)[-s_j + (ikr - 1)((x_i - y_j).v_j)/r^2] c_i
       if (precision == 32) {
-        const StreamK sk = plan_sk<float, PolAF<float>>(h, S.n, n);
+        using PA = PerTarget<float, PolAF<float>>;
+        const StreamK sk = plan_sk<float, PA>(h, S.n, n);
         VSIE_TRY(handle_slots(h, slot_elems(sk), &slots));
-        PolAF<float> p{S.adj_p32, S.adj_v32, A->c_a32, A->c_b32};
-        VSIE_TRY((run_nbody<float, PolAF<float>>(p, sk, A->w, 0, slots, st, nullptr)));
+        PA p;
+        p.tps = S.adj_p32;
+        p.tv = S.adj_v32;
+        p.sa = A->c_a32;
+        p.sb = A->c_b32;
+        VSIE_TRY((run_nbody<float, PA>(p, sk, A->w, 0, slots, st, nullptr)));
       } else {
-        const StreamK sk = plan_sk<double, PolAF<double>>(h, S.n, n);
+        using PA = PerTarget<double, PolAF<double>>;
+        const StreamK sk = plan_sk<double, PA>(h, S.n, n);
         VSIE_TRY(handle_slots(h, slot_elems(sk), &slots));
-        PolAF<double> p{S.adj_p64, S.adj_v64, A->c_a64, A->c_b64};
-        VSIE_TRY((run_nbody<double, PolAF<double>>(p, sk, A->w, 0, slots, st, nullptr)));
+        PA p;
+        p.tps = S.adj_p64;
+        p.tv = S.adj_v64;
+        p.sa = A->c_a64;
+        p.sb = A->c_b64;
+        VSIE_TRY((run_nbody<double, PA>(p, sk, A->w, 0, slots, st, nullptr)));
       }
       gather_adjoint_kernel<<<nblk(S.n_elem), 256, 0, st>>>(A->w, S.pos_s, 0, S.elem_first, S.elem_list,
                                                             S.n_elem, x);
