@@ -142,6 +142,17 @@ vsie_status vsie_apply_timed(vsie_handle* h, const void* d_x, void* d_y, int32_t
 vsie_status vsie_apply_noalloc(vsie_handle* h, const void* d_x, void* d_y, int32_t nrhs,
                                int32_t precision, void* stream);
 
+/* y = A x for a block of nrhs right-hand sides with the far-field sums over volume and
+ * interface sources contracted on the tensor cores: each tile of kernel values is
+ * evaluated once in FP32 and multiplied into 64 charge columns at a time (three-term
+ * TF32 split, FP32 accumulation folded into FP64 every 2048 sources).  Volume sources with
+ * grad(alpha) != 0, the correction and the mass use the per-column FP32 path.  Same
+ * layouts as vsie_apply (precision 32).  Blocks until done (reads the kernels' timeout
+ * flag).  Errors: VSIE_ERR_ARG, VSIE_ERR_OOM, VSIE_ERR_CUDA (also when a bounded wait in
+ * the tensor-core kernel expired). */
+vsie_status vsie_apply_batched(vsie_handle* h, const void* d_x, void* d_y, int32_t nrhs,
+                               void* stream);
+
 /* x = A^H y (conjugate transpose), same layouts and precisions as vsie_apply. */
 vsie_status vsie_adjoint_apply(vsie_handle* h, const void* d_y, void* d_x, int32_t nrhs,
                                int32_t precision, void* stream);

@@ -24,7 +24,7 @@ STATUS = {
 VSIE_ERR_NOT_CONVERGED = 5
 
 EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_apply_host",
-           "vsie_apply_timed", "vsie_apply_noalloc",
+           "vsie_apply_timed", "vsie_apply_noalloc", "vsie_apply_batched",
            "vsie_adjoint_apply", "vsie_plane_wave_rhs", "vsie_far_field", "vsie_solve",
            "vsie_last_error")
 
@@ -95,6 +95,7 @@ def load_library(path: str = LIB_PATH):
     lib.vsie_apply.argtypes = [P, P, P, I32, I32, P]
     lib.vsie_apply_host.argtypes = [P, P, P, I32, I32, P]
     lib.vsie_apply_noalloc.argtypes = [P, P, P, I32, I32, P]
+    lib.vsie_apply_batched.argtypes = [P, P, P, I32, P]
     lib.vsie_adjoint_apply.argtypes = [P, P, P, I32, I32, P]
     lib.vsie_apply_timed.argtypes = [P, P, P, I32, P, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(I32)]
@@ -206,6 +207,15 @@ class Operator:
             y = torch.empty_like(x)
         _check(_lib.vsie_apply(self._h, _dev(x, "x"), _dev(y, "y"), nrhs, int(precision),
                                _stream(stream)))
+        return y
+
+    def apply_batched(self, x, y=None, stream=None):
+        """Y = A X for a block (nrhs, n) with the tensor-core far field (vsie_apply_batched)."""
+        import torch
+        nrhs = self._nrhs(x)
+        if y is None:
+            y = torch.empty_like(x)
+        _check(_lib.vsie_apply_batched(self._h, _dev(x, "x"), _dev(y, "y"), nrhs, _stream(stream)))
         return y
 
     def apply_noalloc(self, x, y, precision=32, stream=None):

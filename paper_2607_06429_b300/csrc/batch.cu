@@ -1,0 +1,589 @@
+// Multi-right-hand-side far-field sums on the 5th-generation tensor cores (tcgen05).
+//
+// For R right-hand sides the far-field sum of one source class is a dense contraction
+//     Y[i, r] = sum_j C(x_i, y_j) q_j^(r),
+// where the kernel tile C (complex) depends on the geometry only.  Each tile of C is
+// evaluated once in FP32 on the CUDA cores and contracted with a block of R = 64 charge
+// columns on the tensor cores, so the sine/cosine/rsqrt work is amortised R-fold.
+//
+// Precision: the contraction runs as three TF32 products with FP32 accumulation
+// (C_hi Q_hi + C_hi Q_lo + C_lo Q_hi, where x_hi = tf32(x), x_lo = tf32(x - x_hi)),
+// about 21 significant bits per product.  The FP32 tensor accumulator is folded into
+// FP64 registers every 2048 sources.  Complex arithmetic uses four real products,
+//     Y_re = C_re Q_re - C_im Q_im,   Y_im = C_re Q_im + C_im Q_re,
+// the minus sign coming from the instruction descriptor's negate-B bit.
+//
+// Layout.  One CTA (512 threads, one per SM) owns a tile of 128 targets (the MMA M) and
+// streams the sources in tiles of 16 (the MMA K is 8, two k-steps per tile).
+//   * A operands (128 x 16, K-major, no swizzle, 8 x 16-byte core matrices): C_re and
+//     C_im, hi and lo, written to shared memory by the evaluating threads;
+//   * B operands (64 x 16 per matrix): Q_re, Q_im, hi and lo, prepared per apply in
+//     global memory as the exact shared-memory image of each source tile, preceded by the
+//     tile's 16 source records, and fetched with one bulk asynchronous copy (TMA engine)
+//     that completes on an mbarrier;
+//   * the accumulator D (128 lanes x 128 FP32 columns: Y_re | Y_im) lives in tensor
+//     memory, allocated by warp 0; every 2048 sources it is added into an FP64
+//     accumulator that each CTA keeps in its own slot of global memory (L2-resident).
+// Pipeline: two stages of evaluated operands and eight of charge images, so the copy
+// engine runs up to seven tiles ahead of the tensor cores (covering the HBM latency of
+// the 16.5 KB image copies) while the CUDA cores evaluate the next tile.  Work is split over the CTAs with
+// the same balanced item ranges (target tile, 2048-source chunk) and deterministic fix-up
+// as the single-RHS sums.  Every wait on an mbarrier is bounded; on expiry the kernel
+// records an error code, stops issuing work and still releases its tensor memory.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "vsie_internal.h"
+
+namespace vsie {
+
+constexpr int BT_M = 128;             // targets per CTA tile
+constexpr int BT_S = 16;              // sources per tile (MMA K = 8: two k-steps)
+constexpr int BT_R = 64;              // right-hand sides per launch
+constexpr int BT_CHUNK_TILES = 128;   // source tiles per work item (2048 sources)
+constexpr int BT_A_MAT = BT_M * BT_S * 4;        // 8 KB per A matrix
+constexpr int BT_B_MAT = BT_R * BT_S * 4;        // 4 KB per B matrix
+constexpr int BT_HDR = BT_S * 32;                // 16 source records of 32 bytes
+constexpr int BT_IMG = BT_HDR + 4 * BT_B_MAT;    // per-tile image in global memory
+constexpr int BT_NA = 2;                         // stages of evaluated A operands (32 KB each)
+constexpr int BT_NB = 8;                         // stages of charge images (prefetch distance 7)
+constexpr int BT_A_STAGE = 4 * BT_A_MAT;         // 32,768 bytes
+constexpr int BT_B_OFF = BT_NA * BT_A_STAGE;     // image stages follow the A stages
+constexpr int BT_BAR_OFF = BT_B_OFF + BT_NB * BT_IMG;
+constexpr int BT_SMEM = BT_BAR_OFF + 8 * (BT_NA + 2 * BT_NB + 1) + 16;
+static_assert(BT_IMG % 16 == 0 && BT_BAR_OFF % 8 == 0, "alignment");
+static_assert(BT_SMEM <= 227 * 1024, "shared memory budget");
+constexpr uint32_t BT_WAIT_LIMIT = 1u << 22;
+
+// byte offset of element (row, k) in a K-major, no-swizzle operand with K = 16:
+// core matrices of 8 rows x 16 bytes; along K they are 128 bytes apart (leading byte
+// offset), along rows 512 bytes apart (stride byte offset).
+__host__ __device__ __forceinline__ uint32_t bt_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 512 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(128u >> 4) << 16;   // leading byte offset: next core matrix along K
+  d |= (uint64_t)(512u >> 4) << 32;   // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;             // descriptor version (sm_100 family)
+  return d;                           // base offset 0, no swizzle
+}
+
+// instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 64
+__host__ __device__ constexpr uint32_t bt_idesc(bool negate_b) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((negate_b ? 1u : 0u) << 14) |
+         ((uint32_t)(BT_R >> 3) << 17) | ((uint32_t)(BT_M >> 4) << 24);
+}
+
+__device__ __forceinline__ float tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < BT_WAIT_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// ----------------------------------------------------------------- tile evaluation
+
+// Per-source record in the image header (32 bytes): (x~, y~, z~, 0) (nx, ny, nz, 0).
+// G class:  C~ = e^{2 pi i t} / |d~|
+// K class:  C~ = e^{2 pi i t} (2 pi i t - 1)(d~ . n) / |d~|^3
+struct EvalG {
+  static constexpr bool kNormal = false;
+};
+struct EvalK {
+  static constexpr bool kNormal = true;
+};
+
+template <class Ev>
+__device__ __forceinline__ float2 eval_pair(float tx, float ty, float tz, float4 s, float4 nrm) {
+  const float dx = tx - s.x, dy = ty - s.y, dz = tz - s.z;
+  const float r2 = dx * dx + dy * dy + dz * dz;
+  const float rinv = (r2 > 0.0f) ? rsqrtf(r2) : 0.0f;
+  const float t = r2 * rinv;
+  const float rt = __fsub_rn(__fadd_rn(t, 12582912.0f), 12582912.0f);
+  const float f = __fsub_rn(t, rt);
+  float sn, cs;
+  __sincosf(f * 6.28318530717958647692f, &sn, &cs);
+  if (!Ev::kNormal) return make_float2(cs * rinv, sn * rinv);
+  const float dn = dx * nrm.x + dy * nrm.y + dz * nrm.z;
+  const float g3 = rinv * rinv * rinv * dn;
+  const float kr = t * 6.28318530717958647692f;
+  // (cos + i sin)(i kr - 1) = -(cos + kr sin) + i (kr cos - sin)
+  return make_float2(-g3 * (cs + kr * sn), g3 * (kr * cs - sn));
+}
+
+struct BatchArgs {
+  const float4* tgt;        // kappa-scaled FP32 target positions (n)
+  const unsigned char* img; // per-source-tile images (n_src_tiles * BT_IMG bytes)
+  int64_t nt;               // targets
+  int64_t ntiles_src;       // source tiles
+  int64_t ntile_t;          // target tiles
+  int64_t nchunk;           // chunks of BT_CHUNK_TILES source tiles
+  int64_t nitems;
+  int64_t grid;
+  double2* out;             // n x nrhs_out column-major
+  int64_t ld_out;           // n
+  int nrhs_out;             // columns written (<= BT_R)
+  int mode;                 // 0 store, 1 add
+  double* slots;            // [2 grid][2][BT_R][BT_M] FP64 accumulators / partial tiles
+  int* status;              // nonzero on a timed-out wait
+};
+
+__device__ __forceinline__ int64_t bt_begin(const BatchArgs& a, int64_t b) { return (b * a.nitems) / a.grid; }
+
+// Warp roles: warps 0-15 (512 threads) evaluate the kernel tile and fold the tensor
+// accumulator; warp 16 issues the bulk copies and, from one lane, the MMAs.  They meet
+// only through mbarriers (a_full per A stage; b_full, mma_done per image stage; d_free per chunk), so
+// evaluation, copies and tensor-core work overlap across the three stages.
+constexpr int BT_EVAL_THREADS = 512;
+constexpr int BT_ALL_THREADS = BT_EVAL_THREADS + 32;
+
+template <class Ev>
+__global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + BT_BAR_OFF);
+  uint64_t* a_full = bars;                      // [NA] evaluated A operands written (16 warp arrivals)
+  uint64_t* b_full = bars + BT_NA;              // [NB] charge image landed (tx bytes)
+  uint64_t* mma_done = bars + BT_NA + BT_NB;    // [NB] MMAs of tile g retired (index g % NB)
+  uint64_t* d_free = bars + BT_NA + 2 * BT_NB;  // accumulator read by the folding warps (16 arrivals)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + BT_NA + 2 * BT_NB + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int i = 0; i < BT_NA; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(a_full + i)), "r"(16));
+    for (int i = 0; i < BT_NB; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b_full + i)), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(mma_done + i)), "r"(1));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(d_free)), "r"(16));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  bool err = false;
+  const int64_t b = blockIdx.x;
+  const int64_t k0 = bt_begin(a, b), k1 = bt_begin(a, b + 1);
+
+  if (warp == BT_EVAL_THREADS / 32) {
+    // ------------------------------------------------------------ producer warp
+    if (lane == 0) {
+      // copy cursor (runs up to NS tiles ahead of the MMA cursor)
+      int64_t pk = k0, ps = 0, pend = 0;
+      bool pstarted = false;
+      auto pnext = [&]() -> int64_t {
+        if (!pstarted) {
+          pstarted = true;
+          if (pk >= k1) return -1;
+          ps = (pk % a.nchunk) * BT_CHUNK_TILES;
+          pend = min(a.ntiles_src, ps + BT_CHUNK_TILES);
+          return ps;
+        }
+        if (pk >= k1) return -1;
+        if (++ps < pend) return ps;
+        if (++pk >= k1) return -1;
+        ps = (pk % a.nchunk) * BT_CHUNK_TILES;
+        pend = min(a.ntiles_src, ps + BT_CHUNK_TILES);
+        return ps;
+      };
+      uint32_t gp = 0;  // copies issued
+      auto refill = [&](uint32_t g_limit) {
+        // issue copies for tiles gp < g_limit; image stage gp % NB was last read by tile gp - NB
+        while (gp < g_limit && !err) {
+          const int64_t s_next = pnext();
+          if (s_next < 0) {
+            gp = 0xFFFFFFFFu;  // no more tiles
+            break;
+          }
+          const int st2 = gp % BT_NB;
+          if (gp >= BT_NB) err = !mbar_wait(mma_done + st2, ((gp - BT_NB) / BT_NB) & 1);
+          if (err) break;
+          unsigned char* bimg = smem + BT_B_OFF + st2 * BT_IMG;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b_full + st2)),
+                       "r"(BT_IMG)
+                       : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  su32(bimg)),
+              "l"(a.img + s_next * (int64_t)BT_IMG), "r"(BT_IMG), "r"(su32(b_full + st2))
+              : "memory");
+          ++gp;
+        }
+      };
+      refill(BT_NB - 1);
+      uint32_t g = 0, nchunks = 0;
+      for (int64_t k = k0; k < k1 && !err;) {
+        const int64_t tile = k / a.nchunk;
+        const int64_t c0 = k - tile * a.nchunk;
+        const int64_t c1 = min(a.nchunk, c0 + (k1 - k));
+        for (int64_t c = c0; c < c1 && !err; ++c) {
+          const int64_t s_begin = c * BT_CHUNK_TILES;
+          const int64_t s_end = min(a.ntiles_src, s_begin + BT_CHUNK_TILES);
+          // the previous chunk's accumulator must have been read before it is overwritten
+          if (nchunks > 0) err = !mbar_wait(d_free, (nchunks - 1) & 1);
+          for (int64_t s = s_begin; s < s_end && !err; ++s, ++g) {
+            const int sa = g % BT_NA, sb = g % BT_NB;
+            err = !mbar_wait(b_full + sb, (g / BT_NB) & 1) || !mbar_wait(a_full + sa, (g / BT_NA) & 1);
+            if (err) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t abase = su32(smem + sa * BT_A_STAGE);
+            const uint32_t bbase = su32(smem + BT_B_OFF + sb * BT_IMG + BT_HDR);
+            const bool fresh = (s == s_begin);
+            const uint32_t dre = tmem, dim = tmem + BT_R;
+            constexpr uint32_t ip = bt_idesc(false), in = bt_idesc(true);
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              const uint32_t kof = ks * 256;
+              const uint64_t arh = smem_desc(abase + 0 * BT_A_MAT + kof), arl = smem_desc(abase + 1 * BT_A_MAT + kof);
+              const uint64_t aih = smem_desc(abase + 2 * BT_A_MAT + kof), ail = smem_desc(abase + 3 * BT_A_MAT + kof);
+              const uint64_t brh = smem_desc(bbase + 0 * BT_B_MAT + kof), brl = smem_desc(bbase + 1 * BT_B_MAT + kof);
+              const uint64_t bih = smem_desc(bbase + 2 * BT_B_MAT + kof), bil = smem_desc(bbase + 3 * BT_B_MAT + kof);
+              const uint32_t first = (fresh && ks == 0) ? 0u : 1u;
+              // Y_re += C_re Q_re - C_im Q_im
+              mma_tf32(dre, arh, brh, ip, first);
+              mma_tf32(dre, arh, brl, ip, 1);
+              mma_tf32(dre, arl, brh, ip, 1);
+              mma_tf32(dre, aih, bih, in, 1);
+              mma_tf32(dre, aih, bil, in, 1);
+              mma_tf32(dre, ail, bih, in, 1);
+              // Y_im += C_re Q_im + C_im Q_re
+              mma_tf32(dim, arh, bih, ip, first);
+              mma_tf32(dim, arh, bil, ip, 1);
+              mma_tf32(dim, arl, bih, ip, 1);
+              mma_tf32(dim, aih, brh, ip, 1);
+              mma_tf32(dim, aih, brl, ip, 1);
+              mma_tf32(dim, ail, brh, ip, 1);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             su32(mma_done + sb))
+                         : "memory");
+            if (gp != 0xFFFFFFFFu) refill(g + BT_NB);
+          }
+          ++nchunks;
+        }
+        k = tile * a.nchunk + c1;
+      }
+      if (err) atomicExch(a.status, 1);
+    }
+  } else {
+    // ------------------------------------------------------------ evaluating warps
+    const int m = tid & (BT_M - 1);   // evaluated target row
+    const int quad = tid >> 7;        // evaluated sources 4 quad .. 4 quad + 3
+    const int lq = warp & 3;          // TMEM lane quarter this warp may read
+    const int cb = warp >> 2;         // column block of 32 read by this warp
+    uint32_t g = 0, nchunks = 0;
+    int64_t k = k0;
+    while (k < k1) {
+      const int64_t tile = k / a.nchunk;
+      const int64_t c0 = k - tile * a.nchunk;
+      const int64_t c1 = min(a.nchunk, c0 + (k1 - k));
+      const int64_t ti = tile * BT_M + m;
+      const float4 tp = ti < a.nt ? a.tgt[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
+      // FP64 accumulator of this segment: the CTA's own slot (first segment: 2b, later: 2b+1),
+      // laid out [part][rhs][row] so a warp's 32 rows are contiguous
+      const int64_t slot = (k == k0) ? 2 * b : 2 * b + 1;
+      const int row = lq * 32 + lane;
+      const int part = cb >> 1;  // 0: real, 1: imaginary
+      const int r0 = (cb & 1) * 32;
+      double* accp = a.slots + slot * (2 * BT_M * BT_R) + ((int64_t)part * BT_R + r0) * BT_M + row;
+#pragma unroll 8
+      for (int q = 0; q < 32; ++q) accp[(int64_t)q * BT_M] = 0.0;
+      for (int64_t c = c0; c < c1; ++c) {
+        const int64_t s_begin = c * BT_CHUNK_TILES;
+        const int64_t s_end = min(a.ntiles_src, s_begin + BT_CHUNK_TILES);
+        for (int64_t s = s_begin; s < s_end; ++s, ++g) {
+          const int sa = g % BT_NA, sb = g % BT_NB;
+          unsigned char* st = smem + sa * BT_A_STAGE;
+          const float4* hdr = reinterpret_cast<const float4*>(smem + BT_B_OFF + sb * BT_IMG);
+          if (!err) err = !mbar_wait(b_full + sb, (g / BT_NB) & 1);
+          // the MMAs of tile g - NA read this A stage
+          if (g >= BT_NA && !err) err = !mbar_wait(mma_done + (g - BT_NA) % BT_NB, ((g - BT_NA) / BT_NB) & 1);
+          float cre[4], cim[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = 4 * quad + q;
+            const float2 cv = eval_pair<Ev>(tp.x, tp.y, tp.z, hdr[2 * j], hdr[2 * j + 1]);
+            cre[q] = cv.x;
+            cim[q] = cv.y;
+          }
+          float4 rh, rl, ih, il;
+          float* prh = &rh.x;
+          float* prl = &rl.x;
+          float* pih = &ih.x;
+          float* pil = &il.x;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            prh[q] = tf32(cre[q]);
+            prl[q] = tf32(cre[q] - prh[q]);
+            pih[q] = tf32(cim[q]);
+            pil[q] = tf32(cim[q] - pih[q]);
+          }
+          const uint32_t o = bt_off(m, 4 * quad);
+          *reinterpret_cast<float4*>(st + 0 * BT_A_MAT + o) = rh;
+          *reinterpret_cast<float4*>(st + 1 * BT_A_MAT + o) = rl;
+          *reinterpret_cast<float4*>(st + 2 * BT_A_MAT + o) = ih;
+          *reinterpret_cast<float4*>(st + 3 * BT_A_MAT + o) = il;
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(a_full + sa)) : "memory");
+        }
+        // fold the chunk's FP32 accumulator into FP64 registers
+        if (!err && g > 0) err = !mbar_wait(mma_done + ((g - 1) % BT_NB), ((g - 1) / BT_NB) & 1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!err) {
+          uint32_t r[32];
+          const uint32_t ta = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(cb * 32);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+              : "r"(ta)
+              : "memory");
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 32; ++q) accp[(int64_t)q * BT_M] += (double)__uint_as_float(r[q]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(d_free)) : "memory");
+        ++nchunks;
+      }
+      // a complete target tile goes to the output; a partial one stays in its slot for the fix-up
+      const bool complete = (c0 == 0 && c1 == a.nchunk);
+      const int64_t i = tile * BT_M + row;
+      if (complete && i < a.nt) {
+#pragma unroll 8
+        for (int q = 0; q < 32; ++q) {
+          const int r = r0 + q;
+          if (r < a.nrhs_out) {
+            double* o = reinterpret_cast<double*>(a.out + (int64_t)r * a.ld_out + i) + part;
+            const double v = accp[(int64_t)q * BT_M];
+            *o = a.mode ? *o + v : v;
+          }
+        }
+      }
+      k = tile * a.nchunk + c1;
+    }
+    if (err && lane == 0) atomicExch(a.status, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+}
+
+__device__ __forceinline__ int64_t bt_block_of(const BatchArgs& a, int64_t k) {
+  int64_t b = (k * a.grid) / a.nitems;
+  while (b + 1 < a.grid && bt_begin(a, b + 1) <= k) ++b;
+  while (b > 0 && bt_begin(a, b) > k) --b;
+  return b;
+}
+
+// adds the pieces of target tiles that span several CTAs, in CTA order
+__global__ void batch_fixup_kernel(BatchArgs a) {
+  const int64_t tile = blockIdx.x;
+  const int64_t kf = tile * a.nchunk, kl = kf + a.nchunk - 1;
+  const int64_t bs = bt_block_of(a, kf), be = bt_block_of(a, kl);
+  if (bs == be) return;
+  for (int e = threadIdx.x; e < BT_M * a.nrhs_out; e += blockDim.x) {
+    const int row = e % BT_M, r = e / BT_M;
+    const int64_t i = tile * BT_M + row;
+    if (i >= a.nt) continue;
+    double sr = 0.0, si = 0.0;
+    for (int64_t bb = bs; bb <= be; ++bb) {
+      if (bt_begin(a, bb) == bt_begin(a, bb + 1)) continue;
+      const int64_t slot = (bb == bs && bt_begin(a, bb) != kf) ? 2 * bb + 1 : 2 * bb;
+      const double* sp = a.slots + slot * (2 * BT_M * BT_R);
+      sr += sp[(int64_t)r * BT_M + row];
+      si += sp[(int64_t)(BT_R + r) * BT_M + row];
+    }
+    double2* o = a.out + (int64_t)r * a.ld_out + i;
+    if (a.mode) {
+      const double2 v = *o;
+      *o = make_double2(v.x + sr, v.y + si);
+    } else {
+      *o = make_double2(sr, si);
+    }
+  }
+}
+
+// ----------------------------------------------------------------- per-apply images
+
+// One thread per (source tile, source in tile, rhs column): writes the tf32 hi/lo of the
+// charge's real and imaginary parts into the tile image; rhs 0 also writes the header.
+// G: q~ = -kappa s p/(4 pi);  K: c~ = kappa^2 sigma p/(4 pi) (position header + normal).
+__global__ void batch_images_kernel(const double4_32a* __restrict__ ps, const double4_32a* __restrict__ aux,
+                                    const int32_t* __restrict__ own, int64_t ns, const double2* __restrict__ x,
+                                    int64_t ld_x, int nrhs, int r_base, double kap, int is_k,
+                                    unsigned char* __restrict__ img, int64_t ntiles) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ntiles * BT_S * BT_R) return;
+  const int r = (int)(e % BT_R);
+  const int64_t js = e / BT_R;       // source slot: tile * 16 + j
+  const int64_t tile = js / BT_S;
+  const int j = (int)(js % BT_S);
+  unsigned char* base = img + tile * (int64_t)BT_IMG;
+  const bool valid = js < ns;
+  double qr = 0.0, qi = 0.0;
+  double4_32a y = make_double4_32a(0, 0, 0, 0);
+  if (valid) {
+    y = ps[js];
+    const int rr = r_base + r;
+    if (rr < nrhs) {
+      const double2 p = x[(int64_t)rr * ld_x + own[js]];
+      const double sc = is_k ? kap * kap * aux[js].w / kFourPi : -kap * y.w / kFourPi;
+      qr = sc * p.x;
+      qi = sc * p.y;
+    }
+  }
+  if (r == 0) {
+    float4* h = reinterpret_cast<float4*>(base) + 2 * j;
+    h[0] = make_float4((float)(kap * y.x), (float)(kap * y.y), (float)(kap * y.z), 0.0f);
+    if (is_k && valid) {
+      const double4_32a nn = aux[js];
+      h[1] = make_float4((float)nn.x, (float)nn.y, (float)nn.z, 0.0f);
+    } else {
+      h[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  const float fr = (float)qr, fi = (float)qi;
+  uint32_t hr, lr, hi, li;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hr) : "f"(fr));
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lr) : "f"(fr - __uint_as_float(hr)));
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(fi));
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(li) : "f"(fi - __uint_as_float(hi)));
+  unsigned char* bm = base + BT_HDR;
+  const uint32_t o = bt_off(r, j);
+  *reinterpret_cast<uint32_t*>(bm + 0 * BT_B_MAT + o) = hr;
+  *reinterpret_cast<uint32_t*>(bm + 1 * BT_B_MAT + o) = lr;
+  *reinterpret_cast<uint32_t*>(bm + 2 * BT_B_MAT + o) = hi;
+  *reinterpret_cast<uint32_t*>(bm + 3 * BT_B_MAT + o) = li;
+}
+
+// ----------------------------------------------------------------- host side
+
+static vsie_status batch_class(vsie_handle* h, const Sources& S, bool is_k, const double2* x, double2* y,
+                               int nrhs, int r_base, int mode, cudaStream_t st) {
+  if (!S.n || !h->n) return VSIE_OK;
+  const int64_t ntiles = (S.n + BT_S - 1) / BT_S;
+  const size_t img_bytes = (size_t)ntiles * BT_IMG;
+  if (h->batch.img_bytes < img_bytes) {
+    unsigned char* p = nullptr;
+    VSIE_TRY(dalloc_t(h, &p, img_bytes));
+    h->batch.img = p;
+    h->batch.img_bytes = img_bytes;
+  }
+  const double kap = h->k0 / (2.0 * kPi);
+  const int64_t nthr = ntiles * BT_S * BT_R;
+  batch_images_kernel<<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(S.pos_s, S.aux, S.owner, S.n, x, h->n, nrhs,
+                                                                      r_base, kap, is_k ? 1 : 0, h->batch.img, ntiles);
+  VSIE_CUDA(cudaGetLastError());
+  BatchArgs a;
+  a.tgt = h->tgt32;
+  a.img = h->batch.img;
+  a.nt = h->n;
+  a.ntiles_src = ntiles;
+  a.ntile_t = (h->n + BT_M - 1) / BT_M;
+  a.nchunk = (ntiles + BT_CHUNK_TILES - 1) / BT_CHUNK_TILES;
+  a.nitems = a.ntile_t * a.nchunk;
+  a.grid = std::max<int64_t>(1, std::min<int64_t>(h->num_sms > 0 ? h->num_sms : 148, a.nitems));
+  a.out = y + (int64_t)r_base * h->n;
+  a.ld_out = h->n;
+  a.nrhs_out = std::min(BT_R, nrhs - r_base);
+  a.mode = mode;
+  const size_t slot_elems = (size_t)(2 * a.grid) * 2 * BT_M * BT_R;
+  if (h->batch.slot_elems < slot_elems) {
+    double* p = nullptr;
+    VSIE_TRY(dalloc_t(h, &p, slot_elems));
+    h->batch.slots = p;
+    h->batch.slot_elems = slot_elems;
+  }
+  a.slots = h->batch.slots;
+  if (!h->batch.status) {
+    VSIE_TRY(dalloc_t(h, &h->batch.status, 1));
+    VSIE_CUDA(cudaMemsetAsync(h->batch.status, 0, sizeof(int), st));
+  }
+  a.status = h->batch.status;
+  if (is_k) {
+    VSIE_CUDA(cudaFuncSetAttribute(batch_tc_kernel<EvalK>, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
+    batch_tc_kernel<EvalK><<<(unsigned)a.grid, BT_ALL_THREADS, BT_SMEM, st>>>(a);
+  } else {
+    VSIE_CUDA(cudaFuncSetAttribute(batch_tc_kernel<EvalG>, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
+    batch_tc_kernel<EvalG><<<(unsigned)a.grid, BT_ALL_THREADS, BT_SMEM, st>>>(a);
+  }
+  VSIE_CUDA(cudaGetLastError());
+  batch_fixup_kernel<<<(unsigned)a.ntile_t, 256, 0, st>>>(a);
+  VSIE_CUDA(cudaGetLastError());
+  return VSIE_OK;
+}
+
+// y[:, r] = (far-field sums over the G and K classes) for all columns r, 64 at a time
+vsie_status far_batched_gk(vsie_handle* h, const double2* x, double2* y, int nrhs, cudaStream_t st) {
+  for (int r0 = 0; r0 < nrhs; r0 += BT_R) {
+    int mode = 0;
+    if (h->G.n) {
+      VSIE_TRY(batch_class(h, h->G, false, x, y, nrhs, r0, mode, st));
+      mode = 1;
+    }
+    if (h->K.n) {
+      VSIE_TRY(batch_class(h, h->K, true, x, y, nrhs, r0, mode, st));
+      mode = 1;
+    }
+    if (!mode) {
+      const int cols = std::min(BT_R, nrhs - r0);
+      VSIE_CUDA(cudaMemsetAsync(y + (int64_t)r0 * h->n, 0, sizeof(double2) * h->n * cols, st));
+    }
+  }
+  return VSIE_OK;
+}
+
+vsie_status batch_status(vsie_handle* h, cudaStream_t st) {
+  if (!h->batch.status) return VSIE_OK;
+  int flag = 0;
+  VSIE_CUDA(cudaMemcpyAsync(&flag, h->batch.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VSIE_CUDA(cudaStreamSynchronize(st));
+  if (flag) {
+    cudaMemsetAsync(h->batch.status, 0, sizeof(int), st);
+    set_error("batched tensor-core far-field sum: an mbarrier wait exceeded its iteration limit");
+    return VSIE_ERR_CUDA;
+  }
+  return VSIE_OK;
+}
+
+}  // namespace vsie

@@ -924,7 +924,7 @@ static vsie_status forward_sums(vsie_handle* h, double2* y, const ForwardPlans& 
     mode = 1;
   }
   if (h->F.n) {
-    if (phase_mask & 2) VSIE_TRY((run_nbody<R, typename PS::F>(make_f<R>(h), P.f, y, mode, slots, st, launches)));
+    if (phase_mask & 4) VSIE_TRY((run_nbody<R, typename PS::F>(make_f<R>(h), P.f, y, mode, slots, st, launches)));
     mode = 1;
   }
   if (!mode && (phase_mask & 1)) VSIE_CUDA(cudaMemsetAsync(y, 0, sizeof(double2) * h->n, st));
@@ -940,18 +940,25 @@ static vsie_status forward(vsie_handle* h, double2* y, int precision, double2* s
   return forward_sums<double>(h, y, P, slots, st, phase_mask, launches);
 }
 
-// phase 1: the volume (G) sum; phase 2: interface (K) and heterogeneous-volume (F) sums
+// phase bits: 1 the volume (G) sum, 2 the interface (K) sum, 4 the heterogeneous-volume (F)
+// sum; each phase stores into y if it is the first class present, else adds.
 vsie_status far_sum_g(vsie_handle* h, double2* y, int precision, cudaStream_t st, int* launches) {
   return forward(h, y, precision, nullptr, st, 1, launches);
 }
 vsie_status far_sum_f(vsie_handle* h, double2* y, int precision, cudaStream_t st, int* launches) {
-  return forward(h, y, precision, nullptr, st, 2, launches);
+  return forward(h, y, precision, nullptr, st, 6, launches);
 }
 
 vsie_status far_apply(vsie_handle* h, const double2* x, double2* y, int precision,
                       cudaStream_t st) {
   VSIE_TRY(far_prescale(h, x, precision, st, nullptr));
-  return forward(h, y, precision, nullptr, st, 3, nullptr);
+  return forward(h, y, precision, nullptr, st, 7, nullptr);
+}
+
+vsie_status far_sum_f_only(vsie_handle* h, const double2* x, double2* y, cudaStream_t st) {
+  if (!h->F.n) return VSIE_OK;
+  VSIE_TRY(far_prescale(h, x, 32, st, nullptr));
+  return forward(h, y, 32, nullptr, st, 4, nullptr);
 }
 
 size_t far_split_elems(const vsie_handle* h) {
@@ -960,7 +967,7 @@ size_t far_split_elems(const vsie_handle* h) {
 
 vsie_status far_sums_into(vsie_handle* h, double2* y, int precision, double2* scratch,
                           cudaStream_t st) {
-  return forward(h, y, precision, scratch, st, 3, nullptr);
+  return forward(h, y, precision, scratch, st, 7, nullptr);
 }
 
 // ----------------------------------------------------------------- adjoint apply

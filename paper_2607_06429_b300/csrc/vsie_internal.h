@@ -81,6 +81,15 @@ struct AdjRecords {
   double2* w = nullptr;      // per-source-point sums
 };
 
+// Buffers of the tensor-core multi-RHS path (grown on demand).
+struct BatchBuffers {
+  unsigned char* img = nullptr;  // per-source-tile images (records + tf32 charge operands)
+  size_t img_bytes = 0;
+  double* slots = nullptr;       // per-CTA FP64 accumulators / partial tiles of the fix-up
+  size_t slot_elems = 0;
+  int* status = nullptr;         // set by a timed-out mbarrier wait
+};
+
 }  // namespace vsie
 
 struct vsie_handle {
@@ -106,6 +115,7 @@ struct vsie_handle {
   double2* split = nullptr;   // per-block partial-tile slots of the far-field kernels
   size_t split_elems = 0;
   vsie::AdjRecords adj;
+  vsie::BatchBuffers batch;
 
   std::vector<void*> allocs;  // every device allocation, freed by vsie_destroy
 };
@@ -154,6 +164,14 @@ vsie_status correction_adjoint(vsie_handle* h, const double2* lam, double2* x,
 
 vsie_status apply_one(vsie_handle* h, const double2* x, double2* y, int precision,
                       cudaStream_t st);
+
+// Far-field sums over the G and K classes for nrhs columns on the tensor cores (FP32 tile
+// evaluation, three-term TF32 contraction); y is overwritten.  batch_status reads (and
+// clears) the timeout flag of those kernels, synchronising the stream.
+vsie_status far_batched_gk(vsie_handle* h, const double2* x, double2* y, int nrhs, cudaStream_t st);
+vsie_status batch_status(vsie_handle* h, cudaStream_t st);
+// Far-field sum of the F class only (added into y), for one column.
+vsie_status far_sum_f_only(vsie_handle* h, const double2* x, double2* y, cudaStream_t st);
 
 
 }  // namespace vsie
