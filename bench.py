@@ -172,6 +172,26 @@ def solve_timing(torch, B, W, name="nested24_k10", tol=1e-8):
     return out
 
 
+def batched_timing(torch, op, W, nrhs=64, steps=2):
+    """Tensor-core multi-RHS apply (vsie_apply_batched) on the same operator: one block of
+    nrhs right-hand sides per step; pair interactions counted per right-hand side."""
+    X = torch.from_numpy(np.stack([W.random_vector(op.n, 1000 + r) for r in range(nrhs)])).cuda()
+    Y = op.apply_batched(X)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        op.apply_batched(X, Y)
+    b.record()
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / steps * 1e-3
+    # agreement with the per-column FP32 apply on two columns
+    err = max(float(torch.linalg.norm(Y[r] - op.apply(X[r], precision=32)) / torch.linalg.norm(Y[r]))
+              for r in (0, nrhs - 1))
+    return {"nrhs": nrhs, "seconds_per_block": t, "interactions_per_s": op.n * op.n_far_sources * nrhs / t,
+            "max_rel_diff_vs_per_column_fp32": err}
+
+
 def flush_l2(torch, buf):
     buf.add_(1.0)
 
@@ -187,6 +207,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -285,6 +306,10 @@ def main():
               "peak_basis": f"min(MUFU {n_sm} SMs x 16/clk / 3 per pair, FP32 {n_sm} x 128/clk / 20 per pair) at {f_mhz:.0f} MHz (median SM clock sampled under load)",
               "traffic": None, "kernel_ms": g_ms}
 
+    batched = None
+    if not args.no_batched and args.precision == 32:
+        batched = batched_timing(torch, op, W)
+
     solve = None
     if not args.no_solve:
         solve = solve_timing(torch, B, W)
@@ -311,6 +336,7 @@ def main():
         "create_s": create_s,
         "roofline": rf, "peaks": pk_kind,
         "solve": solve,
+        "batched": batched,
         "cpu_baseline": cpu,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }

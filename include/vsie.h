@@ -178,6 +178,7 @@ typedef struct {
   int32_t restart;          /* Krylov basis size; 0 = max_iters (no restart)           */
   double inner_tol;         /* mode 32: relative tolerance of each inner solve         */
   int32_t max_refinements;  /* mode 32: outer refinement steps                         */
+  int32_t adjoint;          /* nonzero: solve A^H x = b (adjoint state of a gradient)   */
 } vsie_solve_opts;
 
 typedef struct {
@@ -193,6 +194,13 @@ typedef struct {
  * Returns VSIE_ERR_NOT_CONVERGED (x still written, info filled) when the limits are hit. */
 vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
                        const vsie_solve_opts* opts, vsie_solve_info* info, void* stream);
+
+/* Adjoint of vsie_far_field: x_e = (1/4pi) sum_{j in e} sum_d e^{+ik0 xhat_d.y_j}
+ * (s_j + i k0 xhat_d.v_j) r_d, i.e. x = F^H r for the far-field map F of vsie_far_field
+ * (the right-hand side of the adjoint equation of a far-field misfit).  r: device
+ * complex128 ndir x nrhs; dirs: host 3*ndir; x: device complex128 n x nrhs.  FP64. */
+vsie_status vsie_far_field_adjoint(vsie_handle* h, const void* d_r, int32_t nrhs,
+                                   const double* h_dirs, int32_t ndir, void* d_x, void* stream);
 
 /* Thread-local description of the last error ("" if none). */
 const char* vsie_last_error(void);

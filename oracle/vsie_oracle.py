@@ -374,3 +374,67 @@ def gmres(matvec, b: np.ndarray, tol: float = 1e-5, maxiter: int = 1000):
     for i in range(y.shape[0]):
         x = x + y[i] * V[i]
     return x, j + 1, rel
+
+
+# ------------------------------------------------------------------ far-field misfit gradient
+
+def far_field_matrix(D: Discretisation, dirs) -> np.ndarray:
+    """F with (F p)_d = p_inf(xhat_d) of ``Discretisation.far_field``: columns summed over the
+    far-field points of each element."""
+    n = D.n
+    dirs = np.asarray(dirs, dtype=np.float64)
+    k = D.k0
+    F = np.zeros((dirs.shape[0], n), dtype=np.complex128)
+    if D.far_points == 4:
+        for q in range(4):
+            y = D.tet_pts[:, q, :]
+            amp = (D.sdens * D.tet_vol / 4.0)[None, :] - 1j * k * (dirs @ (D.grad_alpha * (D.tet_vol / 4.0)[:, None]).T)
+            F[:, :D.n_tet] += np.exp(-1j * k * (dirs @ y.T)) * amp
+    else:
+        amp = (D.sdens * D.tet_vol)[None, :] - 1j * k * (dirs @ (D.grad_alpha * D.tet_vol[:, None]).T)
+        F[:, :D.n_tet] = np.exp(-1j * k * (dirs @ D.tet_cen.T)) * amp
+    w3 = D.tri_area / 3.0
+    vt = -(D.tri_omega * w3)[:, None] * D.tri_nrm
+    for q in range(3):
+        y = D.tri_pts[:, q, :]
+        F[:, D.n_tet:] += np.exp(-1j * k * (dirs @ y.T)) * (-1j * k * (dirs @ vt.T))
+    return F / FOUR_PI
+
+
+def misfit_and_gradient(w, dirs, target, direction):
+    """L = 1/2 sum_d |p_inf(xhat_d) - t_d|^2 for the solution of A p = p_inc, and dL/drho_e,
+    dL/dc_e for every tetrahedron (piecewise-constant density inside each element, interface
+    densities fixed), by the adjoint method:
+        A^H lam = F^H r,  r = F p - t,
+        dL/dtheta = Re[r^H (dF/dtheta) p] - Re[lam^H (dA/dtheta) p].
+    A and F depend on (rho_e, c_e) only through the single-layer weight
+    s_e = beta_e - k0^2 alpha_e of column e (linear in s_e) and the mass m_e = rho0/rho_e,
+    so dA/ds_e = A_unit[:, e] (the operator assembled with unit weight and no mass) and
+    dF/ds_e = F_unit[:, e].  Dense (tiny meshes only).  Returns (L, dL/drho, dL/dc, p)."""
+    D = Discretisation.from_workload(w)
+    A = D.assemble()
+    F = far_field_matrix(D, dirs)
+    b = D.plane_wave(direction)
+    p = np.linalg.solve(A, b)
+    r = F @ p - target
+    L = 0.5 * float(np.vdot(r, r).real)
+    lam = np.linalg.solve(A.conj().T, F.conj().T @ r)
+    # unit-weight single layer: sdens = 1 on every tetrahedron, no interface term, no mass
+    U = Discretisation.from_workload(w)
+    U.sdens = np.ones_like(U.sdens)
+    U.grad_alpha = np.zeros_like(U.grad_alpha)
+    U.tri_omega = np.zeros_like(U.tri_omega)
+    U.mass = np.zeros_like(U.mass)
+    Au = U.assemble()[:, :D.n_tet]
+    Fu = far_field_matrix(U, dirs)[:, :D.n_tet]
+    pt = p[:D.n_tet]
+    dLds = ((np.conj(r) @ Fu) * pt).real - ((np.conj(lam) @ Au) * pt).real
+    dLdm = -(np.conj(lam[:D.n_tet]) * pt).real
+    rho = np.asarray(w.rho, dtype=np.float64)
+    c = np.asarray(w.c, dtype=np.float64)
+    k0, rho0, c0 = D.k0, D.rho0, D.c0
+    # s = beta - k0^2 alpha = k0^2 (rho0/rho) ((c0/c)^2 - 1),  m = rho0/rho
+    ds_drho = -D.sdens / rho
+    ds_dc = -2.0 * k0 ** 2 * (rho0 / rho) * c0 ** 2 / c ** 3
+    dm_drho = -rho0 / rho ** 2
+    return L, dLds * ds_drho + dLdm * dm_drho, dLds * ds_dc, p

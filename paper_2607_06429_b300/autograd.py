@@ -1,0 +1,82 @@
+"""Differentiable far-field misfit of the nested VSIE (torch.autograd.Function).
+
+For per-tetrahedron density rho_e and sound speed c_e (geometry, exterior medium and
+interface densities fixed) the forward pass solves A(rho, c) p = p_inc with the library's
+GMRES, evaluates the far-field pattern u = F(rho, c) p on a set of directions and returns
+L = 1/2 sum_d |u_d - t_d|^2.  The backward pass is the adjoint method:
+
+    A^H lam = F^H r,   r = u - t,
+    dL/dtheta = Re[r^H (dF/dtheta) p] - Re[lam^H (dA/dtheta) p].
+
+A and F depend on (rho_e, c_e) through the single-layer weight
+s_e = beta_e - k0^2 alpha_e = k0^2 (rho0/rho_e)((c0/c_e)^2 - 1) of column e (Eqs. alpha, beta,
+vsie; every entry of that column is linear in s_e) and the mass m_e = rho0/rho_e
+(Eq. mass_function).  With g = F^H r and w = A^H lam - m * lam (the column sums of the
+single-layer part), the library's adjoint apply gives, per tetrahedron,
+    dL/ds_e = Re[conj(g_e - w_e) p_e] / s_e,    dL/dm_e = -Re[conj(lam_e) p_e],
+and the chain rule through s_e(rho_e, c_e) and m_e(rho_e) gives the gradients.  Elements
+with s_e = 0 (c_e = c0) are not supported (their single-layer column vanishes).
+
+Without a density-gradient term (piecewise-constant density per element, grad(alpha) = 0)
+the column of element e scales as 1/rho_e as a whole, so p_e absorbs rho_e and the far field
+does not depend on it: dL/drho vanishes identically in this discrete model.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+class FarFieldMisfit(torch.autograd.Function):
+    """L(rho, c) for a workload's geometry; rho, c: CPU float64 tensors of length n_tet."""
+
+    @staticmethod
+    def forward(ctx, rho, c, workload, dirs, target, direction, solve_kw):
+        w = workload
+        op = B.Operator(w.vert, w.tet, w.tri, rho.detach().numpy(), c.detach().numpy(), w.tri_rho_in,
+                        w.tri_rho_out, w.k0, w.rho0, w.c0, None, w.tet_far_points, w.near_radius,
+                        w.tri_near_radius)
+        b = op.plane_wave_rhs([direction])[0].contiguous()
+        p, _ = op.solve(b, **solve_kw)
+        u = op.far_field(p, dirs)
+        t = torch.as_tensor(np.asarray(target), dtype=torch.complex128, device=u.device)
+        r = (u - t).contiguous()
+        loss = 0.5 * float((r.abs() ** 2).sum().item())
+        ctx.op, ctx.p, ctx.r, ctx.dirs, ctx.solve_kw = op, p, r, dirs, solve_kw
+        ctx.k0, ctx.rho0, ctx.c0, ctx.n_tet = w.k0, w.rho0, w.c0, w.n_tet
+        ctx.save_for_backward(rho, c)
+        return torch.tensor(loss, dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        rho, c = ctx.saved_tensors
+        op, p, r, nt = ctx.op, ctx.p, ctx.r, ctx.n_tet
+        g = op.far_field_adjoint(r, ctx.dirs)
+        lam, _ = op.solve(g.contiguous(), adjoint=True, **ctx.solve_kw)
+        prec = 64 if ctx.solve_kw.get("mode", 32) == 64 else 32
+        ahl = op.adjoint_apply(lam, precision=prec)
+        rho_d = rho.to(device=p.device)
+        c_d = c.to(device=p.device)
+        m = ctx.rho0 / rho_d
+        s = ctx.k0 ** 2 * (ctx.rho0 / rho_d) * ((ctx.c0 / c_d) ** 2 - 1.0)
+        w = ahl[:nt] - m * lam[:nt]
+        dLds = (torch.conj(g[:nt] - w) * p[:nt]).real / s
+        dLdm = -(torch.conj(lam[:nt]) * p[:nt]).real
+        ds_drho = -s / rho_d
+        ds_dc = -2.0 * ctx.k0 ** 2 * (ctx.rho0 / rho_d) * ctx.c0 ** 2 / c_d ** 3
+        dm_drho = -ctx.rho0 / rho_d ** 2
+        grad_rho = (dLds * ds_drho + dLdm * dm_drho).cpu() * grad_loss
+        grad_c = (dLds * ds_dc).cpu() * grad_loss
+        op.close()
+        return grad_rho, grad_c, None, None, None, None, None
+
+
+def far_field_misfit(rho, c, workload, dirs, target, direction=(1.0, 0.0, 0.0), **solve_kw):
+    """Differentiable L(rho, c); solve_kw go to Operator.solve (default: mixed mode,
+    tolerance 1e-10)."""
+    kw = dict(mode=32, tol=1e-10, max_iters=2000, inner_tol=1e-4, max_refinements=30)
+    kw.update(solve_kw)
+    return FarFieldMisfit.apply(rho, c, workload, np.asarray(dirs, dtype=np.float64), target,
+                                tuple(direction), kw)

@@ -26,6 +26,7 @@ VSIE_ERR_NOT_CONVERGED = 5
 EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_apply_host",
            "vsie_apply_timed", "vsie_apply_noalloc", "vsie_apply_batched",
            "vsie_adjoint_apply", "vsie_plane_wave_rhs", "vsie_far_field", "vsie_solve",
+           "vsie_far_field_adjoint",
            "vsie_last_error")
 
 
@@ -56,7 +57,8 @@ class _Options(ctypes.Structure):
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("max_iters", ctypes.c_int32), ("restart", ctypes.c_int32),
-                ("inner_tol", ctypes.c_double), ("max_refinements", ctypes.c_int32)]
+                ("inner_tol", ctypes.c_double), ("max_refinements", ctypes.c_int32),
+                ("adjoint", ctypes.c_int32)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -101,6 +103,7 @@ def load_library(path: str = LIB_PATH):
                                      ctypes.POINTER(I32)]
     lib.vsie_plane_wave_rhs.argtypes = [P, P, I32, P, P]
     lib.vsie_far_field.argtypes = [P, P, I32, P, I32, P, P]
+    lib.vsie_far_field_adjoint.argtypes = [P, P, I32, P, I32, P, P]
     lib.vsie_solve.argtypes = [P, P, P, ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), P]
     lib.vsie_last_error.argtypes = []
     lib.vsie_last_error.restype = ctypes.c_char_p
@@ -279,15 +282,28 @@ class Operator:
                                    _dev(out, "out"), _stream(stream)))
         return out[0] if p.dim() == 1 else out
 
+    def far_field_adjoint(self, r, dirs, stream=None):
+        """x = F^H r for the far-field map F (vsie_far_field_adjoint); r: (ndir,) or
+        (nrhs, ndir); returns (n,) or (nrhs, n)."""
+        import torch
+        d = _f64(dirs).reshape(-1, 3)
+        rr = r if r.dim() == 2 else r[None]
+        if rr.shape[1] != d.shape[0]:
+            raise ValueError("r must have one entry per direction")
+        x = torch.empty((rr.shape[0], self.n), dtype=torch.complex128, device="cuda")
+        _check(_lib.vsie_far_field_adjoint(self._h, _dev(rr.contiguous(), "r"), rr.shape[0], _ptr(d),
+                                           d.shape[0], _dev(x, "x"), _stream(stream)))
+        return x[0] if r.dim() == 1 else x
+
     def solve(self, b, mode=32, tol=1e-8, max_iters=1000, restart=0, inner_tol=1e-4,
-              max_refinements=20, stream=None, raise_on_fail=True):
-        """x with A x = b (vsie_solve); returns (x, SolveInfo)."""
+              max_refinements=20, stream=None, raise_on_fail=True, adjoint=False):
+        """x with A x = b, or A^H x = b if adjoint (vsie_solve); returns (x, SolveInfo)."""
         import torch
         if b.dim() != 1:
             raise ValueError("vsie_solve takes one right-hand side")
         x = torch.empty_like(b)
         o = _SolveOpts(int(mode), float(tol), int(max_iters), int(restart), float(inner_tol),
-                       int(max_refinements))
+                       int(max_refinements), 1 if adjoint else 0)
         info = _SolveInfo()
         st = _lib.vsie_solve(self._h, _dev(b, "b"), _dev(x, "x"), ctypes.byref(o),
                              ctypes.byref(info), _stream(stream))

@@ -9,24 +9,28 @@
 // Precision: the contraction runs as three TF32 products with FP32 accumulation
 // (C_hi Q_hi + C_hi Q_lo + C_lo Q_hi, where x_hi = tf32(x), x_lo = tf32(x - x_hi)),
 // about 21 significant bits per product.  The FP32 tensor accumulator is folded into
-// FP64 registers every 2048 sources.  Complex arithmetic uses four real products,
-//     Y_re = C_re Q_re - C_im Q_im,   Y_im = C_re Q_im + C_im Q_re,
-// the minus sign coming from the instruction descriptor's negate-B bit.
+// FP64 every 2048 sources.  Complex arithmetic as two real products of width N = 128,
+//     [Y_re | Y_im] += C_re [Q_re | Q_im] + C_im [-Q_im | Q_re],
+// the second with the instruction descriptor's negate-B bit applied to [Q_im | -Q_re].
 //
-// Layout.  One CTA (512 threads, one per SM) owns a tile of 128 targets (the MMA M) and
-// streams the sources in tiles of 16 (the MMA K is 8, two k-steps per tile).
-//   * A operands (128 x 16, K-major, no swizzle, 8 x 16-byte core matrices): C_re and
-//     C_im, hi and lo, written to shared memory by the evaluating threads;
-//   * B operands (64 x 16 per matrix): Q_re, Q_im, hi and lo, prepared per apply in
-//     global memory as the exact shared-memory image of each source tile, preceded by the
-//     tile's 16 source records, and fetched with one bulk asynchronous copy (TMA engine)
-//     that completes on an mbarrier;
+// Layout.  One CTA (16 evaluating warps + 1 issuing warp, one CTA per SM) owns a tile of
+// 128 targets (the MMA M) and streams the sources in tiles of 16 (the MMA K is 8, two
+// k-steps per tile).
+//   * A operands (128 x 16 each): C_re and C_im, hi and lo, written straight into tensor
+//     memory by the evaluating warps (tcgen05.st), two stages of 64 columns;
+//   * B operands (64 x 16 per block, K-major, no swizzle, 8 x 16-byte core matrices):
+//     Q_re, Q_im, hi and lo, prepared per apply in global
+//     memory as the shared-memory image of each source tile, preceded by the tile's 16
+//     source records, and fetched with two bulk asynchronous copies (TMA engine) that
+//     complete on an mbarrier; the evaluating warps add the negated -Q_re blocks, so that
+//     each product is one N = 128 MMA over [Y_re | Y_im];
 //   * the accumulator D (128 lanes x 128 FP32 columns: Y_re | Y_im) lives in tensor
 //     memory, allocated by warp 0; every 2048 sources it is added into an FP64
 //     accumulator that each CTA keeps in its own slot of global memory (L2-resident).
-// Pipeline: two stages of evaluated operands and eight of charge images, so the copy
-// engine runs up to seven tiles ahead of the tensor cores (covering the HBM latency of
-// the 16.5 KB image copies) while the CUDA cores evaluate the next tile.  Work is split over the CTAs with
+// Pipeline: two stages of evaluated operands (in tensor memory) and eight of charge images
+// (in shared memory), so the copy engine runs up to seven tiles ahead of the tensor cores
+// (covering the HBM latency of the 16.5 KB image copies) while the CUDA cores evaluate the
+// next tile.  Keeping A out of shared memory leaves its bandwidth to the B operand reads.  Work is split over the CTAs with
 // the same balanced item ranges (target tile, 2048-source chunk) and deterministic fix-up
 // as the single-RHS sums.  Every wait on an mbarrier is bounded; on expiry the kernel
 // records an error code, stops issuing work and still releases its tensor memory.
@@ -44,17 +48,22 @@ constexpr int BT_M = 128;             // targets per CTA tile
 constexpr int BT_S = 16;              // sources per tile (MMA K = 8: two k-steps)
 constexpr int BT_R = 64;              // right-hand sides per launch
 constexpr int BT_CHUNK_TILES = 128;   // source tiles per work item (2048 sources)
-constexpr int BT_A_MAT = BT_M * BT_S * 4;        // 8 KB per A matrix
 constexpr int BT_B_MAT = BT_R * BT_S * 4;        // 4 KB per B matrix
 constexpr int BT_HDR = BT_S * 32;                // 16 source records of 32 bytes
 constexpr int BT_IMG = BT_HDR + 4 * BT_B_MAT;    // per-tile image in global memory
-constexpr int BT_NA = 2;                         // stages of evaluated A operands (32 KB each)
+constexpr int BT_NA = 2;                         // stages of evaluated A operands (64 TMEM columns each)
 constexpr int BT_NB = 8;                         // stages of charge images (prefetch distance 7)
-constexpr int BT_A_STAGE = 4 * BT_A_MAT;         // 32,768 bytes
-constexpr int BT_B_OFF = BT_NA * BT_A_STAGE;     // image stages follow the A stages
-constexpr int BT_BAR_OFF = BT_B_OFF + BT_NB * BT_IMG;
+// An image stage in shared memory holds [header][Q_re hi][Q_im hi][-Q_re hi][Q_re lo][Q_im lo]
+// [-Q_re lo]; the copy engine fills all but the two negated blocks, which the evaluating
+// warps write.  Stacking (Q_re; Q_im) and (Q_im; -Q_re) along N gives the two B operands
+// of the N = 128 products [Y_re | Y_im] += C_re (Q_re | Q_im) + C_im (-Q_im | Q_re).
+constexpr int BT_SIMG = BT_HDR + 6 * BT_B_MAT;   // 25,088 bytes
+constexpr int BT_S_HI = BT_HDR;                  // Q_re hi (then Q_im hi, -Q_re hi)
+constexpr int BT_S_LO = BT_HDR + 3 * BT_B_MAT;   // Q_re lo (then Q_im lo, -Q_re lo)
+constexpr int BT_B_OFF = 0;
+constexpr int BT_BAR_OFF = BT_B_OFF + BT_NB * BT_SIMG;
 constexpr int BT_SMEM = BT_BAR_OFF + 8 * (BT_NA + 2 * BT_NB + 1) + 16;
-static_assert(BT_IMG % 16 == 0 && BT_BAR_OFF % 8 == 0, "alignment");
+static_assert(BT_IMG % 16 == 0 && BT_SIMG % 16 == 0 && BT_BAR_OFF % 8 == 0, "alignment");
 static_assert(BT_SMEM <= 227 * 1024, "shared memory budget");
 constexpr uint32_t BT_WAIT_LIMIT = 1u << 22;
 
@@ -76,10 +85,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;                           // base offset 0, no swizzle
 }
 
-// instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 64
+// instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 128
 __host__ __device__ constexpr uint32_t bt_idesc(bool negate_b) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((negate_b ? 1u : 0u) << 14) |
-         ((uint32_t)(BT_R >> 3) << 17) | ((uint32_t)(BT_M >> 4) << 24);
+         ((uint32_t)((2 * BT_R) >> 3) << 17) | ((uint32_t)(BT_M >> 4) << 24);
 }
 
 __device__ __forceinline__ float tf32(float x) {
@@ -99,6 +108,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (ok) return true;
   }
   return false;
+}
+
+// A operand in tensor memory (row i of A in lane i, one 32-bit column per k)
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -186,13 +205,13 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(128));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(256));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tslot;
+  const uint32_t tmem = *tslot;  // columns 0-127: accumulator; 128 + 64 s ...: A stage s
   bool err = false;
   const int64_t b = blockIdx.x;
   const int64_t k0 = bt_begin(a, b), k1 = bt_begin(a, b + 1);
@@ -230,14 +249,21 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
           const int st2 = gp % BT_NB;
           if (gp >= BT_NB) err = !mbar_wait(mma_done + st2, ((gp - BT_NB) / BT_NB) & 1);
           if (err) break;
-          unsigned char* bimg = smem + BT_B_OFF + st2 * BT_IMG;
+          unsigned char* bimg = smem + BT_B_OFF + st2 * BT_SIMG;
+          const unsigned char* gimg = a.img + s_next * (int64_t)BT_IMG;
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b_full + st2)),
                        "r"(BT_IMG)
                        : "memory");
+          // [header][Q_re hi][Q_im hi] and [Q_re lo][Q_im lo]
           asm volatile(
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                   su32(bimg)),
-              "l"(a.img + s_next * (int64_t)BT_IMG), "r"(BT_IMG), "r"(su32(b_full + st2))
+              "l"(gimg), "r"(BT_HDR + 2 * BT_B_MAT), "r"(su32(b_full + st2))
+              : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  su32(bimg + BT_S_LO)),
+              "l"(gimg + BT_HDR + 2 * BT_B_MAT), "r"(2 * BT_B_MAT), "r"(su32(b_full + st2))
               : "memory");
           ++gp;
         }
@@ -258,33 +284,26 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
             err = !mbar_wait(b_full + sb, (g / BT_NB) & 1) || !mbar_wait(a_full + sa, (g / BT_NA) & 1);
             if (err) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t abase = su32(smem + sa * BT_A_STAGE);
-            const uint32_t bbase = su32(smem + BT_B_OFF + sb * BT_IMG + BT_HDR);
+            const uint32_t acol = tmem + 128 + 64 * sa;  // C_re hi, C_re lo, C_im hi, C_im lo: 16 columns each
+            const uint32_t bbase = su32(smem + BT_B_OFF + sb * BT_SIMG);
             const bool fresh = (s == s_begin);
-            const uint32_t dre = tmem, dim = tmem + BT_R;
             constexpr uint32_t ip = bt_idesc(false), in = bt_idesc(true);
+            // B windows: (Q_re; Q_im) and (Q_im; -Q_re) of the hi and lo parts, the second
+            // negated by the descriptor.
+            const uint32_t ar[2] = {acol + 0, acol + 16};
+            const uint32_t ai[2] = {acol + 32, acol + 48};
+            const uint32_t bre[2] = {bbase + BT_S_HI, bbase + BT_S_LO};
+            const uint32_t bim[2] = {bbase + BT_S_HI + BT_B_MAT, bbase + BT_S_LO + BT_B_MAT};
+            const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};  // hi hi, hi lo, lo hi
+            uint32_t acc_flag = fresh ? 0u : 1u;
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-              const uint32_t kof = ks * 256;
-              const uint64_t arh = smem_desc(abase + 0 * BT_A_MAT + kof), arl = smem_desc(abase + 1 * BT_A_MAT + kof);
-              const uint64_t aih = smem_desc(abase + 2 * BT_A_MAT + kof), ail = smem_desc(abase + 3 * BT_A_MAT + kof);
-              const uint64_t brh = smem_desc(bbase + 0 * BT_B_MAT + kof), brl = smem_desc(bbase + 1 * BT_B_MAT + kof);
-              const uint64_t bih = smem_desc(bbase + 2 * BT_B_MAT + kof), bil = smem_desc(bbase + 3 * BT_B_MAT + kof);
-              const uint32_t first = (fresh && ks == 0) ? 0u : 1u;
-              // Y_re += C_re Q_re - C_im Q_im
-              mma_tf32(dre, arh, brh, ip, first);
-              mma_tf32(dre, arh, brl, ip, 1);
-              mma_tf32(dre, arl, brh, ip, 1);
-              mma_tf32(dre, aih, bih, in, 1);
-              mma_tf32(dre, aih, bil, in, 1);
-              mma_tf32(dre, ail, bih, in, 1);
-              // Y_im += C_re Q_im + C_im Q_re
-              mma_tf32(dim, arh, bih, ip, first);
-              mma_tf32(dim, arh, bil, ip, 1);
-              mma_tf32(dim, arl, bih, ip, 1);
-              mma_tf32(dim, aih, brh, ip, 1);
-              mma_tf32(dim, aih, brl, ip, 1);
-              mma_tf32(dim, ail, brh, ip, 1);
+            for (int pp = 0; pp < 3; ++pp) {
+#pragma unroll
+              for (int ks = 0; ks < 2; ++ks) {
+                mma_tf32_ta(tmem, ar[pa[pp]] + 8 * ks, smem_desc(bre[pb[pp]] + ks * 256), ip, acc_flag);
+                acc_flag = 1u;
+                mma_tf32_ta(tmem, ai[pa[pp]] + 8 * ks, smem_desc(bim[pb[pp]] + ks * 256), in, 1u);
+              }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              su32(mma_done + sb))
@@ -325,8 +344,8 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
         const int64_t s_end = min(a.ntiles_src, s_begin + BT_CHUNK_TILES);
         for (int64_t s = s_begin; s < s_end; ++s, ++g) {
           const int sa = g % BT_NA, sb = g % BT_NB;
-          unsigned char* st = smem + sa * BT_A_STAGE;
-          const float4* hdr = reinterpret_cast<const float4*>(smem + BT_B_OFF + sb * BT_IMG);
+          unsigned char* simg = smem + BT_B_OFF + sb * BT_SIMG;
+          const float4* hdr = reinterpret_cast<const float4*>(simg);
           if (!err) err = !mbar_wait(b_full + sb, (g / BT_NB) & 1);
           // the MMAs of tile g - NA read this A stage
           if (g >= BT_NA && !err) err = !mbar_wait(mma_done + (g - BT_NA) % BT_NB, ((g - BT_NA) / BT_NB) & 1);
@@ -350,12 +369,34 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
             pih[q] = tf32(cim[q]);
             pil[q] = tf32(cim[q] - pih[q]);
           }
-          const uint32_t o = bt_off(m, 4 * quad);
-          *reinterpret_cast<float4*>(st + 0 * BT_A_MAT + o) = rh;
-          *reinterpret_cast<float4*>(st + 1 * BT_A_MAT + o) = rl;
-          *reinterpret_cast<float4*>(st + 2 * BT_A_MAT + o) = ih;
-          *reinterpret_cast<float4*>(st + 3 * BT_A_MAT + o) = il;
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          {
+            // -Q_re (hi for threads 0-255, lo for 256-511), one 16-byte vector each
+            const int part_lo = tid >> 8;
+            const int v = tid & 255;
+            const float4* src = reinterpret_cast<const float4*>(simg + (part_lo ? BT_S_LO : BT_S_HI)) + v;
+            float4* dst = reinterpret_cast<float4*>(simg + (part_lo ? BT_S_LO : BT_S_HI) + 2 * BT_B_MAT) + v;
+            const float4 q = *src;
+            *dst = make_float4(-q.x, -q.y, -q.z, -q.w);
+          }
+          // A operands into tensor memory: this warp's 32 rows, columns 4 quad .. 4 quad + 3
+          {
+            const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + 128 + 64 * sa + 4 * quad;
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta + 0),
+                         "f"(rh.x), "f"(rh.y), "f"(rh.z), "f"(rh.w)
+                         : "memory");
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta + 16),
+                         "f"(rl.x), "f"(rl.y), "f"(rl.z), "f"(rl.w)
+                         : "memory");
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta + 32),
+                         "f"(ih.x), "f"(ih.y), "f"(ih.z), "f"(ih.w)
+                         : "memory");
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta + 48),
+                         "f"(il.x), "f"(il.y), "f"(il.z), "f"(il.w)
+                         : "memory");
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the -Q_re blocks
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncwarp();
           if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(a_full + sa)) : "memory");
         }
@@ -405,7 +446,7 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
 }
 
 __device__ __forceinline__ int64_t bt_block_of(const BatchArgs& a, int64_t k) {
@@ -491,8 +532,8 @@ __global__ void batch_images_kernel(const double4_32a* __restrict__ ps, const do
   unsigned char* bm = base + BT_HDR;
   const uint32_t o = bt_off(r, j);
   *reinterpret_cast<uint32_t*>(bm + 0 * BT_B_MAT + o) = hr;
-  *reinterpret_cast<uint32_t*>(bm + 1 * BT_B_MAT + o) = lr;
-  *reinterpret_cast<uint32_t*>(bm + 2 * BT_B_MAT + o) = hi;
+  *reinterpret_cast<uint32_t*>(bm + 1 * BT_B_MAT + o) = hi;
+  *reinterpret_cast<uint32_t*>(bm + 2 * BT_B_MAT + o) = lr;
   *reinterpret_cast<uint32_t*>(bm + 3 * BT_B_MAT + o) = li;
 }
 

@@ -77,6 +77,40 @@ __global__ void far_field_kernel(FarClass c0, FarClass c1, FarClass c2, const do
   }
 }
 
+// x_e = (1/4pi) sum_{j in e} sum_d e^{+ik xhat_d.y_j}(s_j + ik xhat_d.v_j) r_d  (F^H r);
+// one thread per element (its quadrature points are contiguous in its class).
+__global__ void far_field_adjoint_kernel(FarClass c, const int32_t* __restrict__ first,
+                                         const int32_t* __restrict__ elem, int64_t n_elem,
+                                         const double2* __restrict__ r, int ndir, int64_t n,
+                                         const double4_32a* __restrict__ dirs, double k, int nrhs,
+                                         double2* __restrict__ x) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_elem) return;
+  for (int q = 0; q < nrhs; ++q) {
+    const double2* rq = r + (int64_t)q * ndir;
+    double ar = 0.0, ai = 0.0;
+    for (int32_t j = first[e]; j < first[e + 1]; ++j) {
+      const double4_32a y = c.ps[j];
+      double vx = 0, vy = 0, vz = 0;
+      if (c.v) {
+        const double4_32a v = c.v[j];
+        vx = v.x; vy = v.y; vz = v.z;
+      }
+      for (int d = 0; d < ndir; ++d) {
+        const double4_32a u = dirs[d];
+        double sn, cs;
+        sincos(k * (u.x * y.x + u.y * y.y + u.z * y.z), &sn, &cs);
+        const double amr = y.w, ami = k * (u.x * vx + u.y * vy + u.z * vz);
+        const double tr = cs * amr - sn * ami, ti = cs * ami + sn * amr;
+        const double2 rr = rq[d];
+        ar += tr * rr.x - ti * rr.y;
+        ai += tr * rr.y + ti * rr.x;
+      }
+    }
+    x[(int64_t)q * n + elem[e]] = make_double2(ar / kFourPi, ai / kFourPi);
+  }
+}
+
 static vsie_status upload_dirs(const double* h_dirs, int ndir, double4_32a** d_dirs, cudaStream_t st) {
   std::vector<double4_32a> u(ndir);
   for (int d = 0; d < ndir; ++d) {
@@ -141,5 +175,32 @@ extern "C" vsie_status vsie_far_field(vsie_handle* h, const void* d_p, int32_t n
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(dirs);
   if (e != cudaSuccess) return cuda_fail(e, "far_field_kernel", __FILE__, __LINE__);
+  return VSIE_OK;
+}
+
+extern "C" vsie_status vsie_far_field_adjoint(vsie_handle* h, const void* d_r, int32_t nrhs, const double* h_dirs,
+                                              int32_t ndir, void* d_x, void* stream) {
+  clear_error();
+  if (!h || !d_r || !h_dirs || !d_x || ndir < 1 || nrhs < 1) {
+    set_error("vsie_far_field_adjoint: invalid argument");
+    return VSIE_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double4_32a* dirs;
+  VSIE_TRY(upload_dirs(h_dirs, ndir, &dirs, st));
+  const Sources* cls[3] = {&h->G, &h->K, &h->F};
+  cudaError_t e = cudaSuccess;
+  for (const Sources* S : cls) {
+    if (!S->n_elem) continue;
+    const FarClass c{S->pos_s, S == &h->G ? nullptr : S->vvec, S->owner, S->n};
+    far_field_adjoint_kernel<<<(unsigned)((S->n_elem + 127) / 128), 128, 0, st>>>(
+        c, S->elem_first, S->elem_list, S->n_elem, (const double2*)d_r, ndir, h->n, dirs, h->k0, nrhs,
+        (double2*)d_x);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) break;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dirs);
+  if (e != cudaSuccess) return cuda_fail(e, "far_field_adjoint_kernel", __FILE__, __LINE__);
   return VSIE_OK;
 }

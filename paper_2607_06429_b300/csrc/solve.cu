@@ -162,8 +162,16 @@ static vsie_status norm2(const double2* w, int64_t n, SolveWork& S, double* out,
 
 // One GMRES cycle for A d = r0 from d = 0 (d is ADDED to x).  Stops when the Arnoldi
 // residual estimate drops below target_abs or after max_it iterations.
-static vsie_status gmres_cycle(vsie_handle* h, int precision, const double2* r0, double r0norm,
-                               double2* x, double target_abs, int max_it, SolveWork& S,
+// y = A x (adjoint == false) or y = A^H x (adjoint == true)
+static vsie_status op_apply(vsie_handle* h, bool adjoint, const double2* x, double2* y, int precision,
+                            cudaStream_t st) {
+  if (!adjoint) return apply_one(h, x, y, precision, st);
+  VSIE_TRY(far_adjoint(h, x, y, precision, st));
+  return correction_adjoint(h, x, y, precision, st);
+}
+
+static vsie_status gmres_cycle(vsie_handle* h, bool adjoint, int precision, const double2* r0,
+                               double r0norm, double2* x, double target_abs, int max_it, SolveWork& S,
                                cudaStream_t st, int* iters, double* est, int* applies,
                                bool* breakdown) {
   const int64_t n = h->n;
@@ -178,7 +186,7 @@ static vsie_status gmres_cycle(vsie_handle* h, int precision, const double2* r0,
   std::vector<cplx> h1, h2;
   for (j = 0; j < m; ++j) {
     double2* vj = S.V + (size_t)j * n;
-    VSIE_TRY(apply_one(h, vj, S.w, precision, st));
+    VSIE_TRY(op_apply(h, adjoint, vj, S.w, precision, st));
     ++*applies;
     // CGS2
     // (multidot leaves the coefficients in S.hdev for the update kernel)
@@ -270,6 +278,7 @@ extern "C" vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
   const int64_t n = h->n;
   const double2* b = (const double2*)d_b;
   double2* x = (double2*)d_x;
+  const bool adjoint = opts->adjoint != 0;
   vsie_solve_info local{};
   vsie_solve_info& inf = info ? *info : local;
   inf = vsie_solve_info{};
@@ -323,7 +332,7 @@ extern "C" vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
       int it = 0, applies = 0;
       double est;
       bool brk;
-      VSIE_TRY(gmres_cycle(h, inner_prec, S.r, rnorm, x, cycle_target,
+      VSIE_TRY(gmres_cycle(h, adjoint, inner_prec, S.r, rnorm, x, cycle_target,
                            opts->max_iters - inf.iterations, S, st, &it, &est, &applies, &brk));
       inf.iterations += it;
       if (inner_prec == 32)
@@ -331,7 +340,7 @@ extern "C" vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
       else
         inf.fp64_applies += applies;
       // true residual with the FP64 apply
-      VSIE_TRY(apply_one(h, x, S.t, 64, st));
+      VSIE_TRY(op_apply(h, adjoint, x, S.t, 64, st));
       inf.fp64_applies += 1;
       sub_kernel<<<nb256(n), 256, 0, st>>>(b, S.t, S.r, n);
       VSIE_CUDA(cudaGetLastError());
