@@ -45,33 +45,34 @@
 namespace vsie {
 
 constexpr int BT_M = 128;             // targets per CTA tile
-constexpr int BT_S = 16;              // sources per tile (MMA K = 8: two k-steps)
+constexpr int BT_S = 32;              // sources per tile (MMA K = 8: four k-steps)
 constexpr int BT_R = 64;              // right-hand sides per launch
-constexpr int BT_CHUNK_TILES = 128;   // source tiles per work item (2048 sources)
-constexpr int BT_B_MAT = BT_R * BT_S * 4;        // 4 KB per B matrix
-constexpr int BT_HDR = BT_S * 32;                // 16 source records of 32 bytes
+constexpr int BT_CHUNK_TILES = 64;    // source tiles per work item (2048 sources)
+constexpr int BT_B_MAT = BT_R * BT_S * 4;        // 8 KB per B block (64 x 32 tf32)
+constexpr int BT_HDR = 6 * BT_S * 4;             // -x, -y, -z, nx, ny, nz of the 32 sources
 constexpr int BT_IMG = BT_HDR + 4 * BT_B_MAT;    // per-tile image in global memory
-constexpr int BT_NA = 2;                         // stages of evaluated A operands (64 TMEM columns each)
-constexpr int BT_NB = 8;                         // stages of charge images (prefetch distance 7)
+constexpr int BT_NA = 3;                         // stages of evaluated A operands (128 TMEM columns each)
+constexpr int BT_NB = 4;                         // stages of charge images (prefetch distance 3)
 // An image stage in shared memory holds [header][Q_re hi][Q_im hi][-Q_re hi][Q_re lo][Q_im lo]
 // [-Q_re lo]; the copy engine fills all but the two negated blocks, which the evaluating
 // warps write.  Stacking (Q_re; Q_im) and (Q_im; -Q_re) along N gives the two B operands
 // of the N = 128 products [Y_re | Y_im] += C_re (Q_re | Q_im) + C_im (-Q_im | Q_re).
-constexpr int BT_SIMG = BT_HDR + 6 * BT_B_MAT;   // 25,088 bytes
+constexpr int BT_SIMG = BT_HDR + 6 * BT_B_MAT;   // 49,920 bytes
 constexpr int BT_S_HI = BT_HDR;                  // Q_re hi (then Q_im hi, -Q_re hi)
 constexpr int BT_S_LO = BT_HDR + 3 * BT_B_MAT;   // Q_re lo (then Q_im lo, -Q_re lo)
 constexpr int BT_B_OFF = 0;
 constexpr int BT_BAR_OFF = BT_B_OFF + BT_NB * BT_SIMG;
 constexpr int BT_SMEM = BT_BAR_OFF + 8 * (BT_NA + 2 * BT_NB + 1) + 16;
+constexpr int BT_TMEM_COLS = 512;                // D: 0-127; A stage s: 128 + 128 s
 static_assert(BT_IMG % 16 == 0 && BT_SIMG % 16 == 0 && BT_BAR_OFF % 8 == 0, "alignment");
 static_assert(BT_SMEM <= 227 * 1024, "shared memory budget");
 constexpr uint32_t BT_WAIT_LIMIT = 1u << 22;
 
-// byte offset of element (row, k) in a K-major, no-swizzle operand with K = 16:
+// byte offset of element (row, k) in a K-major, no-swizzle operand with K = 32:
 // core matrices of 8 rows x 16 bytes; along K they are 128 bytes apart (leading byte
-// offset), along rows 512 bytes apart (stride byte offset).
+// offset), along rows 1024 bytes apart (stride byte offset).
 __host__ __device__ __forceinline__ uint32_t bt_off(int row, int k) {
-  return (uint32_t)((row >> 3) * 512 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+  return (uint32_t)((row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
 }
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -80,7 +81,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFFu);
   d |= (uint64_t)(128u >> 4) << 16;   // leading byte offset: next core matrix along K
-  d |= (uint64_t)(512u >> 4) << 32;   // stride byte offset: next 8-row group
+  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: next 8-row group
   d |= (uint64_t)1 << 46;             // descriptor version (sm_100 family)
   return d;                           // base offset 0, no swizzle
 }
@@ -130,9 +131,11 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
 
 // ----------------------------------------------------------------- tile evaluation
 
-// Per-source record in the image header (32 bytes): (x~, y~, z~, 0) (nx, ny, nz, 0).
+// Image header (structure of arrays over the tile's 32 sources): -x~, -y~, -z~ (kappa-
+// scaled positions, negated) and the unit normal n (K class; zero for G).
 // G class:  C~ = e^{2 pi i t} / |d~|
 // K class:  C~ = e^{2 pi i t} (2 pi i t - 1)(d~ . n) / |d~|^3
+// Two sources per packed FP32x2 instruction (the same target).
 struct EvalG {
   static constexpr bool kNormal = false;
 };
@@ -140,22 +143,41 @@ struct EvalK {
   static constexpr bool kNormal = true;
 };
 
+__device__ __forceinline__ float2 bf2(float a) { return make_float2(a, a); }
+
 template <class Ev>
-__device__ __forceinline__ float2 eval_pair(float tx, float ty, float tz, float4 s, float4 nrm) {
-  const float dx = tx - s.x, dy = ty - s.y, dz = tz - s.z;
-  const float r2 = dx * dx + dy * dy + dz * dz;
-  const float rinv = (r2 > 0.0f) ? rsqrtf(r2) : 0.0f;
-  const float t = r2 * rinv;
-  const float rt = __fsub_rn(__fadd_rn(t, 12582912.0f), 12582912.0f);
-  const float f = __fsub_rn(t, rt);
-  float sn, cs;
-  __sincosf(f * 6.28318530717958647692f, &sn, &cs);
-  if (!Ev::kNormal) return make_float2(cs * rinv, sn * rinv);
-  const float dn = dx * nrm.x + dy * nrm.y + dz * nrm.z;
-  const float g3 = rinv * rinv * rinv * dn;
-  const float kr = t * 6.28318530717958647692f;
+__device__ __forceinline__ void eval_pair2(float2 tx, float2 ty, float2 tz, float2 nsx, float2 nsy, float2 nsz,
+                                          float2 nx, float2 ny, float2 nz, float2& cre, float2& cim) {
+  const float2 dx = __fadd2_rn(tx, nsx), dy = __fadd2_rn(ty, nsy), dz = __fadd2_rn(tz, nsz);
+  float2 r2 = __fmul2_rn(dx, dx);
+  r2 = __ffma2_rn(dy, dy, r2);
+  r2 = __ffma2_rn(dz, dz, r2);
+  float2 rinv;
+  rinv.x = (r2.x > 0.0f) ? rsqrtf(r2.x) : 0.0f;
+  rinv.y = (r2.y > 0.0f) ? rsqrtf(r2.y) : 0.0f;
+  const float2 t = __fmul2_rn(r2, rinv);
+  const float2 u = __fadd2_rn(t, bf2(12582912.0f));
+  const float2 w = __fadd2_rn(u, bf2(-12582912.0f));
+  const float2 f = __ffma2_rn(w, bf2(-1.0f), t);
+  const float2 ang = __fmul2_rn(f, bf2(6.28318530717958647692f));
+  float2 cs, sn;
+  __sincosf(ang.x, &sn.x, &cs.x);
+  __sincosf(ang.y, &sn.y, &cs.y);
+  if (!Ev::kNormal) {
+    cre = __fmul2_rn(cs, rinv);
+    cim = __fmul2_rn(sn, rinv);
+    return;
+  }
+  float2 dn = __fmul2_rn(dx, nx);
+  dn = __ffma2_rn(dy, ny, dn);
+  dn = __ffma2_rn(dz, nz, dn);
+  const float2 g3 = __fmul2_rn(__fmul2_rn(__fmul2_rn(rinv, rinv), rinv), dn);
+  const float2 kr = __fmul2_rn(t, bf2(6.28318530717958647692f));
   // (cos + i sin)(i kr - 1) = -(cos + kr sin) + i (kr cos - sin)
-  return make_float2(-g3 * (cs + kr * sn), g3 * (kr * cs - sn));
+  const float2 A = __ffma2_rn(kr, sn, cs);
+  const float2 Q = __ffma2_rn(kr, cs, __fmul2_rn(sn, bf2(-1.0f)));
+  cre = __fmul2_rn(__fmul2_rn(g3, bf2(-1.0f)), A);
+  cim = __fmul2_rn(g3, Q);
 }
 
 struct BatchArgs {
@@ -205,19 +227,20 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(256));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                 "r"(BT_TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tslot;  // columns 0-127: accumulator; 128 + 64 s ...: A stage s
+  const uint32_t tmem = *tslot;  // columns 0-127: accumulator; 128 + 128 s ...: A stage s
   bool err = false;
   const int64_t b = blockIdx.x;
   const int64_t k0 = bt_begin(a, b), k1 = bt_begin(a, b + 1);
 
   if (warp == BT_EVAL_THREADS / 32) {
-    // ------------------------------------------------------------ producer warp
+    // ------------------------------------------------------------ issuing warp
     if (lane == 0) {
       // copy cursor (runs up to NS tiles ahead of the MMA cursor)
       int64_t pk = k0, ps = 0, pend = 0;
@@ -284,14 +307,14 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
             err = !mbar_wait(b_full + sb, (g / BT_NB) & 1) || !mbar_wait(a_full + sa, (g / BT_NA) & 1);
             if (err) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t acol = tmem + 128 + 64 * sa;  // C_re hi, C_re lo, C_im hi, C_im lo: 16 columns each
+            const uint32_t acol = tmem + 128 + 128 * sa;  // C_re hi, C_re lo, C_im hi, C_im lo: 32 columns each
             const uint32_t bbase = su32(smem + BT_B_OFF + sb * BT_SIMG);
             const bool fresh = (s == s_begin);
             constexpr uint32_t ip = bt_idesc(false), in = bt_idesc(true);
             // B windows: (Q_re; Q_im) and (Q_im; -Q_re) of the hi and lo parts, the second
             // negated by the descriptor.
-            const uint32_t ar[2] = {acol + 0, acol + 16};
-            const uint32_t ai[2] = {acol + 32, acol + 48};
+            const uint32_t ar[2] = {acol + 0, acol + 32};
+            const uint32_t ai[2] = {acol + 64, acol + 96};
             const uint32_t bre[2] = {bbase + BT_S_HI, bbase + BT_S_LO};
             const uint32_t bim[2] = {bbase + BT_S_HI + BT_B_MAT, bbase + BT_S_LO + BT_B_MAT};
             const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};  // hi hi, hi lo, lo hi
@@ -299,7 +322,7 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
 #pragma unroll
             for (int pp = 0; pp < 3; ++pp) {
 #pragma unroll
-              for (int ks = 0; ks < 2; ++ks) {
+              for (int ks = 0; ks < BT_S / 8; ++ks) {
                 mma_tf32_ta(tmem, ar[pa[pp]] + 8 * ks, smem_desc(bre[pb[pp]] + ks * 256), ip, acc_flag);
                 acc_flag = 1u;
                 mma_tf32_ta(tmem, ai[pa[pp]] + 8 * ks, smem_desc(bim[pb[pp]] + ks * 256), in, 1u);
@@ -319,7 +342,7 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
   } else {
     // ------------------------------------------------------------ evaluating warps
     const int m = tid & (BT_M - 1);   // evaluated target row
-    const int quad = tid >> 7;        // evaluated sources 4 quad .. 4 quad + 3
+    const int oct = tid >> 7;         // evaluated sources 8 oct .. 8 oct + 7
     const int lq = warp & 3;          // TMEM lane quarter this warp may read
     const int cb = warp >> 2;         // column block of 32 read by this warp
     uint32_t g = 0, nchunks = 0;
@@ -345,54 +368,77 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
         for (int64_t s = s_begin; s < s_end; ++s, ++g) {
           const int sa = g % BT_NA, sb = g % BT_NB;
           unsigned char* simg = smem + BT_B_OFF + sb * BT_SIMG;
-          const float4* hdr = reinterpret_cast<const float4*>(simg);
+          const float* hdr = reinterpret_cast<const float*>(simg);
           if (!err) err = !mbar_wait(b_full + sb, (g / BT_NB) & 1);
           // the MMAs of tile g - NA read this A stage
           if (g >= BT_NA && !err) err = !mbar_wait(mma_done + (g - BT_NA) % BT_NB, ((g - BT_NA) / BT_NB) & 1);
-          float cre[4], cim[4];
+          // C for (target m, sources 8 oct .. 8 oct + 7), two sources per packed instruction
+          float cre[8], cim[8];
+          {
+            const int j0 = 8 * oct;
+            const float4 xa = *reinterpret_cast<const float4*>(hdr + 0 * BT_S + j0);
+            const float4 xb = *reinterpret_cast<const float4*>(hdr + 0 * BT_S + j0 + 4);
+            const float4 ya = *reinterpret_cast<const float4*>(hdr + 1 * BT_S + j0);
+            const float4 yb = *reinterpret_cast<const float4*>(hdr + 1 * BT_S + j0 + 4);
+            const float4 za = *reinterpret_cast<const float4*>(hdr + 2 * BT_S + j0);
+            const float4 zb = *reinterpret_cast<const float4*>(hdr + 2 * BT_S + j0 + 4);
+            float4 nxa = make_float4(0, 0, 0, 0), nxb = nxa, nya = nxa, nyb = nxa, nza = nxa, nzb = nxa;
+            if (Ev::kNormal) {
+              nxa = *reinterpret_cast<const float4*>(hdr + 3 * BT_S + j0);
+              nxb = *reinterpret_cast<const float4*>(hdr + 3 * BT_S + j0 + 4);
+              nya = *reinterpret_cast<const float4*>(hdr + 4 * BT_S + j0);
+              nyb = *reinterpret_cast<const float4*>(hdr + 4 * BT_S + j0 + 4);
+              nza = *reinterpret_cast<const float4*>(hdr + 5 * BT_S + j0);
+              nzb = *reinterpret_cast<const float4*>(hdr + 5 * BT_S + j0 + 4);
+            }
+            const float2 tx = bf2(tp.x), ty = bf2(tp.y), tz = bf2(tp.z);
+            const float2 sx[4] = {{xa.x, xa.y}, {xa.z, xa.w}, {xb.x, xb.y}, {xb.z, xb.w}};
+            const float2 sy[4] = {{ya.x, ya.y}, {ya.z, ya.w}, {yb.x, yb.y}, {yb.z, yb.w}};
+            const float2 sz[4] = {{za.x, za.y}, {za.z, za.w}, {zb.x, zb.y}, {zb.z, zb.w}};
+            const float2 qx[4] = {{nxa.x, nxa.y}, {nxa.z, nxa.w}, {nxb.x, nxb.y}, {nxb.z, nxb.w}};
+            const float2 qy[4] = {{nya.x, nya.y}, {nya.z, nya.w}, {nyb.x, nyb.y}, {nyb.z, nyb.w}};
+            const float2 qz[4] = {{nza.x, nza.y}, {nza.z, nza.w}, {nzb.x, nzb.y}, {nzb.z, nzb.w}};
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int j = 4 * quad + q;
-            const float2 cv = eval_pair<Ev>(tp.x, tp.y, tp.z, hdr[2 * j], hdr[2 * j + 1]);
-            cre[q] = cv.x;
-            cim[q] = cv.y;
+            for (int pr = 0; pr < 4; ++pr) {
+              float2 cr2, ci2;
+              eval_pair2<Ev>(tx, ty, tz, sx[pr], sy[pr], sz[pr], qx[pr], qy[pr], qz[pr], cr2, ci2);
+              cre[2 * pr] = cr2.x;
+              cre[2 * pr + 1] = cr2.y;
+              cim[2 * pr] = ci2.x;
+              cim[2 * pr + 1] = ci2.y;
+            }
           }
-          float4 rh, rl, ih, il;
-          float* prh = &rh.x;
-          float* prl = &rl.x;
-          float* pih = &ih.x;
-          float* pil = &il.x;
+          uint32_t rh[8], rl[8], ih[8], il[8];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            prh[q] = tf32(cre[q]);
-            prl[q] = tf32(cre[q] - prh[q]);
-            pih[q] = tf32(cim[q]);
-            pil[q] = tf32(cim[q] - pih[q]);
+          for (int q = 0; q < 8; ++q) {
+            const float h1 = tf32(cre[q]), h2 = tf32(cim[q]);
+            rh[q] = __float_as_uint(h1);
+            rl[q] = __float_as_uint(tf32(cre[q] - h1));
+            ih[q] = __float_as_uint(h2);
+            il[q] = __float_as_uint(tf32(cim[q] - h2));
           }
           {
-            // -Q_re (hi for threads 0-255, lo for 256-511), one 16-byte vector each
+            // -Q_re (hi for threads 0-255, lo for 256-511), two 16-byte vectors each
             const int part_lo = tid >> 8;
-            const int v = tid & 255;
+            const int v = (tid & 255) * 2;
             const float4* src = reinterpret_cast<const float4*>(simg + (part_lo ? BT_S_LO : BT_S_HI)) + v;
             float4* dst = reinterpret_cast<float4*>(simg + (part_lo ? BT_S_LO : BT_S_HI) + 2 * BT_B_MAT) + v;
-            const float4 q = *src;
-            *dst = make_float4(-q.x, -q.y, -q.z, -q.w);
+            const float4 q0 = src[0], q1 = src[1];
+            dst[0] = make_float4(-q0.x, -q0.y, -q0.z, -q0.w);
+            dst[1] = make_float4(-q1.x, -q1.y, -q1.z, -q1.w);
           }
-          // A operands into tensor memory: this warp's 32 rows, columns 4 quad .. 4 quad + 3
+          // A operands into tensor memory: this warp's 32 rows, columns 8 oct .. 8 oct + 7
           {
-            const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + 128 + 64 * sa + 4 * quad;
-            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta + 0),
-                         "f"(rh.x), "f"(rh.y), "f"(rh.z), "f"(rh.w)
-                         : "memory");
-            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta + 16),
-                         "f"(rl.x), "f"(rl.y), "f"(rl.z), "f"(rl.w)
-                         : "memory");
-            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta + 32),
-                         "f"(ih.x), "f"(ih.y), "f"(ih.z), "f"(ih.w)
-                         : "memory");
-            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta + 48),
-                         "f"(il.x), "f"(il.y), "f"(il.z), "f"(il.w)
-                         : "memory");
+            const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + 128 + 128 * sa + 8 * oct;
+#define BT_ST8(off, v)                                                                                   \
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(ta + (off)), \
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])           \
+               : "memory")
+            BT_ST8(0, rh);
+            BT_ST8(32, rl);
+            BT_ST8(64, ih);
+            BT_ST8(96, il);
+#undef BT_ST8
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the -Q_re blocks
@@ -446,7 +492,8 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BT_TMEM_COLS));
 }
 
 __device__ __forceinline__ int64_t bt_block_of(const BatchArgs& a, int64_t k) {
@@ -514,13 +561,19 @@ __global__ void batch_images_kernel(const double4_32a* __restrict__ ps, const do
     }
   }
   if (r == 0) {
-    float4* h = reinterpret_cast<float4*>(base) + 2 * j;
-    h[0] = make_float4((float)(kap * y.x), (float)(kap * y.y), (float)(kap * y.z), 0.0f);
+    float* hd = reinterpret_cast<float*>(base);
+    hd[0 * BT_S + j] = -(float)(kap * y.x);
+    hd[1 * BT_S + j] = -(float)(kap * y.y);
+    hd[2 * BT_S + j] = -(float)(kap * y.z);
     if (is_k && valid) {
       const double4_32a nn = aux[js];
-      h[1] = make_float4((float)nn.x, (float)nn.y, (float)nn.z, 0.0f);
+      hd[3 * BT_S + j] = (float)nn.x;
+      hd[4 * BT_S + j] = (float)nn.y;
+      hd[5 * BT_S + j] = (float)nn.z;
     } else {
-      h[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      hd[3 * BT_S + j] = 0.0f;
+      hd[4 * BT_S + j] = 0.0f;
+      hd[5 * BT_S + j] = 0.0f;
     }
   }
   const float fr = (float)qr, fi = (float)qi;

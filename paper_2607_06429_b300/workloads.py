@@ -354,6 +354,7 @@ def fibonacci_dirs(m: int) -> np.ndarray:
 
 CONFIGS = {
     "ball12_k2": lambda: single_ball(12, 3, 2.0),
+    "nested24_k10": lambda: nested_k10(24, 4, 10.0),
     "nested80_k10": lambda: nested_k10(80, 6, 10.0),
     "perturbed40_k6": lambda: nested_perturbed(40, 5, 6.0),
     "nested128_k25": lambda: nested_k25(128, 7, 25.0),
