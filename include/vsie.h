@@ -87,6 +87,10 @@ typedef struct {
                                use the singularity-subtracted rule (exact Laplace
                                solid angle + three-point Helmholtz remainder); 0 = off */
   int32_t tile_override;    /* 0 = library default launch shape                       */
+  int32_t debug_flags;      /* 0 in normal use.  Bit 0 (failure-path testing): the
+                               tensor-core kernel of vsie_apply_batched never starts its
+                               bulk copies, so its bounded waits expire and the call
+                               returns VSIE_ERR_CUDA without faulting the device      */
 } vsie_options;
 
 /* Build the discrete operator on the current CUDA device: element geometry, material

@@ -51,7 +51,8 @@ class _Material(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("tet_far_points", ctypes.c_int32), ("near_radius", ctypes.c_double),
-                ("tri_near_radius", ctypes.c_double), ("tile_override", ctypes.c_int32)]
+                ("tri_near_radius", ctypes.c_double), ("tile_override", ctypes.c_int32),
+                ("debug_flags", ctypes.c_int32)]
 
 
 class _SolveOpts(ctypes.Structure):
@@ -152,7 +153,7 @@ class Operator:
 
     def __init__(self, vert, tet, tri, rho, c, tri_rho_in, tri_rho_out, k0, rho0=1.0, c0=1.0,
                  grad_alpha=None, tet_far_points=1, near_radius=0.0, tri_near_radius=0.0,
-                 tile_override=0):
+                 tile_override=0, debug_flags=0):
         lib = load_library()
         self._keep = dict(vert=_f64(vert).reshape(-1), tet=_i32(tet).reshape(-1),
                           tri=_i32(tri).reshape(-1), rho=_f64(rho), c=_f64(c),
@@ -164,7 +165,7 @@ class Operator:
         mat = _Material(float(rho0), float(c0), _ptr(k["rho"]), _ptr(k["c"]), _ptr(k["ga"]),
                         _ptr(k["rin"]), _ptr(k["rout"]))
         opt = _Options(int(tet_far_points), float(near_radius), float(tri_near_radius),
-                       int(tile_override))
+                       int(tile_override), int(debug_flags))
         h = ctypes.c_void_p()
         _check(lib.vsie_create(ctypes.byref(mesh), ctypes.byref(mat), float(k0),
                                ctypes.byref(opt), ctypes.byref(h)))

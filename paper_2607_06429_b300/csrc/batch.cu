@@ -32,8 +32,9 @@
 // (covering the HBM latency of the 16.5 KB image copies) while the CUDA cores evaluate the
 // next tile.  Keeping A out of shared memory leaves its bandwidth to the B operand reads.  Work is split over the CTAs with
 // the same balanced item ranges (target tile, 2048-source chunk) and deterministic fix-up
-// as the single-RHS sums.  Every wait on an mbarrier is bounded; on expiry the kernel
-// records an error code, stops issuing work and still releases its tensor memory.
+// as the single-RHS sums.  Every wait on an mbarrier is bounded (2 s of wall time); on
+// expiry the kernel records an error code, stops issuing work and still releases its
+// tensor memory.
 
 #include <cuda_runtime.h>
 
@@ -66,7 +67,6 @@ constexpr int BT_SMEM = BT_BAR_OFF + 8 * (BT_NA + 2 * BT_NB + 1) + 16;
 constexpr int BT_TMEM_COLS = 512;                // D: 0-127; A stage s: 128 + 128 s
 static_assert(BT_IMG % 16 == 0 && BT_SIMG % 16 == 0 && BT_BAR_OFF % 8 == 0, "alignment");
 static_assert(BT_SMEM <= 227 * 1024, "shared memory budget");
-constexpr uint32_t BT_WAIT_LIMIT = 1u << 22;
 
 // byte offset of element (row, k) in a K-major, no-swizzle operand with K = 32:
 // core matrices of 8 rows x 16 bytes; along K they are 128 bytes apart (leading byte
@@ -98,8 +98,19 @@ __device__ __forceinline__ float tf32(float x) {
   return __uint_as_float(r);
 }
 
+// Bounded wait: polls the mbarrier phase and gives up after BT_WAIT_NS of wall time
+// (read from the global nanosecond timer every 256 polls).
+constexpr uint64_t BT_WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < BT_WAIT_LIMIT; ++it) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -107,8 +118,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(su32(bar)), "r"(parity)
         : "memory");
     if (ok) return true;
+    if ((it & 255) == 0) {
+      const uint64_t t = global_ns();
+      if (it == 0) t0 = t;
+      else if (t - t0 > BT_WAIT_NS) return false;
+    }
   }
-  return false;
 }
 
 // A operand in tensor memory (row i of A in lane i, one 32-bit column per k)
@@ -195,6 +210,7 @@ struct BatchArgs {
   int mode;                 // 0 store, 1 add
   double* slots;            // [2 grid][2][BT_R][BT_M] FP64 accumulators / partial tiles
   int* status;              // nonzero on a timed-out wait
+  int withhold_copies;      // failure-path test: the issuing warp never starts the copies
 };
 
 __device__ __forceinline__ int64_t bt_begin(const BatchArgs& a, int64_t b) { return (b * a.nitems) / a.grid; }
@@ -274,6 +290,10 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
           if (err) break;
           unsigned char* bimg = smem + BT_B_OFF + st2 * BT_SIMG;
           const unsigned char* gimg = a.img + s_next * (int64_t)BT_IMG;
+          if (a.withhold_copies) {
+            ++gp;
+            continue;
+          }
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b_full + st2)),
                        "r"(BT_IMG)
                        : "memory");
@@ -634,6 +654,7 @@ static vsie_status batch_class(vsie_handle* h, const Sources& S, bool is_k, cons
     VSIE_CUDA(cudaMemsetAsync(h->batch.status, 0, sizeof(int), st));
   }
   a.status = h->batch.status;
+  a.withhold_copies = (h->debug_flags & 1) ? 1 : 0;
   if (is_k) {
     VSIE_CUDA(cudaFuncSetAttribute(batch_tc_kernel<EvalK>, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
     batch_tc_kernel<EvalK><<<(unsigned)a.grid, BT_ALL_THREADS, BT_SMEM, st>>>(a);
@@ -674,7 +695,7 @@ vsie_status batch_status(vsie_handle* h, cudaStream_t st) {
   VSIE_CUDA(cudaStreamSynchronize(st));
   if (flag) {
     cudaMemsetAsync(h->batch.status, 0, sizeof(int), st);
-    set_error("batched tensor-core far-field sum: an mbarrier wait exceeded its iteration limit");
+    set_error("batched tensor-core far-field sum: a bounded mbarrier wait expired");
     return VSIE_ERR_CUDA;
   }
   return VSIE_OK;

@@ -123,6 +123,7 @@ static vsie_status create_impl(const vsie_mesh* mesh, const vsie_material* mat, 
   h->near_radius = opt ? opt->near_radius : 0.0;
   h->tri_near_radius = opt ? opt->tri_near_radius : 0.0;
   h->tile_override = opt ? opt->tile_override : 0;
+  h->debug_flags = opt ? opt->debug_flags : 0;
   if (h->far_points != 1 && h->far_points != 4) {
     set_error("vsie_create: tet_far_points must be 1 or 4");
     return VSIE_ERR_ARG;

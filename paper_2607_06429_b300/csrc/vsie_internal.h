@@ -100,6 +100,7 @@ struct vsie_handle {
   int far_points = 1;
   double near_radius = 0, tri_near_radius = 0;
   int tile_override = 0;
+  int debug_flags = 0;
 
   double4_32a* tgt64 = nullptr;   // (x, y, z, 0) collocation points, FP64
   float4* tgt32 = nullptr;    // FP32 copies of kappa * x (kappa = k0/(2 pi))

@@ -55,3 +55,24 @@ def test_batched_matches_per_column_apply_mid_size():
         assert e <= TOL, (r, e)
     # the same call twice gives identical results (deterministic reduction order)
     assert torch.equal(op.apply_batched(X), Y)
+
+
+def test_expired_wait_reports_error_and_context_survives():
+    """Failure path without a fault: the issuing warp withholds its bulk copies, every
+    bounded mbarrier wait expires (2 s), the call returns VSIE_ERR_CUDA, and the device
+    context keeps working for the next operator."""
+    torch, B = _setup()
+    import time
+    w = W.single_ball(6, 1, 2.0)
+    op = B.Operator.from_workload(w, debug_flags=1)
+    X = torch.from_numpy(_block(op.n, 2, 1)).cuda()
+    t0 = time.time()
+    with pytest.raises(B.VsieError) as e:
+        op.apply_batched(X)
+    assert e.value.status == 3 and "wait expired" in str(e.value)
+    assert time.time() - t0 < 60
+    op.close()
+    good = B.Operator.from_workload(w)
+    Y = good.apply_batched(X)
+    Yc = good.apply(X, precision=32)
+    assert float(torch.linalg.norm(Y - Yc) / torch.linalg.norm(Yc)) <= TOL
