@@ -7,34 +7,38 @@
 // columns on the tensor cores, so the sine/cosine/rsqrt work is amortised R-fold.
 //
 // Precision: the contraction runs as three TF32 products with FP32 accumulation
-// (C_hi Q_hi + C_hi Q_lo + C_lo Q_hi, where x_hi = tf32(x), x_lo = tf32(x - x_hi)),
-// about 21 significant bits per product.  The FP32 tensor accumulator is folded into
-// FP64 every 2048 sources.  Complex arithmetic as two real products of width N = 128,
+// (C_lo Q_hi + C_hi Q_lo + C_hi Q_hi, where x_hi = tf32(x), x_lo = tf32(x - x_hi)),
+// about 21 significant bits per product.  The tensor accumulator's rounding error grows
+// with the number of MMAs summed into it, so it holds one source tile only: after each
+// tile the evaluating warps fold it into a running FP32 sum H in tensor memory with a
+// compensated (Kahan) step and leave the step's rounding error in the accumulator, where
+// the next tile's MMAs add onto it.  A target tile leaves the CTA as H plus the pending
+// compensation, in FP64.  Complex arithmetic as two real products of width N = 128,
 //     [Y_re | Y_im] += C_re [Q_re | Q_im] + C_im [-Q_im | Q_re],
 // the second with the instruction descriptor's negate-B bit applied to [Q_im | -Q_re].
 //
 // Layout.  One CTA (16 evaluating warps + 1 issuing warp, one CTA per SM) owns a tile of
-// 128 targets (the MMA M) and streams the sources in tiles of 16 (the MMA K is 8, two
+// 128 targets (the MMA M) and streams the sources in tiles of 32 (the MMA K is 8, four
 // k-steps per tile).
-//   * A operands (128 x 16 each): C_re and C_im, hi and lo, written straight into tensor
-//     memory by the evaluating warps (tcgen05.st), two stages of 64 columns;
-//   * B operands (64 x 16 per block, K-major, no swizzle, 8 x 16-byte core matrices):
-//     Q_re, Q_im, hi and lo, prepared per apply in global
-//     memory as the shared-memory image of each source tile, preceded by the tile's 16
-//     source records, and fetched with two bulk asynchronous copies (TMA engine) that
-//     complete on an mbarrier; the evaluating warps add the negated -Q_re blocks, so that
-//     each product is one N = 128 MMA over [Y_re | Y_im];
-//   * the accumulator D (128 lanes x 128 FP32 columns: Y_re | Y_im) lives in tensor
-//     memory, allocated by warp 0; every 2048 sources it is added into an FP64
-//     accumulator that each CTA keeps in its own slot of global memory (L2-resident).
-// Pipeline: two stages of evaluated operands (in tensor memory) and eight of charge images
-// (in shared memory), so the copy engine runs up to seven tiles ahead of the tensor cores
-// (covering the HBM latency of the 16.5 KB image copies) while the CUDA cores evaluate the
-// next tile.  Keeping A out of shared memory leaves its bandwidth to the B operand reads.  Work is split over the CTAs with
-// the same balanced item ranges (target tile, 2048-source chunk) and deterministic fix-up
-// as the single-RHS sums.  Every wait on an mbarrier is bounded (2 s of wall time); on
-// expiry the kernel records an error code, stops issuing work and still releases its
-// tensor memory.
+//   * A operand (128 x 32 each): C_re and C_im, hi and lo, written straight into tensor
+//     memory by the evaluating warps (tcgen05.st) once the previous tile's MMAs retired;
+//   * B operands (64 x 32 per block, K-major, no swizzle, 8 x 16-byte core matrices):
+//     Q_re, Q_im, hi and lo, prepared per apply in global memory as the shared-memory
+//     image of each source tile, preceded by the tile's 32 source records, and fetched
+//     with two bulk asynchronous copies (TMA engine) that complete on an mbarrier; the
+//     evaluating warps add the negated -Q_re blocks, so that each product is one N = 128
+//     MMA over [Y_re | Y_im];
+//   * two accumulator buffers D0, D1 (128 lanes x 128 FP32 columns: Y_re | Y_im) used by
+//     alternate tiles, so the fold of one overlaps the MMAs of the next, and the running
+//     sum H: all 512 tensor-memory columns, allocated by warp 0.
+// Pipeline: four stages of charge images in shared memory (the copy engine runs up to
+// three tiles ahead of the tensor cores) while the CUDA cores evaluate the next tile.
+// Keeping A out of shared memory leaves its bandwidth to the B operand reads.  Work is
+// split over the CTAs with the same balanced item ranges (target tile, 2048-source chunk)
+// and deterministic fix-up as the single-RHS sums.  Every wait on an mbarrier is bounded
+// (2 s of wall time); on expiry the kernel records an error code, stops issuing work,
+// waits (bounded again) for its copies and MMAs in flight and still releases its tensor
+// memory.
 
 #include <cuda_runtime.h>
 
@@ -52,7 +56,6 @@ constexpr int BT_CHUNK_TILES = 64;    // source tiles per work item (2048 source
 constexpr int BT_B_MAT = BT_R * BT_S * 4;        // 8 KB per B block (64 x 32 tf32)
 constexpr int BT_HDR = 6 * BT_S * 4;             // -x, -y, -z, nx, ny, nz of the 32 sources
 constexpr int BT_IMG = BT_HDR + 4 * BT_B_MAT;    // per-tile image in global memory
-constexpr int BT_NA = 3;                         // stages of evaluated A operands (128 TMEM columns each)
 constexpr int BT_NB = 4;                         // stages of charge images (prefetch distance 3)
 // An image stage in shared memory holds [header][Q_re hi][Q_im hi][-Q_re hi][Q_re lo][Q_im lo]
 // [-Q_re lo]; the copy engine fills all but the two negated blocks, which the evaluating
@@ -63,8 +66,12 @@ constexpr int BT_S_HI = BT_HDR;                  // Q_re hi (then Q_im hi, -Q_re
 constexpr int BT_S_LO = BT_HDR + 3 * BT_B_MAT;   // Q_re lo (then Q_im lo, -Q_re lo)
 constexpr int BT_B_OFF = 0;
 constexpr int BT_BAR_OFF = BT_B_OFF + BT_NB * BT_SIMG;
-constexpr int BT_SMEM = BT_BAR_OFF + 8 * (BT_NA + 2 * BT_NB + 1) + 16;
-constexpr int BT_TMEM_COLS = 512;                // D: 0-127; A stage s: 128 + 128 s
+constexpr int BT_NBARS = 1 + 2 * BT_NB + 2;      // a_full, b_full[NB], mma_done[NB], d_ready[2]
+constexpr int BT_SMEM = BT_BAR_OFF + 8 * BT_NBARS + 16;
+// tensor memory columns: accumulator buffers D0, D1 (Y_re | Y_im, 128 each), the running sum
+// H (same layout) and the A operand of the current tile (C_re hi, C_re lo, C_im hi, C_im lo)
+constexpr int BT_TMEM_COLS = 512;
+constexpr uint32_t BT_COL_D = 0, BT_COL_H = 256, BT_COL_A = 384;
 static_assert(BT_IMG % 16 == 0 && BT_SIMG % 16 == 0 && BT_BAR_OFF % 8 == 0, "alignment");
 static_assert(BT_SMEM <= 227 * 1024, "shared memory budget");
 
@@ -208,7 +215,7 @@ struct BatchArgs {
   int64_t ld_out;           // n
   int nrhs_out;             // columns written (<= BT_R)
   int mode;                 // 0 store, 1 add
-  double* slots;            // [2 grid][2][BT_R][BT_M] FP64 accumulators / partial tiles
+  double* slots;            // [2 grid][2][BT_R][BT_M] FP64 partial target tiles for the fix-up
   int* status;              // nonzero on a timed-out wait
   int withhold_copies;      // failure-path test: the issuing warp never starts the copies
 };
@@ -217,29 +224,39 @@ __device__ __forceinline__ int64_t bt_begin(const BatchArgs& a, int64_t b) { ret
 
 // Warp roles: warps 0-15 (512 threads) evaluate the kernel tile and fold the tensor
 // accumulator; warp 16 issues the bulk copies and, from one lane, the MMAs.  They meet
-// only through mbarriers (a_full per A stage; b_full, mma_done per image stage; d_free per chunk), so
-// evaluation, copies and tensor-core work overlap across the three stages.
+// only through mbarriers (a_full for the A operand; b_full, mma_done per image stage;
+// d_ready per accumulator buffer), so evaluation, copies and tensor-core work overlap.
 constexpr int BT_EVAL_THREADS = 512;
 constexpr int BT_ALL_THREADS = BT_EVAL_THREADS + 32;
+
+#define BT_LD8(addr, v)                                                                               \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"                  \
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]) \
+               : "r"(addr)                                                                            \
+               : "memory")
+#define BT_ST8(addr, v)                                                                               \
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(addr),       \
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])         \
+               : "memory")
 
 template <class Ev>
 __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + BT_BAR_OFF);
-  uint64_t* a_full = bars;                      // [NA] evaluated A operands written (16 warp arrivals)
-  uint64_t* b_full = bars + BT_NA;              // [NB] charge image landed (tx bytes)
-  uint64_t* mma_done = bars + BT_NA + BT_NB;    // [NB] MMAs of tile g retired (index g % NB)
-  uint64_t* d_free = bars + BT_NA + 2 * BT_NB;  // accumulator read by the folding warps (16 arrivals)
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + BT_NA + 2 * BT_NB + 1);
+  uint64_t* a_full = bars;                      // A operand of the current tile written (16 warp arrivals)
+  uint64_t* b_full = bars + 1;                  // [NB] charge image landed (tx bytes)
+  uint64_t* mma_done = bars + 1 + BT_NB;        // [NB] MMAs of tile g retired (index g % NB)
+  uint64_t* d_ready = bars + 1 + 2 * BT_NB;     // [2] accumulator buffer of tile g folded (index g % 2)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + BT_NBARS);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int i = 0; i < BT_NA; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(a_full + i)), "r"(16));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(a_full)), "r"(16));
     for (int i = 0; i < BT_NB; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b_full + i)), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(mma_done + i)), "r"(1));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(d_free)), "r"(16));
+    for (int i = 0; i < 2; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(d_ready + i)), "r"(16));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -250,17 +267,19 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tslot;  // columns 0-127: accumulator; 128 + 128 s ...: A stage s
+  const uint32_t tmem = *tslot;
   bool err = false;
   const int64_t b = blockIdx.x;
   const int64_t k0 = bt_begin(a, b), k1 = bt_begin(a, b + 1);
 
+  // The CTA's items [k0, k1) form segments: runs of consecutive chunks of one target tile.
+  // Both roles walk the same sequence of source tiles; g counts them over the whole range.
   if (warp == BT_EVAL_THREADS / 32) {
     // ------------------------------------------------------------ issuing warp
     if (lane == 0) {
-      // copy cursor (runs up to NS tiles ahead of the MMA cursor)
+      // copy cursor (runs up to NB - 1 tiles ahead of the MMA cursor)
       int64_t pk = k0, ps = 0, pend = 0;
-      bool pstarted = false;
+      bool pstarted = false, pdone = false;
       auto pnext = [&]() -> int64_t {
         if (!pstarted) {
           pstarted = true;
@@ -279,10 +298,10 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
       uint32_t gp = 0;  // copies issued
       auto refill = [&](uint32_t g_limit) {
         // issue copies for tiles gp < g_limit; image stage gp % NB was last read by tile gp - NB
-        while (gp < g_limit && !err) {
+        while (!pdone && gp < g_limit && !err) {
           const int64_t s_next = pnext();
           if (s_next < 0) {
-            gp = 0xFFFFFFFFu;  // no more tiles
+            pdone = true;
             break;
           }
           const int st2 = gp % BT_NB;
@@ -290,10 +309,8 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
           if (err) break;
           unsigned char* bimg = smem + BT_B_OFF + st2 * BT_SIMG;
           const unsigned char* gimg = a.img + s_next * (int64_t)BT_IMG;
-          if (a.withhold_copies) {
-            ++gp;
-            continue;
-          }
+          ++gp;
+          if (a.withhold_copies) continue;
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b_full + st2)),
                        "r"(BT_IMG)
                        : "memory");
@@ -308,202 +325,251 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
                   su32(bimg + BT_S_LO)),
               "l"(gimg + BT_HDR + 2 * BT_B_MAT), "r"(2 * BT_B_MAT), "r"(su32(b_full + st2))
               : "memory");
-          ++gp;
         }
       };
       refill(BT_NB - 1);
-      uint32_t g = 0, nchunks = 0;
+      uint32_t g = 0;
       for (int64_t k = k0; k < k1 && !err;) {
         const int64_t tile = k / a.nchunk;
         const int64_t c0 = k - tile * a.nchunk;
         const int64_t c1 = min(a.nchunk, c0 + (k1 - k));
-        for (int64_t c = c0; c < c1 && !err; ++c) {
-          const int64_t s_begin = c * BT_CHUNK_TILES;
-          const int64_t s_end = min(a.ntiles_src, s_begin + BT_CHUNK_TILES);
-          // the previous chunk's accumulator must have been read before it is overwritten
-          if (nchunks > 0) err = !mbar_wait(d_free, (nchunks - 1) & 1);
-          for (int64_t s = s_begin; s < s_end && !err; ++s, ++g) {
-            const int sa = g % BT_NA, sb = g % BT_NB;
-            err = !mbar_wait(b_full + sb, (g / BT_NB) & 1) || !mbar_wait(a_full + sa, (g / BT_NA) & 1);
-            if (err) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t acol = tmem + 128 + 128 * sa;  // C_re hi, C_re lo, C_im hi, C_im lo: 32 columns each
-            const uint32_t bbase = su32(smem + BT_B_OFF + sb * BT_SIMG);
-            const bool fresh = (s == s_begin);
-            constexpr uint32_t ip = bt_idesc(false), in = bt_idesc(true);
-            // B windows: (Q_re; Q_im) and (Q_im; -Q_re) of the hi and lo parts, the second
-            // negated by the descriptor.
-            const uint32_t ar[2] = {acol + 0, acol + 32};
-            const uint32_t ai[2] = {acol + 64, acol + 96};
-            const uint32_t bre[2] = {bbase + BT_S_HI, bbase + BT_S_LO};
-            const uint32_t bim[2] = {bbase + BT_S_HI + BT_B_MAT, bbase + BT_S_LO + BT_B_MAT};
-            const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};  // hi hi, hi lo, lo hi
-            uint32_t acc_flag = fresh ? 0u : 1u;
+        const int64_t s_begin = c0 * BT_CHUNK_TILES, s_end = min(a.ntiles_src, c1 * BT_CHUNK_TILES);
+        for (int64_t s = s_begin; s < s_end && !err; ++s, ++g) {
+          const int sb = g % BT_NB;
+          err = !mbar_wait(b_full + sb, (g / BT_NB) & 1) || !mbar_wait(a_full, g & 1);
+          // accumulator buffer g % 2 was last used by tile g - 2, whose fold must have read it
+          if (!err && g >= 2) err = !mbar_wait(d_ready + (g & 1), ((g - 2) >> 1) & 1);
+          if (err) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t dcol = tmem + BT_COL_D + 128 * (g & 1);
+          const uint32_t acol = tmem + BT_COL_A;  // C_re hi, C_re lo, C_im hi, C_im lo: 32 columns each
+          const uint32_t bbase = su32(smem + BT_B_OFF + sb * BT_SIMG);
+          constexpr uint32_t ip = bt_idesc(false), in = bt_idesc(true);
+          // B windows: (Q_re; Q_im) and (Q_im; -Q_re) of the hi and lo parts, the second
+          // negated by the descriptor.
+          const uint32_t ar[2] = {acol + 0, acol + 32};
+          const uint32_t ai[2] = {acol + 64, acol + 96};
+          const uint32_t bre[2] = {bbase + BT_S_HI, bbase + BT_S_LO};
+          const uint32_t bim[2] = {bbase + BT_S_HI + BT_B_MAT, bbase + BT_S_LO + BT_B_MAT};
+          // the small cross terms first (lo hi, hi lo), while the accumulator is small, then hi hi
+          const int pa[3] = {1, 0, 0}, pb[3] = {0, 1, 0};
+          // the first two tiles of a segment start their buffer afresh; later tiles accumulate
+          // onto the compensation term that the fold of tile g - 2 left in it
+          uint32_t acc_flag = (s - s_begin < 2) ? 0u : 1u;
 #pragma unroll
-            for (int pp = 0; pp < 3; ++pp) {
+          for (int pp = 0; pp < 3; ++pp) {
 #pragma unroll
-              for (int ks = 0; ks < BT_S / 8; ++ks) {
-                mma_tf32_ta(tmem, ar[pa[pp]] + 8 * ks, smem_desc(bre[pb[pp]] + ks * 256), ip, acc_flag);
-                acc_flag = 1u;
-                mma_tf32_ta(tmem, ai[pa[pp]] + 8 * ks, smem_desc(bim[pb[pp]] + ks * 256), in, 1u);
-              }
+            for (int ks = 0; ks < BT_S / 8; ++ks) {
+              mma_tf32_ta(dcol, ar[pa[pp]] + 8 * ks, smem_desc(bre[pb[pp]] + ks * 256), ip, acc_flag);
+              acc_flag = 1u;
+              mma_tf32_ta(dcol, ai[pa[pp]] + 8 * ks, smem_desc(bim[pb[pp]] + ks * 256), in, 1u);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             su32(mma_done + sb))
-                         : "memory");
-            if (gp != 0xFFFFFFFFu) refill(g + BT_NB);
           }
-          ++nchunks;
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           su32(mma_done + sb))
+                       : "memory");
+          refill(g + BT_NB);
         }
         k = tile * a.nchunk + c1;
       }
-      if (err) atomicExch(a.status, 1);
+      // before the CTA exits (and its shared and tensor memory go away): copies still in
+      // flight and the last MMAs must have landed (only the error path leaves any)
+      const bool err_wait = err;
+      if (!a.withhold_copies)
+        for (uint32_t t = g; t < gp; ++t)
+          if (!mbar_wait(b_full + t % BT_NB, (t / BT_NB) & 1)) err = true;
+      if (g > 0 && !mbar_wait(mma_done + (g - 1) % BT_NB, ((g - 1) / BT_NB) & 1)) err = true;
+      if (err || err_wait) atomicExch(a.status, 1);
     }
   } else {
     // ------------------------------------------------------------ evaluating warps
     const int m = tid & (BT_M - 1);   // evaluated target row
     const int oct = tid >> 7;         // evaluated sources 8 oct .. 8 oct + 7
-    const int lq = warp & 3;          // TMEM lane quarter this warp may read
-    const int cb = warp >> 2;         // column block of 32 read by this warp
-    uint32_t g = 0, nchunks = 0;
-    int64_t k = k0;
-    while (k < k1) {
+    const int lq = warp & 3;          // TMEM lane quarter this warp may access
+    const int cb = warp >> 2;         // accumulator column block of 32 folded by this warp
+    const int row = lq * 32 + lane;   // accumulator row (target) of this thread
+    const int part = cb >> 1;         // 0: real, 1: imaginary
+    const int r0 = (cb & 1) * 32;     // first right-hand side of the column block
+    const uint32_t tlane = tmem + ((uint32_t)(lq * 32) << 16);
+    uint32_t g = 0;
+    // Compensated fold of tile gg's accumulator (buffer gg % 2) into the running sum H:
+    //   t = H + d,  e = d - (t - H),  H <- t,  buffer <- e
+    // so that the next tile accumulating into the buffer carries the rounding error e of
+    // this step (Kahan summation, the compensation kept in the tensor accumulator).  After
+    // a segment's last fold its sum is H plus the compensations pending in both buffers.
+    auto fold = [&](uint32_t gg, bool first) {
+      const uint32_t dcol = tlane + BT_COL_D + 128 * (gg & 1) + 32 * cb;
+      const uint32_t hcol = tlane + BT_COL_H + 32 * cb;
+#pragma unroll
+      for (int piece = 0; piece < 2; ++piece) {
+        uint32_t d[16], h[16];
+        BT_LD8(dcol + 16 * piece, d);
+        BT_LD8(dcol + 16 * piece + 8, (d + 8));
+        if (!first) {
+          BT_LD8(hcol + 16 * piece, h);
+          BT_LD8(hcol + 16 * piece + 8, (h + 8));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < 16; q += 2) {
+          const float2 dv = make_float2(__uint_as_float(d[q]), __uint_as_float(d[q + 1]));
+          float2 t, e;
+          if (first) {
+            t = dv;
+            e = make_float2(0.0f, 0.0f);
+          } else {
+            const float2 hv = make_float2(__uint_as_float(h[q]), __uint_as_float(h[q + 1]));
+            t = __fadd2_rn(hv, dv);
+            const float2 z = __ffma2_rn(hv, bf2(-1.0f), t);
+            e = __ffma2_rn(z, bf2(-1.0f), dv);
+          }
+          h[q] = __float_as_uint(t.x);
+          h[q + 1] = __float_as_uint(t.y);
+          d[q] = __float_as_uint(e.x);
+          d[q + 1] = __float_as_uint(e.y);
+        }
+        BT_ST8(hcol + 16 * piece, h);
+        BT_ST8(hcol + 16 * piece + 8, (h + 8));
+        BT_ST8(dcol + 16 * piece, d);
+        BT_ST8(dcol + 16 * piece + 8, (d + 8));
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(d_ready + (gg & 1))) : "memory");
+    };
+    for (int64_t k = k0; k < k1;) {
       const int64_t tile = k / a.nchunk;
       const int64_t c0 = k - tile * a.nchunk;
       const int64_t c1 = min(a.nchunk, c0 + (k1 - k));
+      const int64_t s_begin = c0 * BT_CHUNK_TILES, s_end = min(a.ntiles_src, c1 * BT_CHUNK_TILES);
       const int64_t ti = tile * BT_M + m;
       const float4 tp = ti < a.nt ? a.tgt[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
-      // FP64 accumulator of this segment: the CTA's own slot (first segment: 2b, later: 2b+1),
-      // laid out [part][rhs][row] so a warp's 32 rows are contiguous
-      const int64_t slot = (k == k0) ? 2 * b : 2 * b + 1;
-      const int row = lq * 32 + lane;
-      const int part = cb >> 1;  // 0: real, 1: imaginary
-      const int r0 = (cb & 1) * 32;
-      double* accp = a.slots + slot * (2 * BT_M * BT_R) + ((int64_t)part * BT_R + r0) * BT_M + row;
-#pragma unroll 8
-      for (int q = 0; q < 32; ++q) accp[(int64_t)q * BT_M] = 0.0;
-      for (int64_t c = c0; c < c1; ++c) {
-        const int64_t s_begin = c * BT_CHUNK_TILES;
-        const int64_t s_end = min(a.ntiles_src, s_begin + BT_CHUNK_TILES);
-        for (int64_t s = s_begin; s < s_end; ++s, ++g) {
-          const int sa = g % BT_NA, sb = g % BT_NB;
-          unsigned char* simg = smem + BT_B_OFF + sb * BT_SIMG;
-          const float* hdr = reinterpret_cast<const float*>(simg);
-          if (!err) err = !mbar_wait(b_full + sb, (g / BT_NB) & 1);
-          // the MMAs of tile g - NA read this A stage
-          if (g >= BT_NA && !err) err = !mbar_wait(mma_done + (g - BT_NA) % BT_NB, ((g - BT_NA) / BT_NB) & 1);
-          // C for (target m, sources 8 oct .. 8 oct + 7), two sources per packed instruction
-          float cre[8], cim[8];
-          {
-            const int j0 = 8 * oct;
-            const float4 xa = *reinterpret_cast<const float4*>(hdr + 0 * BT_S + j0);
-            const float4 xb = *reinterpret_cast<const float4*>(hdr + 0 * BT_S + j0 + 4);
-            const float4 ya = *reinterpret_cast<const float4*>(hdr + 1 * BT_S + j0);
-            const float4 yb = *reinterpret_cast<const float4*>(hdr + 1 * BT_S + j0 + 4);
-            const float4 za = *reinterpret_cast<const float4*>(hdr + 2 * BT_S + j0);
-            const float4 zb = *reinterpret_cast<const float4*>(hdr + 2 * BT_S + j0 + 4);
-            float4 nxa = make_float4(0, 0, 0, 0), nxb = nxa, nya = nxa, nyb = nxa, nza = nxa, nzb = nxa;
-            if (Ev::kNormal) {
-              nxa = *reinterpret_cast<const float4*>(hdr + 3 * BT_S + j0);
-              nxb = *reinterpret_cast<const float4*>(hdr + 3 * BT_S + j0 + 4);
-              nya = *reinterpret_cast<const float4*>(hdr + 4 * BT_S + j0);
-              nyb = *reinterpret_cast<const float4*>(hdr + 4 * BT_S + j0 + 4);
-              nza = *reinterpret_cast<const float4*>(hdr + 5 * BT_S + j0);
-              nzb = *reinterpret_cast<const float4*>(hdr + 5 * BT_S + j0 + 4);
-            }
-            const float2 tx = bf2(tp.x), ty = bf2(tp.y), tz = bf2(tp.z);
-            const float2 sx[4] = {{xa.x, xa.y}, {xa.z, xa.w}, {xb.x, xb.y}, {xb.z, xb.w}};
-            const float2 sy[4] = {{ya.x, ya.y}, {ya.z, ya.w}, {yb.x, yb.y}, {yb.z, yb.w}};
-            const float2 sz[4] = {{za.x, za.y}, {za.z, za.w}, {zb.x, zb.y}, {zb.z, zb.w}};
-            const float2 qx[4] = {{nxa.x, nxa.y}, {nxa.z, nxa.w}, {nxb.x, nxb.y}, {nxb.z, nxb.w}};
-            const float2 qy[4] = {{nya.x, nya.y}, {nya.z, nya.w}, {nyb.x, nyb.y}, {nyb.z, nyb.w}};
-            const float2 qz[4] = {{nza.x, nza.y}, {nza.z, nza.w}, {nzb.x, nzb.y}, {nzb.z, nzb.w}};
+      for (int64_t s = s_begin; s < s_end; ++s, ++g) {
+        const int sb = g % BT_NB;
+        unsigned char* simg = smem + BT_B_OFF + sb * BT_SIMG;
+        const float* hdr = reinterpret_cast<const float*>(simg);
+        if (!err) err = !mbar_wait(b_full + sb, (g / BT_NB) & 1);
+        // C for (target m, sources 8 oct .. 8 oct + 7), two sources per packed instruction
+        float cre[8], cim[8];
+        {
+          const int j0 = 8 * oct;
+          const float4 xa = *reinterpret_cast<const float4*>(hdr + 0 * BT_S + j0);
+          const float4 xb = *reinterpret_cast<const float4*>(hdr + 0 * BT_S + j0 + 4);
+          const float4 ya = *reinterpret_cast<const float4*>(hdr + 1 * BT_S + j0);
+          const float4 yb = *reinterpret_cast<const float4*>(hdr + 1 * BT_S + j0 + 4);
+          const float4 za = *reinterpret_cast<const float4*>(hdr + 2 * BT_S + j0);
+          const float4 zb = *reinterpret_cast<const float4*>(hdr + 2 * BT_S + j0 + 4);
+          float4 nxa = make_float4(0, 0, 0, 0), nxb = nxa, nya = nxa, nyb = nxa, nza = nxa, nzb = nxa;
+          if (Ev::kNormal) {
+            nxa = *reinterpret_cast<const float4*>(hdr + 3 * BT_S + j0);
+            nxb = *reinterpret_cast<const float4*>(hdr + 3 * BT_S + j0 + 4);
+            nya = *reinterpret_cast<const float4*>(hdr + 4 * BT_S + j0);
+            nyb = *reinterpret_cast<const float4*>(hdr + 4 * BT_S + j0 + 4);
+            nza = *reinterpret_cast<const float4*>(hdr + 5 * BT_S + j0);
+            nzb = *reinterpret_cast<const float4*>(hdr + 5 * BT_S + j0 + 4);
+          }
+          const float2 tx = bf2(tp.x), ty = bf2(tp.y), tz = bf2(tp.z);
+          const float2 sx[4] = {{xa.x, xa.y}, {xa.z, xa.w}, {xb.x, xb.y}, {xb.z, xb.w}};
+          const float2 sy[4] = {{ya.x, ya.y}, {ya.z, ya.w}, {yb.x, yb.y}, {yb.z, yb.w}};
+          const float2 sz[4] = {{za.x, za.y}, {za.z, za.w}, {zb.x, zb.y}, {zb.z, zb.w}};
+          const float2 qx[4] = {{nxa.x, nxa.y}, {nxa.z, nxa.w}, {nxb.x, nxb.y}, {nxb.z, nxb.w}};
+          const float2 qy[4] = {{nya.x, nya.y}, {nya.z, nya.w}, {nyb.x, nyb.y}, {nyb.z, nyb.w}};
+          const float2 qz[4] = {{nza.x, nza.y}, {nza.z, nza.w}, {nzb.x, nzb.y}, {nzb.z, nzb.w}};
 #pragma unroll
-            for (int pr = 0; pr < 4; ++pr) {
-              float2 cr2, ci2;
-              eval_pair2<Ev>(tx, ty, tz, sx[pr], sy[pr], sz[pr], qx[pr], qy[pr], qz[pr], cr2, ci2);
-              cre[2 * pr] = cr2.x;
-              cre[2 * pr + 1] = cr2.y;
-              cim[2 * pr] = ci2.x;
-              cim[2 * pr + 1] = ci2.y;
-            }
+          for (int pr = 0; pr < 4; ++pr) {
+            float2 cr2, ci2;
+            eval_pair2<Ev>(tx, ty, tz, sx[pr], sy[pr], sz[pr], qx[pr], qy[pr], qz[pr], cr2, ci2);
+            cre[2 * pr] = cr2.x;
+            cre[2 * pr + 1] = cr2.y;
+            cim[2 * pr] = ci2.x;
+            cim[2 * pr + 1] = ci2.y;
           }
-          uint32_t rh[8], rl[8], ih[8], il[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const float h1 = tf32(cre[q]), h2 = tf32(cim[q]);
-            rh[q] = __float_as_uint(h1);
-            rl[q] = __float_as_uint(tf32(cre[q] - h1));
-            ih[q] = __float_as_uint(h2);
-            il[q] = __float_as_uint(tf32(cim[q] - h2));
-          }
-          {
-            // -Q_re (hi for threads 0-255, lo for 256-511), two 16-byte vectors each
-            const int part_lo = tid >> 8;
-            const int v = (tid & 255) * 2;
-            const float4* src = reinterpret_cast<const float4*>(simg + (part_lo ? BT_S_LO : BT_S_HI)) + v;
-            float4* dst = reinterpret_cast<float4*>(simg + (part_lo ? BT_S_LO : BT_S_HI) + 2 * BT_B_MAT) + v;
-            const float4 q0 = src[0], q1 = src[1];
-            dst[0] = make_float4(-q0.x, -q0.y, -q0.z, -q0.w);
-            dst[1] = make_float4(-q1.x, -q1.y, -q1.z, -q1.w);
-          }
-          // A operands into tensor memory: this warp's 32 rows, columns 8 oct .. 8 oct + 7
-          {
-            const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + 128 + 128 * sa + 8 * oct;
-#define BT_ST8(off, v)                                                                                   \
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(ta + (off)), \
-               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])           \
-               : "memory")
-            BT_ST8(0, rh);
-            BT_ST8(32, rl);
-            BT_ST8(64, ih);
-            BT_ST8(96, il);
-#undef BT_ST8
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the -Q_re blocks
-          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(a_full + sa)) : "memory");
         }
-        // fold the chunk's FP32 accumulator into FP64 registers
-        if (!err && g > 0) err = !mbar_wait(mma_done + ((g - 1) % BT_NB), ((g - 1) / BT_NB) & 1);
+        uint32_t rh[8], rl[8], ih[8], il[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float h1 = tf32(cre[q]), h2 = tf32(cim[q]);
+          rh[q] = __float_as_uint(h1);
+          rl[q] = __float_as_uint(tf32(cre[q] - h1));
+          ih[q] = __float_as_uint(h2);
+          il[q] = __float_as_uint(tf32(cim[q] - h2));
+        }
+        {
+          // -Q_re (hi for threads 0-255, lo for 256-511), two 16-byte vectors each
+          const int part_lo = tid >> 8;
+          const int v = (tid & 255) * 2;
+          const float4* src = reinterpret_cast<const float4*>(simg + (part_lo ? BT_S_LO : BT_S_HI)) + v;
+          float4* dst = reinterpret_cast<float4*>(simg + (part_lo ? BT_S_LO : BT_S_HI) + 2 * BT_B_MAT) + v;
+          const float4 q0 = src[0], q1 = src[1];
+          dst[0] = make_float4(-q0.x, -q0.y, -q0.z, -q0.w);
+          dst[1] = make_float4(-q1.x, -q1.y, -q1.z, -q1.w);
+        }
+        // the A operand buffer is free once the MMAs of the previous tile have retired
+        if (g > 0 && !err) err = !mbar_wait(mma_done + (g - 1) % BT_NB, ((g - 1) / BT_NB) & 1);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!err) {
-          uint32_t r[32];
-          const uint32_t ta = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(cb * 32);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-              : "r"(ta)
-              : "memory");
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-          for (int q = 0; q < 32; ++q) accp[(int64_t)q * BT_M] += (double)__uint_as_float(r[q]);
+        // A operand into tensor memory: this warp's 32 rows, columns 8 oct .. 8 oct + 7
+        {
+          const uint32_t ta = tlane + BT_COL_A + 8 * oct;
+          BT_ST8(ta + 0, rh);
+          BT_ST8(ta + 32, rl);
+          BT_ST8(ta + 64, ih);
+          BT_ST8(ta + 96, il);
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the -Q_re blocks
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(d_free)) : "memory");
-        ++nchunks;
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(a_full)) : "memory");
+        // folds: the previous tile's accumulator (its MMAs retired, waited above) and, on the
+        // segment's last tile, this tile's
+        const int f_end = (s == s_end - 1) ? 2 : 1;
+#pragma unroll 1
+        for (int f = (s > s_begin) ? 0 : 1; f < f_end; ++f) {
+          const uint32_t gg = g - 1 + f;
+          if (f == 1) {
+            if (!err) err = !mbar_wait(mma_done + gg % BT_NB, (gg / BT_NB) & 1);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          }
+          fold(gg, s - 1 + f == s_begin);
+        }
       }
-      // a complete target tile goes to the output; a partial one stays in its slot for the fix-up
-      const bool complete = (c0 == 0 && c1 == a.nchunk);
-      const int64_t i = tile * BT_M + row;
-      if (complete && i < a.nt) {
-#pragma unroll 8
-        for (int q = 0; q < 32; ++q) {
-          const int r = r0 + q;
-          if (r < a.nrhs_out) {
-            double* o = reinterpret_cast<double*>(a.out + (int64_t)r * a.ld_out + i) + part;
-            const double v = accp[(int64_t)q * BT_M];
-            *o = a.mode ? *o + v : v;
+      {
+        // the segment's sum in FP64, H + the compensation in the last tile's buffer (+ that
+        // in the other buffer, used by the segment's previous tile): the target tile
+        // (complete) or its part (partial: the CTA's first segment to slot 2b, a later one
+        // to 2b + 1)
+        const uint32_t gl = g - 1;
+        const bool complete = (c0 == 0 && c1 == a.nchunk);
+        const bool other = (s_end - s_begin >= 2);
+        const int64_t slot = (k == k0) ? 2 * b : 2 * b + 1;
+        const int64_t i = tile * BT_M + row;
+        const uint32_t dcol = tlane + BT_COL_D + 128 * (gl & 1) + 32 * cb;
+        const uint32_t ocol = tlane + BT_COL_D + 128 * ((gl & 1) ^ 1) + 32 * cb;
+        const uint32_t hcol = tlane + BT_COL_H + 32 * cb;
+#pragma unroll 1
+        for (int piece = 0; piece < 4; ++piece) {
+          uint32_t d[8], h[8], o[8];
+          BT_LD8(dcol + 8 * piece, d);
+          BT_LD8(hcol + 8 * piece, h);
+          if (other) BT_LD8(ocol + 8 * piece, o);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float c = __uint_as_float(d[q]) + (other ? __uint_as_float(o[q]) : 0.0f);
+            const double v = (double)__uint_as_float(h[q]) + (double)c;
+            const int r = r0 + 8 * piece + q;
+            if (complete) {
+              if (i < a.nt && r < a.nrhs_out) {
+                double* op = reinterpret_cast<double*>(a.out + (int64_t)r * a.ld_out + i) + part;
+                *op = a.mode ? *op + v : v;
+              }
+            } else {
+              a.slots[slot * (2 * BT_M * BT_R) + ((int64_t)part * BT_R + r) * BT_M + row] = v;
+            }
           }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       }
       k = tile * a.nchunk + c1;
     }
@@ -515,6 +581,8 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BT_TMEM_COLS));
 }
+#undef BT_LD8
+#undef BT_ST8
 
 __device__ __forceinline__ int64_t bt_block_of(const BatchArgs& a, int64_t k) {
   int64_t b = (k * a.grid) / a.nitems;

@@ -41,6 +41,11 @@ def test_batched_matches_oracle(maker, nrhs):
     Y = op.apply_batched(torch.from_numpy(X).cuda()).cpu().numpy()
     errs = [float(np.linalg.norm(Y[r] - ref[r]) / np.linalg.norm(ref[r])) for r in range(nrhs)]
     assert max(errs) <= TOL, max(errs)
+    # the tensor-core path is as accurate as the per-column FP32 apply (accumulator error
+    # compensated), not merely inside the tolerance
+    Y32 = op.apply(torch.from_numpy(X[:3]).cuda(), precision=32).cpu().numpy()
+    e32 = max(float(np.linalg.norm(Y32[r] - ref[r]) / np.linalg.norm(ref[r])) for r in range(min(3, nrhs)))
+    assert max(errs) <= 3.0 * e32 + 1e-7, (max(errs), e32)
 
 
 def test_batched_matches_per_column_apply_mid_size():
@@ -55,6 +60,26 @@ def test_batched_matches_per_column_apply_mid_size():
         assert e <= TOL, (r, e)
     # the same call twice gives identical results (deterministic reduction order)
     assert torch.equal(op.apply_batched(X), Y)
+
+
+def test_batched_oracle_rows_nested24_k10():
+    """Mid-size nested k0 = 10 workload (2,048-source work items, target tiles split over
+    CTAs): sampled rows of eight right-hand sides against the oracle, at the accuracy of
+    the per-column FP32 apply."""
+    torch, B = _setup()
+    w = W.nested_k10(24, 4, 10.0)
+    op = B.Operator.from_workload(w)
+    D = O.Discretisation.from_workload(w)
+    rows = np.sort(np.random.default_rng(0).choice(w.n, 16, replace=False))
+    X = _block(op.n, 64, 100)
+    Xd = torch.from_numpy(X).cuda()
+    Y = op.apply_batched(Xd).cpu().numpy()
+    ref = D.matrix_rows(rows) @ X[:8].T
+    errs = [float(np.linalg.norm(Y[r, rows] - ref[:, r]) / np.linalg.norm(ref[:, r])) for r in range(8)]
+    Y32 = op.apply(Xd[:8], precision=32).cpu().numpy()
+    e32 = max(float(np.linalg.norm(Y32[r, rows] - ref[:, r]) / np.linalg.norm(ref[:, r])) for r in range(8))
+    assert max(errs) <= TOL, max(errs)
+    assert max(errs) <= 3.0 * e32 + 1e-7, (max(errs), e32)
 
 
 def test_expired_wait_reports_error_and_context_survives():
