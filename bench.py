@@ -168,6 +168,26 @@ def solve_timing(torch, B, W, name="nested24_k10", tol=1e-8):
                      "rel_residual": info.rel_residual, "fp64_applies": info.fp64_applies,
                      "fp32_applies": info.fp32_applies}
     out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    # the batched mixed solve: 64 plane waves (Fibonacci directions) in one lockstep solve,
+    # tensor-core FP32 inner applies, FP64 multi-RHS residuals; per right-hand side against
+    # the single-column mixed and FP64 solves above (columns are independent systems)
+    nb = 64
+    B64 = op.plane_wave_rhs(W.fibonacci_dirs(nb)).contiguous()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X, infos = op.solve_batched(B64, mode=32, tol=tol, max_iters=1000, restart=400,
+                                inner_tol=1e-4, max_refinements=20)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    r = B64 - op.apply_batched(X, precision=64)
+    worst = float((torch.linalg.norm(r, dim=1) / torch.linalg.norm(B64, dim=1)).max())
+    its = [i.iterations for i in infos]
+    out["batched_mixed"] = {
+        "nrhs": nb, "seconds": dt, "seconds_per_rhs": dt / nb,
+        "max_rel_residual_fp64": worst, "iterations_mean": float(np.mean(its)), "iterations_max": max(its),
+        "refinements_max": max(i.refinements for i in infos),
+        "speedup_per_rhs_vs_mixed_single": out["mixed"]["seconds"] / (dt / nb),
+        "speedup_per_rhs_vs_fp64_single": out["fp64"]["seconds"] / (dt / nb)}
     op.close()
     return out
 

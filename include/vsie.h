@@ -146,16 +146,20 @@ vsie_status vsie_apply_timed(vsie_handle* h, const void* d_x, void* d_y, int32_t
 vsie_status vsie_apply_noalloc(vsie_handle* h, const void* d_x, void* d_y, int32_t nrhs,
                                int32_t precision, void* stream);
 
-/* y = A x for a block of nrhs right-hand sides with the far-field sums over volume and
- * interface sources contracted on the tensor cores: each tile of kernel values is
- * evaluated once in FP32 and multiplied into 64 charge columns at a time (three-term
- * TF32 split, FP32 accumulation folded into FP64 every 2048 sources).  Volume sources with
- * grad(alpha) != 0, the correction and the mass use the per-column FP32 path.  Same
- * layouts as vsie_apply (precision 32).  Blocks until done (reads the kernels' timeout
- * flag).  Errors: VSIE_ERR_ARG, VSIE_ERR_OOM, VSIE_ERR_CUDA (also when a bounded wait in
- * the tensor-core kernel expired). */
+/* y = A x for a block of nrhs right-hand sides (Eq. vsie at every collocation point, as
+ * vsie_apply) with the far-field sums over volume and interface sources computed once per
+ * kernel value for 64 columns at a time.
+ *   precision 32: each tile of kernel values is evaluated in FP32 and contracted with the
+ *     charge columns on the tensor cores (three-term TF32 split, FP32 accumulation of one
+ *     32-source tile at a time, compensated running sum, FP64 output);
+ *   precision 64: every kernel value is evaluated in FP64 on the CUDA cores and applied
+ *     to the 64 columns in FP64 (the residual operator of vsie_solve_batched).
+ * Volume sources with grad(alpha) != 0, the correction and the mass use the per-column
+ * path of the same precision.  Same layouts as vsie_apply.  Blocks until done (precision
+ * 32 reads the tensor-core kernels' timeout flag).  Errors: VSIE_ERR_ARG, VSIE_ERR_OOM,
+ * VSIE_ERR_CUDA (also when a bounded wait in the tensor-core kernel expired). */
 vsie_status vsie_apply_batched(vsie_handle* h, const void* d_x, void* d_y, int32_t nrhs,
-                               void* stream);
+                               int32_t precision, void* stream);
 
 /* x = A^H y (conjugate transpose), same layouts and precisions as vsie_apply. */
 vsie_status vsie_adjoint_apply(vsie_handle* h, const void* d_y, void* d_x, int32_t nrhs,
@@ -198,6 +202,22 @@ typedef struct {
  * Returns VSIE_ERR_NOT_CONVERGED (x still written, info filled) when the limits are hit. */
 vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
                        const vsie_solve_opts* opts, vsie_solve_info* info, void* stream);
+
+/* Solve A x_c = b_c for nrhs right-hand sides at once: b, x device complex128, n x nrhs
+ * column-major.  Each column runs its own GMRES from x0 = 0 with the options of vsie_solve
+ * (Sec. 3.1: no preconditioner, relative residual tolerance) and its own Krylov basis;
+ * every operator application is shared by the block (lockstep Arnoldi steps, CGS2).
+ *   mode 32: FP64 iterative refinement whose residuals use the FP64 apply, around inner
+ *            cycles with the tensor-core multi-RHS FP32 apply of vsie_apply_batched (the
+ *            single-column FP32 apply once fewer than four columns remain active);
+ *   mode 64: FP64 GMRES with the FP64 apply, column by column.
+ * infos: host array of nrhs entries (per-column counts and final residuals) or NULL.
+ * The Krylov basis (restart, else max_iters) is limited to 1000 columns; the device
+ * workspace is (basis + 4) x n x nrhs complex128, freed on return.  Adjoint solves are
+ * rejected (VSIE_ERR_ARG; use vsie_solve).  Blocking.  Returns VSIE_ERR_NOT_CONVERGED when
+ * any column misses the tolerance (every x column is still written). */
+vsie_status vsie_solve_batched(vsie_handle* h, const void* d_b, void* d_x, int32_t nrhs,
+                               const vsie_solve_opts* opts, vsie_solve_info* infos, void* stream);
 
 /* Adjoint of vsie_far_field: x_e = (1/4pi) sum_{j in e} sum_d e^{+ik0 xhat_d.y_j}
  * (s_j + i k0 xhat_d.v_j) r_d, i.e. x = F^H r for the far-field map F of vsie_far_field

@@ -26,7 +26,7 @@ VSIE_ERR_NOT_CONVERGED = 5
 EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_apply_host",
            "vsie_apply_timed", "vsie_apply_noalloc", "vsie_apply_batched",
            "vsie_adjoint_apply", "vsie_plane_wave_rhs", "vsie_far_field", "vsie_solve",
-           "vsie_far_field_adjoint",
+           "vsie_far_field_adjoint", "vsie_solve_batched",
            "vsie_last_error")
 
 
@@ -98,7 +98,7 @@ def load_library(path: str = LIB_PATH):
     lib.vsie_apply.argtypes = [P, P, P, I32, I32, P]
     lib.vsie_apply_host.argtypes = [P, P, P, I32, I32, P]
     lib.vsie_apply_noalloc.argtypes = [P, P, P, I32, I32, P]
-    lib.vsie_apply_batched.argtypes = [P, P, P, I32, P]
+    lib.vsie_apply_batched.argtypes = [P, P, P, I32, I32, P]
     lib.vsie_adjoint_apply.argtypes = [P, P, P, I32, I32, P]
     lib.vsie_apply_timed.argtypes = [P, P, P, I32, P, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(I32)]
@@ -106,6 +106,8 @@ def load_library(path: str = LIB_PATH):
     lib.vsie_far_field.argtypes = [P, P, I32, P, I32, P, P]
     lib.vsie_far_field_adjoint.argtypes = [P, P, I32, P, I32, P, P]
     lib.vsie_solve.argtypes = [P, P, P, ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), P]
+    lib.vsie_solve_batched.argtypes = [P, P, P, ctypes.c_int32, ctypes.POINTER(_SolveOpts),
+                                       ctypes.POINTER(_SolveInfo), P]
     lib.vsie_last_error.argtypes = []
     lib.vsie_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -213,13 +215,15 @@ class Operator:
                                _stream(stream)))
         return y
 
-    def apply_batched(self, x, y=None, stream=None):
-        """Y = A X for a block (nrhs, n) with the tensor-core far field (vsie_apply_batched)."""
+    def apply_batched(self, x, y=None, precision=32, stream=None):
+        """Y = A X for a block (nrhs, n) with the multi-RHS far field (vsie_apply_batched):
+        precision 32 on the tensor cores, 64 in FP64 on the CUDA cores."""
         import torch
         nrhs = self._nrhs(x)
         if y is None:
             y = torch.empty_like(x)
-        _check(_lib.vsie_apply_batched(self._h, _dev(x, "x"), _dev(y, "y"), nrhs, _stream(stream)))
+        _check(_lib.vsie_apply_batched(self._h, _dev(x, "x"), _dev(y, "y"), nrhs, int(precision),
+                                       _stream(stream)))
         return y
 
     def apply_noalloc(self, x, y, precision=32, stream=None):
@@ -295,6 +299,23 @@ class Operator:
         _check(_lib.vsie_far_field_adjoint(self._h, _dev(rr.contiguous(), "r"), rr.shape[0], _ptr(d),
                                            d.shape[0], _dev(x, "x"), _stream(stream)))
         return x[0] if r.dim() == 1 else x
+
+    def solve_batched(self, b, mode=32, tol=1e-8, max_iters=1000, restart=0, inner_tol=1e-4,
+                      max_refinements=20, stream=None, raise_on_fail=True):
+        """X with A X[c] = B[c] for a block B (nrhs, n), every column its own GMRES, the
+        operator applications shared (vsie_solve_batched); returns (X, [SolveInfo])."""
+        import torch
+        nrhs = self._nrhs(b)
+        x = torch.empty_like(b)
+        o = _SolveOpts(int(mode), float(tol), int(max_iters), int(restart), float(inner_tol),
+                       int(max_refinements), 0)
+        infos = (_SolveInfo * nrhs)()
+        st = _lib.vsie_solve_batched(self._h, _dev(b, "b"), _dev(x, "x"), nrhs, ctypes.byref(o),
+                                     infos, _stream(stream))
+        if raise_on_fail:
+            _check(st)
+        return x, [SolveInfo(st, i.iterations, i.refinements, i.rel_residual, i.fp64_applies,
+                             i.fp32_applies) for i in infos]
 
     def solve(self, b, mode=32, tol=1e-8, max_iters=1000, restart=0, inner_tol=1e-4,
               max_refinements=20, stream=None, raise_on_fail=True, adjoint=False):

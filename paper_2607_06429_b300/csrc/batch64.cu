@@ -1,0 +1,256 @@
+// Multi-right-hand-side far-field sums in FP64 on the CUDA cores: the residual operator of
+// the batched iterative refinement (the outer residual b - A x must be accurate to FP64
+// level, which an FP32 tensor-core accumulator cannot give).
+//
+// Same sums as the FP64 single-column path (Eq. vsie; G and K source classes, positions
+// scaled by kappa = k0/(2 pi), phase in revolutions), but each kernel coefficient C(x_i, y_j)
+// is evaluated once and applied to a block of up to 64 right-hand sides:
+//     Y[i, r] = sum_j C(x_i, y_j) q_j^(r).
+// One block owns 64 targets x 64 right-hand sides; per tile of 32 sources its 256 threads
+// evaluate the 2048 coefficients into shared memory (8 per thread, own target), then each
+// thread accumulates its target against 16 right-hand sides (16 complex FP64 accumulators),
+// reading the charges as warp-wide broadcasts.  The FP64 pipe (1/64 of the FP32 rate on
+// B300) bounds the kernel: 4 DFMA per pair and right-hand side plus the amortised
+// coefficient evaluation.  Source ranges are split over blockIdx.y when the target blocks
+// alone do not fill the GPU; the partial sums are added in split order (deterministic).
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "vsie_internal.h"
+
+namespace vsie {
+
+namespace {
+
+constexpr int B64_T = 64;        // targets per block
+constexpr int B64_S = 32;        // sources per tile
+constexpr int B64_R = 64;        // right-hand sides per launch
+constexpr int B64_THREADS = 256;
+constexpr int B64_RPT = B64_R / (B64_THREADS / B64_T);  // right-hand sides per thread (16)
+constexpr size_t B64_SMEM = sizeof(double4_32a) * 2 * B64_S + sizeof(double2) * 2 * B64_S * B64_T;
+
+struct B64Args {
+  const double4_32a* tgt;   // collocation points (FP64)
+  const double4_32a* pos;   // source (x, y, z, s)
+  const double4_32a* nrm;   // source (nx, ny, nz, sigma) (K class)
+  const double2* q;         // charges [source][B64_R]
+  double kap;
+  int64_t nt, ns, ntiles;
+  int nsplit;
+  double2* out;             // n x nrhs_out column-major
+  int64_t ld_out;
+  int nrhs_out;
+  int mode;                 // 0 store, 1 add
+  double2* part;            // [nsplit][B64_R][nt] when nsplit > 1
+};
+
+// coefficient of a G source: e^{2 pi i t} / |d~|;  K source: e^{2 pi i t}(2 pi i t - 1)(d~ . n)/|d~|^3
+template <bool IsK>
+__device__ __forceinline__ double2 coef64(double tx, double ty, double tz, const double4_32a& p,
+                                          const double4_32a& nv) {
+  const double dx = tx - p.x, dy = ty - p.y, dz = tz - p.z;
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  const double rinv = (r2 > 0.0) ? rsqrt(r2) : 0.0;
+  const double t = r2 * rinv;
+  const double f = t - rint(t);
+  double sn, cs;
+  sincospi(2.0 * f, &sn, &cs);
+  if (!IsK) return make_double2(cs * rinv, sn * rinv);
+  const double dn = dx * nv.x + dy * nv.y + dz * nv.z;
+  const double g3 = rinv * rinv * rinv * dn;
+  const double kr = t * 6.28318530717958647692;
+  return make_double2((-cs - kr * sn) * g3, (kr * cs - sn) * g3);
+}
+
+template <bool IsK>
+__global__ void __launch_bounds__(B64_THREADS, 2) b64_kernel(B64Args a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  double4_32a* sp = reinterpret_cast<double4_32a*>(sm);            // kappa-scaled positions
+  double4_32a* sn = sp + B64_S;                                     // normals (K)
+  double2* sC = reinterpret_cast<double2*>(sn + B64_S);            // [S][T] coefficients
+  double2* sQ = sC + B64_S * B64_T;                                 // [S][R] charges
+  const int tid = threadIdx.x;
+  const int t = tid & (B64_T - 1), rg = tid / B64_T;
+  const int64_t i = (int64_t)blockIdx.x * B64_T + t;
+  const bool tok = i < a.nt;
+  double tx = 0.0, ty = 0.0, tz = 0.0;
+  if (tok) {
+    const double4_32a p = a.tgt[i];
+    tx = p.x * a.kap;
+    ty = p.y * a.kap;
+    tz = p.z * a.kap;
+  }
+  double2 acc[B64_RPT];
+#pragma unroll
+  for (int r = 0; r < B64_RPT; ++r) acc[r] = make_double2(0.0, 0.0);
+  const int sp_i = blockIdx.y;
+  const int64_t tile0 = (a.ntiles * sp_i) / a.nsplit, tile1 = (a.ntiles * (sp_i + 1)) / a.nsplit;
+  for (int64_t tile = tile0; tile < tile1; ++tile) {
+    __syncthreads();
+    const int64_t j0 = tile * B64_S;
+    if (tid < B64_S) {
+      const int64_t j = j0 + tid;
+      double4_32a p = make_double4_32a(0, 0, 0, 0), nv = make_double4_32a(0, 0, 0, 0);
+      if (j < a.ns) {
+        const double4_32a q = a.pos[j];
+        p = make_double4_32a(q.x * a.kap, q.y * a.kap, q.z * a.kap, 0.0);
+        if (IsK) nv = a.nrm[j];
+      }
+      sp[tid] = p;
+      sn[tid] = nv;
+    }
+    for (int e = tid; e < B64_S * B64_R; e += B64_THREADS) {
+      const int64_t j = j0 + e / B64_R;
+      sQ[e] = (j < a.ns) ? a.q[j0 * B64_R + e] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int q = 0; q < B64_S / (B64_THREADS / B64_T); ++q) {
+      const int jj = rg + (B64_THREADS / B64_T) * q;
+      sC[jj * B64_T + t] = coef64<IsK>(tx, ty, tz, sp[jj], sn[jj]);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < B64_S; ++jj) {
+      const double2 c = sC[jj * B64_T + t];
+      const double2* qr = sQ + jj * B64_R + rg * B64_RPT;
+#pragma unroll
+      for (int r = 0; r < B64_RPT; ++r) {
+        const double2 qv = qr[r];
+        acc[r].x = fma(c.x, qv.x, fma(-c.y, qv.y, acc[r].x));
+        acc[r].y = fma(c.x, qv.y, fma(c.y, qv.x, acc[r].y));
+      }
+    }
+  }
+  if (!tok) return;
+#pragma unroll
+  for (int r = 0; r < B64_RPT; ++r) {
+    const int rr = rg * B64_RPT + r;
+    if (rr >= a.nrhs_out) continue;
+    if (a.nsplit == 1) {
+      double2* o = a.out + (int64_t)rr * a.ld_out + i;
+      *o = a.mode ? make_double2(o->x + acc[r].x, o->y + acc[r].y) : acc[r];
+    } else {
+      a.part[((int64_t)sp_i * B64_R + rr) * a.nt + i] = acc[r];
+    }
+  }
+}
+
+// out (+)= sum over splits of part, in split order
+__global__ void b64_reduce_kernel(B64Args a) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)a.nrhs_out * a.nt) return;
+  const int64_t r = e / a.nt, i = e % a.nt;
+  double sr = 0.0, si = 0.0;
+  for (int s = 0; s < a.nsplit; ++s) {
+    const double2 v = a.part[((int64_t)s * B64_R + r) * a.nt + i];
+    sr += v.x;
+    si += v.y;
+  }
+  double2* o = a.out + r * a.ld_out + i;
+  *o = a.mode ? make_double2(o->x + sr, o->y + si) : make_double2(sr, si);
+}
+
+// charges of one block of right-hand sides: q[j][r] = sc_j p_r(e(j)), zero past nrhs
+// G: sc = -kappa s / (4 pi);  K: sc = kappa^2 sigma / (4 pi)
+__global__ void b64_charges_kernel(const double4_32a* __restrict__ pos, const double4_32a* __restrict__ aux,
+                                   const int32_t* __restrict__ own, int64_t ns, const double2* __restrict__ x,
+                                   int64_t ld_x, int nrhs, int r_base, double kap, int is_k,
+                                   double2* __restrict__ q) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ns * B64_R) return;
+  const int r = (int)(e % B64_R);
+  const int64_t j = e / B64_R;
+  const int rr = r_base + r;
+  double2 v = make_double2(0.0, 0.0);
+  if (rr < nrhs) {
+    const double sc = is_k ? kap * kap * aux[j].w / kFourPi : -kap * pos[j].w / kFourPi;
+    const double2 p = x[(int64_t)rr * ld_x + own[j]];
+    v = make_double2(sc * p.x, sc * p.y);
+  }
+  q[e] = v;
+}
+
+vsie_status b64_class(vsie_handle* h, const Sources& S, bool is_k, const double2* x, double2* y, int nrhs,
+                      int r_base, int mode, cudaStream_t st) {
+  const int64_t n = h->n;
+  const size_t qn = (size_t)S.n * B64_R;
+  if (h->batch.q64_elems < qn) {
+    double2* p = nullptr;
+    VSIE_TRY(dalloc_t(h, &p, qn));
+    h->batch.q64 = p;
+    h->batch.q64_elems = qn;
+  }
+  const double kap = h->k0 / (2.0 * kPi);
+  b64_charges_kernel<<<(unsigned)((qn + 255) / 256), 256, 0, st>>>(S.pos_s, S.aux, S.owner, S.n, x, n, nrhs,
+                                                                   r_base, kap, is_k ? 1 : 0, h->batch.q64);
+  VSIE_CUDA(cudaGetLastError());
+  B64Args a;
+  a.tgt = h->tgt64;
+  a.pos = S.pos_s;
+  a.nrm = S.aux;
+  a.q = h->batch.q64;
+  a.kap = kap;
+  a.nt = n;
+  a.ns = S.n;
+  a.ntiles = (S.n + B64_S - 1) / B64_S;
+  const int64_t ntb = (n + B64_T - 1) / B64_T;
+  const int64_t want = 4LL * 2 * std::max(h->num_sms, 1);  // four waves of two resident blocks per SM
+  a.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(a.ntiles, (want + ntb - 1) / ntb));
+  a.out = y + (int64_t)r_base * n;
+  a.ld_out = n;
+  a.nrhs_out = std::min(B64_R, nrhs - r_base);
+  a.mode = mode;
+  a.part = nullptr;
+  if (a.nsplit > 1) {
+    const size_t pn = (size_t)a.nsplit * B64_R * n;
+    if (h->batch.part64_elems < pn) {
+      double2* p = nullptr;
+      VSIE_TRY(dalloc_t(h, &p, pn));
+      h->batch.part64 = p;
+      h->batch.part64_elems = pn;
+    }
+    a.part = h->batch.part64;
+  }
+  const dim3 grid((unsigned)ntb, (unsigned)a.nsplit);
+  if (is_k) {
+    VSIE_CUDA(cudaFuncSetAttribute(b64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B64_SMEM));
+    b64_kernel<true><<<grid, B64_THREADS, B64_SMEM, st>>>(a);
+  } else {
+    VSIE_CUDA(cudaFuncSetAttribute(b64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B64_SMEM));
+    b64_kernel<false><<<grid, B64_THREADS, B64_SMEM, st>>>(a);
+  }
+  VSIE_CUDA(cudaGetLastError());
+  if (a.nsplit > 1) {
+    const int64_t e = (int64_t)a.nrhs_out * n;
+    b64_reduce_kernel<<<(unsigned)((e + 255) / 256), 256, 0, st>>>(a);
+    VSIE_CUDA(cudaGetLastError());
+  }
+  return VSIE_OK;
+}
+
+}  // namespace
+
+// y[:, r] = (FP64 far-field sums over the G and K classes) for all columns r, 64 at a time
+vsie_status far_batched64_gk(vsie_handle* h, const double2* x, double2* y, int nrhs, cudaStream_t st) {
+  for (int r0 = 0; r0 < nrhs; r0 += B64_R) {
+    int mode = 0;
+    if (h->G.n) {
+      VSIE_TRY(b64_class(h, h->G, false, x, y, nrhs, r0, mode, st));
+      mode = 1;
+    }
+    if (h->K.n) {
+      VSIE_TRY(b64_class(h, h->K, true, x, y, nrhs, r0, mode, st));
+      mode = 1;
+    }
+    if (!mode) {
+      const int cols = std::min(B64_R, nrhs - r0);
+      VSIE_CUDA(cudaMemsetAsync(y + (int64_t)r0 * h->n, 0, sizeof(double2) * h->n * cols, st));
+    }
+  }
+  return VSIE_OK;
+}
+
+}  // namespace vsie

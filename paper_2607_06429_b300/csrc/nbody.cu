@@ -955,10 +955,10 @@ vsie_status far_apply(vsie_handle* h, const double2* x, double2* y, int precisio
   return forward(h, y, precision, nullptr, st, 7, nullptr);
 }
 
-vsie_status far_sum_f_only(vsie_handle* h, const double2* x, double2* y, cudaStream_t st) {
+vsie_status far_sum_f_only(vsie_handle* h, const double2* x, double2* y, int precision, cudaStream_t st) {
   if (!h->F.n) return VSIE_OK;
-  VSIE_TRY(far_prescale(h, x, 32, st, nullptr));
-  return forward(h, y, 32, nullptr, st, 4, nullptr);
+  VSIE_TRY(far_prescale(h, x, precision, st, nullptr));
+  return forward(h, y, precision, nullptr, st, 4, nullptr);
 }
 
 size_t far_split_elems(const vsie_handle* h) {

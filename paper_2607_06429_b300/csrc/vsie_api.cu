@@ -502,19 +502,23 @@ extern "C" vsie_status vsie_apply_timed(vsie_handle* h, const void* d_x, void* d
 }
 
 extern "C" vsie_status vsie_apply_batched(vsie_handle* h, const void* d_x, void* d_y, int32_t nrhs,
-                                          void* stream) {
+                                          int32_t precision, void* stream) {
   clear_error();
-  VSIE_TRY(check_apply_args(h, d_x, d_y, nrhs, 32, "vsie_apply_batched"));
+  VSIE_TRY(check_apply_args(h, d_x, d_y, nrhs, precision, "vsie_apply_batched"));
   cudaStream_t st = (cudaStream_t)stream;
   const double2* x = (const double2*)d_x;
   double2* y = (double2*)d_y;
-  VSIE_TRY(far_batched_gk(h, x, y, nrhs, st));
+  if (precision == 32)
+    VSIE_TRY(far_batched_gk(h, x, y, nrhs, st));
+  else
+    VSIE_TRY(far_batched64_gk(h, x, y, nrhs, st));
   for (int r = 0; r < nrhs; ++r) {
     const double2* xr = x + (size_t)r * h->n;
     double2* yr = y + (size_t)r * h->n;
-    VSIE_TRY(far_sum_f_only(h, xr, yr, st));
-    VSIE_TRY(correction_apply(h, xr, yr, 32, st));
+    VSIE_TRY(far_sum_f_only(h, xr, yr, precision, st));
+    VSIE_TRY(correction_apply(h, xr, yr, precision, st));
   }
   VSIE_CUDA(cudaGetLastError());
+  if (precision == 64) return VSIE_OK;
   return batch_status(h, st);
 }

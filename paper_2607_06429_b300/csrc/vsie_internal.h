@@ -88,6 +88,10 @@ struct BatchBuffers {
   double* slots = nullptr;       // per-CTA FP64 accumulators / partial tiles of the fix-up
   size_t slot_elems = 0;
   int* status = nullptr;         // set by a timed-out mbarrier wait
+  double2* q64 = nullptr;        // FP64 multi-RHS charges [source][64]
+  size_t q64_elems = 0;
+  double2* part64 = nullptr;     // FP64 multi-RHS partial sums of the source splits
+  size_t part64_elems = 0;
 };
 
 }  // namespace vsie
@@ -171,8 +175,11 @@ vsie_status apply_one(vsie_handle* h, const double2* x, double2* y, int precisio
 // clears) the timeout flag of those kernels, synchronising the stream.
 vsie_status far_batched_gk(vsie_handle* h, const double2* x, double2* y, int nrhs, cudaStream_t st);
 vsie_status batch_status(vsie_handle* h, cudaStream_t st);
+// The same sums in FP64 on the CUDA cores (each coefficient evaluated once per block of 64
+// columns); y is overwritten.
+vsie_status far_batched64_gk(vsie_handle* h, const double2* x, double2* y, int nrhs, cudaStream_t st);
 // Far-field sum of the F class only (added into y), for one column.
-vsie_status far_sum_f_only(vsie_handle* h, const double2* x, double2* y, cudaStream_t st);
+vsie_status far_sum_f_only(vsie_handle* h, const double2* x, double2* y, int precision, cudaStream_t st);
 
 
 }  // namespace vsie
