@@ -192,7 +192,7 @@ def solve_timing(torch, B, W, name="nested24_k10", tol=1e-8):
     return out
 
 
-def batched_timing(torch, op, W, nrhs=64, steps=2):
+def batched_timing(torch, op, W, nrhs=64, steps=2, fp64=False):
     """Tensor-core multi-RHS apply (vsie_apply_batched) on the same operator: one block of
     nrhs right-hand sides per step; pair interactions counted per right-hand side."""
     X = torch.from_numpy(np.stack([W.random_vector(op.n, 1000 + r) for r in range(nrhs)])).cuda()
@@ -208,8 +208,20 @@ def batched_timing(torch, op, W, nrhs=64, steps=2):
     # agreement with the per-column FP32 apply on two columns
     err = max(float(torch.linalg.norm(Y[r] - op.apply(X[r], precision=32)) / torch.linalg.norm(Y[r]))
               for r in (0, nrhs - 1))
-    return {"nrhs": nrhs, "seconds_per_block": t, "interactions_per_s": op.n * op.n_far_sources * nrhs / t,
-            "max_rel_diff_vs_per_column_fp32": err}
+    out = {"nrhs": nrhs, "seconds_per_block": t, "interactions_per_s": op.n * op.n_far_sources * nrhs / t,
+           "max_rel_diff_vs_per_column_fp32": err}
+    if fp64:
+        # the FP64 multi-RHS apply (the residual operator of the batched solve)
+        op.apply_batched(X, Y, precision=64)
+        torch.cuda.synchronize()
+        a.record()
+        op.apply_batched(X, Y, precision=64)
+        b.record()
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b) * 1e-3
+        out["fp64_seconds_per_block"] = t64
+        out["fp64_interactions_per_s"] = op.n * op.n_far_sources * nrhs / t64
+    return out
 
 
 def flush_l2(torch, buf):
@@ -328,7 +340,7 @@ def main():
 
     batched = None
     if not args.no_batched and args.precision == 32:
-        batched = batched_timing(torch, op, W)
+        batched = batched_timing(torch, op, W, fp64=n * nsrc < 1e11)
 
     solve = None
     if not args.no_solve:

@@ -29,6 +29,7 @@
 #include <thrust/sequence.h>
 #include <thrust/sort.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "vsie_internal.h"
@@ -351,6 +352,150 @@ vsie_status correction_adjoint(vsie_handle* h, const double2* lam, double2* x, i
   corr_adjoint_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(h->C.row_ptr, h->C.col, val,
                                                                           lam, x, n);
   VSIE_CUDA(cudaGetLastError());
+  return VSIE_OK;
+}
+
+// ----------------------------------------------------------------- block application
+
+// xt[c][r] = x[r][c] for a block of up to 64 columns starting at column r_base: row-major,
+// 64 entries per row (zero past the block), as float2 (FP32 path) or double2 (FP64 path).
+// 32 x 32 tiles through shared memory, so both the reads and the writes are coalesced.
+template <class T2>
+__device__ __forceinline__ T2 to_t2(double2 v);
+template <>
+__device__ __forceinline__ float2 to_t2<float2>(double2 v) {
+  return make_float2((float)v.x, (float)v.y);
+}
+template <>
+__device__ __forceinline__ double2 to_t2<double2>(double2 v) {
+  return v;
+}
+
+template <class T2>
+__global__ void corr_transpose_kernel(const double2* __restrict__ x, int64_t n, int ncols,
+                                      T2* __restrict__ xt) {
+  __shared__ double2 tile[32][33];
+  const int64_t c0 = (int64_t)blockIdx.x * 32;
+  const int r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k;
+    const int64_t c = c0 + threadIdx.x;
+    tile[k][threadIdx.x] = (r < ncols && c < n) ? x[(int64_t)r * n + c] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t c = c0 + k;
+    if (c < n) xt[c * 64 + r0 + threadIdx.x] = to_t2<T2>(tile[threadIdx.x][k]);
+  }
+}
+
+__global__ void to_float2_kernel(const double2* __restrict__ v, float2* __restrict__ o, int64_t m) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) o[i] = make_float2((float)v[i].x, (float)v[i].y);
+}
+
+// Kahan step for the (re, im) pair: s + c carries the sum, c the negated lost low part
+__device__ __forceinline__ void kahan2(float2& s, float2& c, float2 p) {
+  const float2 yv = __fadd2_rn(p, make_float2(-c.x, -c.y));
+  const float2 t = __fadd2_rn(s, yv);
+  c = __fadd2_rn(__fadd2_rn(t, make_float2(-s.x, -s.y)), make_float2(-yv.x, -yv.y));
+  s = t;
+}
+
+// y[r][i] += m_i x[r][i] + sum_k Delta_ik x[r][col_k] for the ncols columns of a block:
+// one warp per row i, lane l owns columns l and l + 32.  The row's (value, column) pairs are
+// loaded 32 at a time (coalesced) and broadcast by shuffles; each nonzero then costs one
+// coalesced read of the charge row xt[col] (256 or 512 bytes, L2-resident for mid-size
+// meshes).  FP32 path: FP32 products, Kahan-compensated sums; FP64 path: FP64 throughout.
+template <class T2>
+__global__ void __launch_bounds__(256) corr_block_kernel(const int64_t* __restrict__ rp,
+                                                         const int32_t* __restrict__ col,
+                                                         const T2* __restrict__ val,
+                                                         const double* __restrict__ mass,
+                                                         const T2* __restrict__ xt,
+                                                         const double2* __restrict__ x,
+                                                         double2* __restrict__ y, int64_t n, int ncols) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  constexpr bool kF32 = sizeof(T2) == 8;
+  T2 s0{}, s1{}, c0{}, c1{};
+  const int64_t pb = rp[row], pe = rp[row + 1];
+  for (int64_t p0 = pb; p0 < pe; p0 += 32) {
+    const int cnt = (int)min((int64_t)32, pe - p0);
+    T2 mv{};
+    int32_t mc = 0;
+    if (lane < cnt) {
+      mv = val[p0 + lane];
+      mc = col[p0 + lane];
+    }
+#pragma unroll 4
+    for (int q = 0; q < cnt; ++q) {
+      T2 v;
+      v.x = __shfl_sync(0xffffffffu, mv.x, q);
+      v.y = __shfl_sync(0xffffffffu, mv.y, q);
+      const int32_t cc = __shfl_sync(0xffffffffu, mc, q);
+      const T2 a = xt[(int64_t)cc * 64 + lane], b = xt[(int64_t)cc * 64 + lane + 32];
+      if constexpr (kF32) {
+        kahan2(s0, c0, make_float2(fmaf(v.x, a.x, -v.y * a.y), fmaf(v.x, a.y, v.y * a.x)));
+        kahan2(s1, c1, make_float2(fmaf(v.x, b.x, -v.y * b.y), fmaf(v.x, b.y, v.y * b.x)));
+      } else {
+        s0.x = fma(v.x, a.x, fma(-v.y, a.y, s0.x));
+        s0.y = fma(v.x, a.y, fma(v.y, a.x, s0.y));
+        s1.x = fma(v.x, b.x, fma(-v.y, b.y, s1.x));
+        s1.y = fma(v.x, b.y, fma(v.y, b.x, s1.y));
+      }
+    }
+  }
+  const double m = mass[row];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = lane + 32 * h;
+    if (r >= ncols) continue;
+    const T2 sv = h ? s1 : s0, cv = h ? c1 : c0;
+    const double ar = (double)sv.x - (double)cv.x, ai = (double)sv.y - (double)cv.y;
+    const double2 q = x[(int64_t)r * n + row];
+    double2* o = y + (int64_t)r * n + row;
+    const double2 ov = *o;
+    *o = make_double2(ov.x + m * q.x + ar, ov.y + m * q.y + ai);
+  }
+}
+
+vsie_status correction_apply_block(vsie_handle* h, const double2* x, double2* y, int ncols, int precision,
+                                   cudaStream_t st) {
+  const int64_t n = h->n;
+  if (n == 0 || ncols < 1) return VSIE_OK;
+  const size_t xt_bytes = (size_t)n * 64 * (precision == 32 ? sizeof(float2) : sizeof(double2));
+  if (h->batch.xt_bytes < xt_bytes) {
+    unsigned char* p = nullptr;
+    VSIE_TRY(dalloc_t(h, &p, xt_bytes));
+    h->batch.xt = p;
+    h->batch.xt_bytes = xt_bytes;
+  }
+  if (precision == 32 && !h->C.val32f && h->C.nnz > 0) {
+    VSIE_TRY(dalloc_t(h, &h->C.val32f, (size_t)h->C.nnz));
+    to_float2_kernel<<<(unsigned)((h->C.nnz + 255) / 256), 256, 0, st>>>(h->C.val32, h->C.val32f, h->C.nnz);
+    VSIE_CUDA(cudaGetLastError());
+  }
+  const dim3 tgrid((unsigned)((n + 31) / 32), 2), tblock(32, 8);
+  const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
+  for (int r0 = 0; r0 < ncols; r0 += 64) {
+    const int nc = std::min(64, ncols - r0);
+    const double2* xb = x + (size_t)r0 * n;
+    double2* yb = y + (size_t)r0 * n;
+    if (precision == 32) {
+      float2* xt = reinterpret_cast<float2*>(h->batch.xt);
+      corr_transpose_kernel<float2><<<tgrid, tblock, 0, st>>>(xb, n, nc, xt);
+      corr_block_kernel<float2><<<blocks, 256, 0, st>>>(h->C.row_ptr, h->C.col, h->C.val32f, h->mass, xt, xb, yb,
+                                                         n, nc);
+    } else {
+      double2* xt = reinterpret_cast<double2*>(h->batch.xt);
+      corr_transpose_kernel<double2><<<tgrid, tblock, 0, st>>>(xb, n, nc, xt);
+      corr_block_kernel<double2><<<blocks, 256, 0, st>>>(h->C.row_ptr, h->C.col, h->C.val64, h->mass, xt, xb,
+                                                          yb, n, nc);
+    }
+    VSIE_CUDA(cudaGetLastError());
+  }
   return VSIE_OK;
 }
 

@@ -218,10 +218,10 @@ vsie_status block_apply(vsie_handle* h, const double2* X, double2* W, int a, int
       VSIE_TRY(far_batched_gk(h, X, W, a, st));
     else
       VSIE_TRY(far_batched64_gk(h, X, W, a, st));
-    for (int y = 0; y < a; ++y) {
-      VSIE_TRY(far_sum_f_only(h, X + (size_t)y * n, W + (size_t)y * n, precision, st));
-      VSIE_TRY(correction_apply(h, X + (size_t)y * n, W + (size_t)y * n, precision, st));
-    }
+    if (h->F.n)
+      for (int y = 0; y < a; ++y)
+        VSIE_TRY(far_sum_f_only(h, X + (size_t)y * n, W + (size_t)y * n, precision, st));
+    VSIE_TRY(correction_apply_block(h, X, W, a, precision, st));
     if (precision == 32) VSIE_TRY(batch_status(h, st));
   } else {
     for (int y = 0; y < a; ++y) VSIE_TRY(apply_one(h, X + (size_t)y * n, W + (size_t)y * n, precision, st));

@@ -512,12 +512,10 @@ extern "C" vsie_status vsie_apply_batched(vsie_handle* h, const void* d_x, void*
     VSIE_TRY(far_batched_gk(h, x, y, nrhs, st));
   else
     VSIE_TRY(far_batched64_gk(h, x, y, nrhs, st));
-  for (int r = 0; r < nrhs; ++r) {
-    const double2* xr = x + (size_t)r * h->n;
-    double2* yr = y + (size_t)r * h->n;
-    VSIE_TRY(far_sum_f_only(h, xr, yr, precision, st));
-    VSIE_TRY(correction_apply(h, xr, yr, precision, st));
-  }
+  if (h->F.n)
+    for (int r = 0; r < nrhs; ++r)
+      VSIE_TRY(far_sum_f_only(h, x + (size_t)r * h->n, y + (size_t)r * h->n, precision, st));
+  VSIE_TRY(correction_apply_block(h, x, y, nrhs, precision, st));
   VSIE_CUDA(cudaGetLastError());
   if (precision == 64) return VSIE_OK;
   return batch_status(h, st);

@@ -70,6 +70,7 @@ struct Correction {
   int32_t* col = nullptr;      // nnz
   double2* val64 = nullptr;    // accurate - far-rule value (FP64 coordinates)
   double2* val32 = nullptr;    // accurate - far-rule value (FP32-rounded coordinates)
+  float2* val32f = nullptr;    // val32 rounded to FP32 (block application, built on first use)
 };
 
 // Per-call buffers of the adjoint far-field sum (allocated on the first adjoint call).
@@ -92,6 +93,8 @@ struct BatchBuffers {
   size_t q64_elems = 0;
   double2* part64 = nullptr;     // FP64 multi-RHS partial sums of the source splits
   size_t part64_elems = 0;
+  unsigned char* xt = nullptr;   // row-major charge block of the block correction
+  size_t xt_bytes = 0;
 };
 
 }  // namespace vsie
@@ -163,6 +166,10 @@ vsie_status far_adjoint(vsie_handle* h, const double2* lam, double2* x, int prec
 // y += m x + Delta x  (Delta for the given precision's far sum)
 vsie_status correction_apply(vsie_handle* h, const double2* x, double2* y, int precision,
                              cudaStream_t st);
+// y[:, r] += m x[:, r] + Delta x[:, r] for ncols columns (n x ncols column-major), 64 at a
+// time with one pass over the correction matrix per 64 columns
+vsie_status correction_apply_block(vsie_handle* h, const double2* x, double2* y, int ncols, int precision,
+                                   cudaStream_t st);
 // x += conj(m) lam + Delta^H lam
 vsie_status correction_adjoint(vsie_handle* h, const double2* lam, double2* x,
                                int precision, cudaStream_t st);

@@ -48,6 +48,12 @@ def test_fp64_batched_apply_matches_oracle(case):
     ref = X @ A.T
     for r in range(7):
         assert _rel(Y[r], ref[r]) <= 1e-12, (name, r, _rel(Y[r], ref[r]))
+    # two blocks of 64 columns (ragged second block) against the single-column FP64 apply
+    X2 = torch.from_numpy(np.stack([W.random_vector(D.n, 200 + r) for r in range(70)])).cuda()
+    Y2 = op.apply_batched(X2, precision=64)
+    Yc = op.apply(X2, precision=64)
+    for r in (0, 63, 64, 69):
+        assert float(torch.linalg.norm(Y2[r] - Yc[r]) / torch.linalg.norm(Yc[r])) <= 1e-13
 
 
 @pytest.mark.parametrize("mode", [32, 64])
