@@ -161,6 +161,30 @@ vsie_status vsie_apply_noalloc(vsie_handle* h, const void* d_x, void* d_y, int32
 vsie_status vsie_apply_batched(vsie_handle* h, const void* d_x, void* d_y, int32_t nrhs,
                                int32_t precision, void* stream);
 
+/* The precision-32 vsie_apply_batched of nop operators at once, operator p applied to its
+ * own block d_x[p] -> d_y[p] (each n x nrhs): the persistent tensor-core launch of each
+ * source class covers the items of up to 16 operators, so that several frequencies (or
+ * materials) on one mesh share one launch and its load balance.  The operators must agree
+ * in n and in the far-field source counts of each class (the same mesh; different k0, rho,
+ * c are fine) and be distinct.  hs, d_x, d_y: host arrays of nop entries.  Blocking (reads
+ * the kernels' timeout flags).  Errors as vsie_apply_batched; VSIE_ERR_ARG on a size
+ * mismatch. */
+vsie_status vsie_apply_batched_multi(vsie_handle* const* hs, int32_t nop, const void* const* d_x,
+                                     void* const* d_y, int32_t nrhs, void* stream);
+
+/* A CUDA-graph plan of vsie_apply_batched_multi for fixed operators and buffers: create
+ * runs the apply once (allocating every scratch buffer, results in d_y), then records all
+ * its launches by stream capture on a private stream; launch replays the graph on
+ * ``stream`` and blocks until done (reads the timeout flags).  The plan holds the device
+ * pointers: the buffers and operators must outlive it, and no other call may use the
+ * operators while a launch runs.  nodes: number of graph nodes (launches and copies). */
+typedef struct vsie_graph vsie_graph;
+vsie_status vsie_graph_create_batched(vsie_handle* const* hs, int32_t nop, const void* const* d_x,
+                                      void* const* d_y, int32_t nrhs, vsie_graph** out);
+vsie_status vsie_graph_launch(vsie_graph* g, void* stream);
+vsie_status vsie_graph_nodes(const vsie_graph* g, int64_t* nodes);
+void vsie_graph_destroy(vsie_graph* g);
+
 /* x = A^H y (conjugate transpose), same layouts and precisions as vsie_apply. */
 vsie_status vsie_adjoint_apply(vsie_handle* h, const void* d_y, void* d_x, int32_t nrhs,
                                int32_t precision, void* stream);

@@ -26,7 +26,8 @@ VSIE_ERR_NOT_CONVERGED = 5
 EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_apply_host",
            "vsie_apply_timed", "vsie_apply_noalloc", "vsie_apply_batched",
            "vsie_adjoint_apply", "vsie_plane_wave_rhs", "vsie_far_field", "vsie_solve",
-           "vsie_far_field_adjoint", "vsie_solve_batched",
+           "vsie_far_field_adjoint", "vsie_solve_batched", "vsie_apply_batched_multi",
+           "vsie_graph_create_batched", "vsie_graph_launch", "vsie_graph_nodes", "vsie_graph_destroy",
            "vsie_last_error")
 
 
@@ -108,10 +109,18 @@ def load_library(path: str = LIB_PATH):
     lib.vsie_solve.argtypes = [P, P, P, ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), P]
     lib.vsie_solve_batched.argtypes = [P, P, P, ctypes.c_int32, ctypes.POINTER(_SolveOpts),
                                        ctypes.POINTER(_SolveInfo), P]
+    lib.vsie_apply_batched_multi.argtypes = [ctypes.POINTER(P), I32, ctypes.POINTER(P), ctypes.POINTER(P),
+                                             I32, P]
+    lib.vsie_graph_create_batched.argtypes = [ctypes.POINTER(P), I32, ctypes.POINTER(P), ctypes.POINTER(P),
+                                              I32, ctypes.POINTER(P)]
+    lib.vsie_graph_launch.argtypes = [P, P]
+    lib.vsie_graph_nodes.argtypes = [P, ctypes.POINTER(I64)]
+    lib.vsie_graph_destroy.argtypes = [P]
+    lib.vsie_graph_destroy.restype = None
     lib.vsie_last_error.argtypes = []
     lib.vsie_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("vsie_destroy", "vsie_last_error"):
+        if name not in ("vsie_destroy", "vsie_last_error", "vsie_graph_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -333,3 +342,60 @@ class Operator:
             _check(st)
         return x, SolveInfo(st, info.iterations, info.refinements, info.rel_residual,
                             info.fp64_applies, info.fp32_applies)
+
+
+def _multi_arrays(ops, xs, ys):
+    if len(ops) != len(xs) or len(ops) != len(ys) or not ops:
+        raise ValueError("one input and one output block per operator")
+    nrhs = ops[0]._nrhs(xs[0])
+    for op, x, y in zip(ops, xs, ys):
+        if op._nrhs(x) != nrhs or tuple(y.shape) != tuple(x.shape):
+            raise ValueError("every block must have shape (nrhs, n) with the same nrhs")
+    P = ctypes.c_void_p
+    hs = (P * len(ops))(*[op._h for op in ops])
+    xa = (P * len(ops))(*[_dev(x, "x") for x in xs])
+    ya = (P * len(ops))(*[_dev(y, "y") for y in ys])
+    return hs, xa, ya, nrhs
+
+
+def apply_batched_multi(ops, xs, ys=None, stream=None):
+    """ys[p] = A_p xs[p] for operators of one mesh (e.g. several frequencies), with one
+    persistent tensor-core launch per source class for all of them (vsie_apply_batched_multi)."""
+    import torch
+    if ys is None:
+        ys = [torch.empty_like(x) for x in xs]
+    hs, xa, ya, nrhs = _multi_arrays(ops, xs, ys)
+    _check(_lib.vsie_apply_batched_multi(hs, len(ops), xa, ya, nrhs, _stream(stream)))
+    return ys
+
+
+class BatchedGraph:
+    """A CUDA-graph plan of apply_batched_multi for fixed operators and blocks
+    (vsie_graph_create_batched); ``launch()`` replays it (vsie_graph_launch)."""
+
+    def __init__(self, ops, xs, ys):
+        hs, xa, ya, nrhs = _multi_arrays(ops, xs, ys)
+        self._keep = (list(ops), list(xs), list(ys))  # the plan holds their device pointers
+        g = ctypes.c_void_p()
+        _check(_lib.vsie_graph_create_batched(hs, len(ops), xa, ya, nrhs, ctypes.byref(g)))
+        self._g = g
+
+    @property
+    def nodes(self) -> int:
+        n = ctypes.c_int64()
+        _check(_lib.vsie_graph_nodes(self._g, ctypes.byref(n)))
+        return n.value
+
+    def launch(self, stream=None):
+        _check(_lib.vsie_graph_launch(self._g, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_g", None) is not None and self._g.value:
+            _lib.vsie_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

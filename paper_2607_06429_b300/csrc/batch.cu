@@ -202,17 +202,23 @@ __device__ __forceinline__ void eval_pair2(float2 tx, float2 ty, float2 tz, floa
   cim = __fmul2_rn(g3, Q);
 }
 
+constexpr int BT_MAXP = 16;  // operators per persistent launch
+
+// One launch covers nprob operators with the same work shape (targets, source tiles): the
+// items (operator, target tile, chunk) are numbered operator-major, so that a global target
+// tile index G stands for tile G % ntile_t of operator G / ntile_t.
 struct BatchArgs {
-  const float4* tgt;        // kappa-scaled FP32 target positions (n)
-  const unsigned char* img; // per-source-tile images (n_src_tiles * BT_IMG bytes)
+  const float4* tgt[BT_MAXP];        // kappa-scaled FP32 target positions (nt) per operator
+  const unsigned char* img[BT_MAXP]; // per-source-tile images (ntiles_src * BT_IMG bytes)
+  double2* out[BT_MAXP];             // nt x nrhs_out column-major per operator
+  int nprob;
   int64_t nt;               // targets
   int64_t ntiles_src;       // source tiles
   int64_t ntile_t;          // target tiles
   int64_t nchunk;           // chunks of BT_CHUNK_TILES source tiles
-  int64_t nitems;
+  int64_t nitems;           // nprob * ntile_t * nchunk
   int64_t grid;
-  double2* out;             // n x nrhs_out column-major
-  int64_t ld_out;           // n
+  int64_t ld_out;           // nt
   int nrhs_out;             // columns written (<= BT_R)
   int mode;                 // 0 store, 1 add
   double* slots;            // [2 grid][2][BT_R][BT_M] FP64 partial target tiles for the fix-up
@@ -280,19 +286,23 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
       // copy cursor (runs up to NB - 1 tiles ahead of the MMA cursor)
       int64_t pk = k0, ps = 0, pend = 0;
       bool pstarted = false, pdone = false;
+      const unsigned char* pimg = nullptr;  // images of the current item's operator
+      auto pitem = [&]() {
+        ps = (pk % a.nchunk) * BT_CHUNK_TILES;
+        pend = min(a.ntiles_src, ps + BT_CHUNK_TILES);
+        pimg = a.img[(pk / a.nchunk) / a.ntile_t];
+      };
       auto pnext = [&]() -> int64_t {
         if (!pstarted) {
           pstarted = true;
           if (pk >= k1) return -1;
-          ps = (pk % a.nchunk) * BT_CHUNK_TILES;
-          pend = min(a.ntiles_src, ps + BT_CHUNK_TILES);
+          pitem();
           return ps;
         }
         if (pk >= k1) return -1;
         if (++ps < pend) return ps;
         if (++pk >= k1) return -1;
-        ps = (pk % a.nchunk) * BT_CHUNK_TILES;
-        pend = min(a.ntiles_src, ps + BT_CHUNK_TILES);
+        pitem();
         return ps;
       };
       uint32_t gp = 0;  // copies issued
@@ -308,7 +318,7 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
           if (gp >= BT_NB) err = !mbar_wait(mma_done + st2, ((gp - BT_NB) / BT_NB) & 1);
           if (err) break;
           unsigned char* bimg = smem + BT_B_OFF + st2 * BT_SIMG;
-          const unsigned char* gimg = a.img + s_next * (int64_t)BT_IMG;
+          const unsigned char* gimg = pimg + s_next * (int64_t)BT_IMG;
           ++gp;
           if (a.withhold_copies) continue;
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b_full + st2)),
@@ -443,8 +453,10 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
       const int64_t c0 = k - tile * a.nchunk;
       const int64_t c1 = min(a.nchunk, c0 + (k1 - k));
       const int64_t s_begin = c0 * BT_CHUNK_TILES, s_end = min(a.ntiles_src, c1 * BT_CHUNK_TILES);
-      const int64_t ti = tile * BT_M + m;
-      const float4 tp = ti < a.nt ? a.tgt[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int prob = (int)(tile / a.ntile_t);         // operator of this segment
+      const int64_t ltile = tile - (int64_t)prob * a.ntile_t;
+      const int64_t ti = ltile * BT_M + m;
+      const float4 tp = ti < a.nt ? a.tgt[prob][ti] : make_float4(0.f, 0.f, 0.f, 0.f);
       for (int64_t s = s_begin; s < s_end; ++s, ++g) {
         const int sb = g % BT_NB;
         unsigned char* simg = smem + BT_B_OFF + sb * BT_SIMG;
@@ -543,7 +555,8 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
         const bool complete = (c0 == 0 && c1 == a.nchunk);
         const bool other = (s_end - s_begin >= 2);
         const int64_t slot = (k == k0) ? 2 * b : 2 * b + 1;
-        const int64_t i = tile * BT_M + row;
+        const int64_t i = ltile * BT_M + row;
+        double2* outp = a.out[prob];
         const uint32_t dcol = tlane + BT_COL_D + 128 * (gl & 1) + 32 * cb;
         const uint32_t ocol = tlane + BT_COL_D + 128 * ((gl & 1) ^ 1) + 32 * cb;
         const uint32_t hcol = tlane + BT_COL_H + 32 * cb;
@@ -561,7 +574,7 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
             const int r = r0 + 8 * piece + q;
             if (complete) {
               if (i < a.nt && r < a.nrhs_out) {
-                double* op = reinterpret_cast<double*>(a.out + (int64_t)r * a.ld_out + i) + part;
+                double* op = reinterpret_cast<double*>(outp + (int64_t)r * a.ld_out + i) + part;
                 *op = a.mode ? *op + v : v;
               }
             } else {
@@ -593,13 +606,15 @@ __device__ __forceinline__ int64_t bt_block_of(const BatchArgs& a, int64_t k) {
 
 // adds the pieces of target tiles that span several CTAs, in CTA order
 __global__ void batch_fixup_kernel(BatchArgs a) {
-  const int64_t tile = blockIdx.x;
+  const int64_t tile = blockIdx.x;  // global target tile (operator-major)
+  const int prob = (int)(tile / a.ntile_t);
+  const int64_t ltile = tile - (int64_t)prob * a.ntile_t;
   const int64_t kf = tile * a.nchunk, kl = kf + a.nchunk - 1;
   const int64_t bs = bt_block_of(a, kf), be = bt_block_of(a, kl);
   if (bs == be) return;
   for (int e = threadIdx.x; e < BT_M * a.nrhs_out; e += blockDim.x) {
     const int row = e % BT_M, r = e / BT_M;
-    const int64_t i = tile * BT_M + row;
+    const int64_t i = ltile * BT_M + row;
     if (i >= a.nt) continue;
     double sr = 0.0, si = 0.0;
     for (int64_t bb = bs; bb <= be; ++bb) {
@@ -609,7 +624,7 @@ __global__ void batch_fixup_kernel(BatchArgs a) {
       sr += sp[(int64_t)r * BT_M + row];
       si += sp[(int64_t)(BT_R + r) * BT_M + row];
     }
-    double2* o = a.out + (int64_t)r * a.ld_out + i;
+    double2* o = a.out[prob] + (int64_t)r * a.ld_out + i;
     if (a.mode) {
       const double2 v = *o;
       *o = make_double2(v.x + sr, v.y + si);
@@ -680,80 +695,111 @@ __global__ void batch_images_kernel(const double4_32a* __restrict__ ps, const do
 
 // ----------------------------------------------------------------- host side
 
-static vsie_status batch_class(vsie_handle* h, const Sources& S, bool is_k, const double2* x, double2* y,
-                               int nrhs, int r_base, int mode, cudaStream_t st) {
-  if (!S.n || !h->n) return VSIE_OK;
-  const int64_t ntiles = (S.n + BT_S - 1) / BT_S;
+// Sets the kernels' shared-memory limit once per device (not during stream capture).
+static vsie_status tc_attributes(int device) {
+  static unsigned done = 0;  // bit per device
+  if (device < 32 && (done >> device) & 1u) return VSIE_OK;
+  VSIE_CUDA(cudaFuncSetAttribute(batch_tc_kernel<EvalK>, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
+  VSIE_CUDA(cudaFuncSetAttribute(batch_tc_kernel<EvalG>, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
+  if (device < 32) done |= 1u << device;
+  return VSIE_OK;
+}
+
+// The G (is_k false) or K class of nop operators with equal work shapes, right-hand sides
+// r_base .. r_base + 63 of each operator's block x[p] -> y[p]: per-operator charge images,
+// then one persistent tensor-core launch over all operators' items and one fix-up launch.
+static vsie_status batch_class_multi(vsie_handle* const* hs, int nop, bool is_k, const double2* const* x,
+                                     double2* const* y, int nrhs, int r_base, int mode, cudaStream_t st) {
+  vsie_handle* h0 = hs[0];
+  const Sources& S0 = is_k ? h0->K : h0->G;
+  if (!S0.n || !h0->n) return VSIE_OK;
+  const int64_t ntiles = (S0.n + BT_S - 1) / BT_S;
   const size_t img_bytes = (size_t)ntiles * BT_IMG;
-  if (h->batch.img_bytes < img_bytes) {
-    unsigned char* p = nullptr;
-    VSIE_TRY(dalloc_t(h, &p, img_bytes));
-    h->batch.img = p;
-    h->batch.img_bytes = img_bytes;
-  }
-  const double kap = h->k0 / (2.0 * kPi);
   const int64_t nthr = ntiles * BT_S * BT_R;
-  batch_images_kernel<<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(S.pos_s, S.aux, S.owner, S.n, x, h->n, nrhs,
-                                                                      r_base, kap, is_k ? 1 : 0, h->batch.img, ntiles);
-  VSIE_CUDA(cudaGetLastError());
-  BatchArgs a;
-  a.tgt = h->tgt32;
-  a.img = h->batch.img;
-  a.nt = h->n;
+  BatchArgs a{};
+  a.nprob = nop;
+  for (int p = 0; p < nop; ++p) {
+    vsie_handle* h = hs[p];
+    const Sources& S = is_k ? h->K : h->G;
+    if (h->batch.img_bytes < img_bytes) {
+      unsigned char* q = nullptr;
+      VSIE_TRY(dalloc_t(h, &q, img_bytes));
+      h->batch.img = q;
+      h->batch.img_bytes = img_bytes;
+    }
+    const double kap = h->k0 / (2.0 * kPi);
+    batch_images_kernel<<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(S.pos_s, S.aux, S.owner, S.n, x[p], h->n,
+                                                                        nrhs, r_base, kap, is_k ? 1 : 0,
+                                                                        h->batch.img, ntiles);
+    VSIE_CUDA(cudaGetLastError());
+    a.tgt[p] = h->tgt32;
+    a.img[p] = h->batch.img;
+    a.out[p] = y[p] + (int64_t)r_base * h->n;
+  }
+  a.nt = h0->n;
   a.ntiles_src = ntiles;
-  a.ntile_t = (h->n + BT_M - 1) / BT_M;
+  a.ntile_t = (h0->n + BT_M - 1) / BT_M;
   a.nchunk = (ntiles + BT_CHUNK_TILES - 1) / BT_CHUNK_TILES;
-  a.nitems = a.ntile_t * a.nchunk;
-  a.grid = std::max<int64_t>(1, std::min<int64_t>(h->num_sms > 0 ? h->num_sms : 148, a.nitems));
-  a.out = y + (int64_t)r_base * h->n;
-  a.ld_out = h->n;
+  a.nitems = (int64_t)nop * a.ntile_t * a.nchunk;
+  a.grid = std::max<int64_t>(1, std::min<int64_t>(h0->num_sms > 0 ? h0->num_sms : 148, a.nitems));
+  a.ld_out = h0->n;
   a.nrhs_out = std::min(BT_R, nrhs - r_base);
   a.mode = mode;
   const size_t slot_elems = (size_t)(2 * a.grid) * 2 * BT_M * BT_R;
-  if (h->batch.slot_elems < slot_elems) {
-    double* p = nullptr;
-    VSIE_TRY(dalloc_t(h, &p, slot_elems));
-    h->batch.slots = p;
-    h->batch.slot_elems = slot_elems;
+  if (h0->batch.slot_elems < slot_elems) {
+    double* q = nullptr;
+    VSIE_TRY(dalloc_t(h0, &q, slot_elems));
+    h0->batch.slots = q;
+    h0->batch.slot_elems = slot_elems;
   }
-  a.slots = h->batch.slots;
-  if (!h->batch.status) {
-    VSIE_TRY(dalloc_t(h, &h->batch.status, 1));
-    VSIE_CUDA(cudaMemsetAsync(h->batch.status, 0, sizeof(int), st));
+  a.slots = h0->batch.slots;
+  if (!h0->batch.status) {
+    VSIE_TRY(dalloc_t(h0, &h0->batch.status, 1));
+    VSIE_CUDA(cudaMemsetAsync(h0->batch.status, 0, sizeof(int), st));
   }
-  a.status = h->batch.status;
-  a.withhold_copies = (h->debug_flags & 1) ? 1 : 0;
-  if (is_k) {
-    VSIE_CUDA(cudaFuncSetAttribute(batch_tc_kernel<EvalK>, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
+  a.status = h0->batch.status;
+  a.withhold_copies = (h0->debug_flags & 1) ? 1 : 0;
+  VSIE_TRY(tc_attributes(h0->device));
+  if (is_k)
     batch_tc_kernel<EvalK><<<(unsigned)a.grid, BT_ALL_THREADS, BT_SMEM, st>>>(a);
-  } else {
-    VSIE_CUDA(cudaFuncSetAttribute(batch_tc_kernel<EvalG>, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
+  else
     batch_tc_kernel<EvalG><<<(unsigned)a.grid, BT_ALL_THREADS, BT_SMEM, st>>>(a);
-  }
   VSIE_CUDA(cudaGetLastError());
-  batch_fixup_kernel<<<(unsigned)a.ntile_t, 256, 0, st>>>(a);
+  batch_fixup_kernel<<<(unsigned)(nop * a.ntile_t), 256, 0, st>>>(a);
   VSIE_CUDA(cudaGetLastError());
   return VSIE_OK;
 }
 
-// y[:, r] = (far-field sums over the G and K classes) for all columns r, 64 at a time
-vsie_status far_batched_gk(vsie_handle* h, const double2* x, double2* y, int nrhs, cudaStream_t st) {
-  for (int r0 = 0; r0 < nrhs; r0 += BT_R) {
-    int mode = 0;
-    if (h->G.n) {
-      VSIE_TRY(batch_class(h, h->G, false, x, y, nrhs, r0, mode, st));
-      mode = 1;
-    }
-    if (h->K.n) {
-      VSIE_TRY(batch_class(h, h->K, true, x, y, nrhs, r0, mode, st));
-      mode = 1;
-    }
-    if (!mode) {
-      const int cols = std::min(BT_R, nrhs - r0);
-      VSIE_CUDA(cudaMemsetAsync(y + (int64_t)r0 * h->n, 0, sizeof(double2) * h->n * cols, st));
+// y[p][:, r] = (far-field sums over the G and K classes of operator p) for all columns r,
+// 64 at a time, up to BT_MAXP operators per launch; the operators must have equal numbers
+// of collocation points and of G and K sources.
+vsie_status far_batched_gk_multi(vsie_handle* const* hs, int nop, const double2* const* x, double2* const* y,
+                                 int nrhs, cudaStream_t st) {
+  for (int p0 = 0; p0 < nop; p0 += BT_MAXP) {
+    const int np = std::min(BT_MAXP, nop - p0);
+    vsie_handle* h0 = hs[p0];
+    for (int r0 = 0; r0 < nrhs; r0 += BT_R) {
+      int mode = 0;
+      if (h0->G.n) {
+        VSIE_TRY(batch_class_multi(hs + p0, np, false, x + p0, y + p0, nrhs, r0, mode, st));
+        mode = 1;
+      }
+      if (h0->K.n) {
+        VSIE_TRY(batch_class_multi(hs + p0, np, true, x + p0, y + p0, nrhs, r0, mode, st));
+        mode = 1;
+      }
+      if (!mode) {
+        const int cols = std::min(BT_R, nrhs - r0);
+        for (int p = 0; p < np; ++p)
+          VSIE_CUDA(cudaMemsetAsync(y[p0 + p] + (int64_t)r0 * h0->n, 0, sizeof(double2) * h0->n * cols, st));
+      }
     }
   }
   return VSIE_OK;
+}
+
+vsie_status far_batched_gk(vsie_handle* h, const double2* x, double2* y, int nrhs, cudaStream_t st) {
+  return far_batched_gk_multi(&h, 1, &x, &y, nrhs, st);
 }
 
 vsie_status batch_status(vsie_handle* h, cudaStream_t st) {

@@ -4,38 +4,47 @@
 //
 // Same sums as the FP64 single-column path (Eq. vsie; G and K source classes, positions
 // scaled by kappa = k0/(2 pi), phase in revolutions), but each kernel coefficient C(x_i, y_j)
-// is evaluated once and applied to a block of up to 64 right-hand sides:
+// is evaluated once (in FP64) and applied to a block of up to 64 right-hand sides:
 //     Y[i, r] = sum_j C(x_i, y_j) q_j^(r).
-// One block owns 64 targets x 64 right-hand sides; per tile of 32 sources its 256 threads
-// evaluate the 2048 coefficients into shared memory (8 per thread, own target), then each
-// thread accumulates its target against 16 right-hand sides (16 complex FP64 accumulators),
-// reading the charges as warp-wide broadcasts.  The FP64 pipe (1/64 of the FP32 rate on
-// B300) bounds the kernel: 4 DFMA per pair and right-hand side plus the amortised
-// coefficient evaluation.  Source ranges are split over blockIdx.y when the target blocks
-// alone do not fill the GPU; the partial sums are added in split order (deterministic).
+// One block owns 32 targets x 64 right-hand sides; per tile of 32 sources its 256 threads
+// evaluate the 1024 coefficients into shared memory (4 per thread, own target), then each
+// thread accumulates its target (its lane) against 8 right-hand sides (its warp's), reading
+// the charges as warp-wide broadcasts.  The contraction runs in double-float arithmetic on the FP32 pipe
+// (coefficients and charges as hi + lo float pairs, TwoProduct / TwoSum, about 48 bits):
+// B300's FP64 pipe runs at 1/64 of the FP32 rate, so 4 DFMA per pair and right-hand side
+// would cost five times the double-float multiply-add.  Source ranges are split over
+// blockIdx.y when the target blocks alone do not fill the GPU; the partial sums are added
+// in split order (deterministic).
 
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
+#include "dfloat.h"
 #include "vsie_internal.h"
 
 namespace vsie {
 
 namespace {
 
-constexpr int B64_T = 64;        // targets per block
+constexpr int B64_T = 32;        // targets per block (one per lane)
 constexpr int B64_S = 32;        // sources per tile
 constexpr int B64_R = 64;        // right-hand sides per launch
 constexpr int B64_THREADS = 256;
-constexpr int B64_RPT = B64_R / (B64_THREADS / B64_T);  // right-hand sides per thread (16)
-constexpr size_t B64_SMEM = sizeof(double4_32a) * 2 * B64_S + sizeof(double2) * 2 * B64_S * B64_T;
+constexpr int B64_RPT = B64_R / (B64_THREADS / B64_T);  // right-hand sides per thread (8)
+// shared memory: source positions and normals, then the coefficient tile [S][T], then the
+// charge tile [S][R]
+constexpr size_t B64_SMEM_P = sizeof(double4_32a) * 2 * B64_S;
+constexpr size_t B64_SMEM_C = sizeof(float4) * B64_S * B64_T;
+constexpr size_t B64_SMEM_Q = sizeof(float4) * B64_S * B64_R;
+constexpr size_t B64_SMEM = B64_SMEM_P + B64_SMEM_C + B64_SMEM_Q;
+static_assert(B64_SMEM <= 227 * 1024 && B64_SMEM_P % 16 == 0, "shared memory layout");
 
 struct B64Args {
   const double4_32a* tgt;   // collocation points (FP64)
   const double4_32a* pos;   // source (x, y, z, s)
   const double4_32a* nrm;   // source (nx, ny, nz, sigma) (K class)
-  const double2* q;         // charges [source][B64_R]
+  const float4* q;          // charges [source][B64_R], double-float
   double kap;
   int64_t nt, ns, ntiles;
   int nsplit;
@@ -67,10 +76,10 @@ __device__ __forceinline__ double2 coef64(double tx, double ty, double tz, const
 template <bool IsK>
 __global__ void __launch_bounds__(B64_THREADS, 2) b64_kernel(B64Args a) {
   extern __shared__ __align__(16) unsigned char sm[];
-  double4_32a* sp = reinterpret_cast<double4_32a*>(sm);            // kappa-scaled positions
-  double4_32a* sn = sp + B64_S;                                     // normals (K)
-  double2* sC = reinterpret_cast<double2*>(sn + B64_S);            // [S][T] coefficients
-  double2* sQ = sC + B64_S * B64_T;                                 // [S][R] charges
+  double4_32a* sp = reinterpret_cast<double4_32a*>(sm);                  // kappa-scaled positions
+  double4_32a* sn = sp + B64_S;                                           // normals (K)
+  float4* sC = reinterpret_cast<float4*>(sm + B64_SMEM_P);               // [S][T] coefficients (double-float)
+  float4* sQ = reinterpret_cast<float4*>(sm + B64_SMEM_P + B64_SMEM_C);  // [S][R] charges (double-float)
   const int tid = threadIdx.x;
   const int t = tid & (B64_T - 1), rg = tid / B64_T;
   const int64_t i = (int64_t)blockIdx.x * B64_T + t;
@@ -82,9 +91,9 @@ __global__ void __launch_bounds__(B64_THREADS, 2) b64_kernel(B64Args a) {
     ty = p.y * a.kap;
     tz = p.z * a.kap;
   }
-  double2 acc[B64_RPT];
+  float2 accS[B64_RPT], accC[B64_RPT];  // double-float sums: hi parts, collected rounding errors
 #pragma unroll
-  for (int r = 0; r < B64_RPT; ++r) acc[r] = make_double2(0.0, 0.0);
+  for (int r = 0; r < B64_RPT; ++r) accS[r] = accC[r] = make_float2(0.0f, 0.0f);
   const int sp_i = blockIdx.y;
   const int64_t tile0 = (a.ntiles * sp_i) / a.nsplit, tile1 = (a.ntiles * (sp_i + 1)) / a.nsplit;
   for (int64_t tile = tile0; tile < tile1; ++tile) {
@@ -103,37 +112,36 @@ __global__ void __launch_bounds__(B64_THREADS, 2) b64_kernel(B64Args a) {
     }
     for (int e = tid; e < B64_S * B64_R; e += B64_THREADS) {
       const int64_t j = j0 + e / B64_R;
-      sQ[e] = (j < a.ns) ? a.q[j0 * B64_R + e] : make_double2(0.0, 0.0);
+      sQ[e] = (j < a.ns) ? a.q[j0 * B64_R + e] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     __syncthreads();
 #pragma unroll 2
     for (int q = 0; q < B64_S / (B64_THREADS / B64_T); ++q) {
       const int jj = rg + (B64_THREADS / B64_T) * q;
-      sC[jj * B64_T + t] = coef64<IsK>(tx, ty, tz, sp[jj], sn[jj]);
+      sC[jj * B64_T + t] = df_pack(coef64<IsK>(tx, ty, tz, sp[jj], sn[jj]));
     }
     __syncthreads();
-#pragma unroll 4
+#pragma unroll 1
     for (int jj = 0; jj < B64_S; ++jj) {
-      const double2 c = sC[jj * B64_T + t];
-      const double2* qr = sQ + jj * B64_R + rg * B64_RPT;
+      const float4 c = sC[jj * B64_T + t];
+      const float4* qr = sQ + jj * B64_R + rg * B64_RPT;
 #pragma unroll
-      for (int r = 0; r < B64_RPT; ++r) {
-        const double2 qv = qr[r];
-        acc[r].x = fma(c.x, qv.x, fma(-c.y, qv.y, acc[r].x));
-        acc[r].y = fma(c.x, qv.y, fma(c.y, qv.x, acc[r].y));
-      }
+      for (int r = 0; r < B64_RPT; ++r) df_cmac(accS[r], accC[r], c, qr[r]);
     }
+#pragma unroll
+    for (int r = 0; r < B64_RPT; ++r) df_renorm2(accS[r], accC[r]);
   }
   if (!tok) return;
 #pragma unroll
   for (int r = 0; r < B64_RPT; ++r) {
     const int rr = rg * B64_RPT + r;
     if (rr >= a.nrhs_out) continue;
+    const double2 v = df_value(accS[r], accC[r]);
     if (a.nsplit == 1) {
       double2* o = a.out + (int64_t)rr * a.ld_out + i;
-      *o = a.mode ? make_double2(o->x + acc[r].x, o->y + acc[r].y) : acc[r];
+      *o = a.mode ? make_double2(o->x + v.x, o->y + v.y) : v;
     } else {
-      a.part[((int64_t)sp_i * B64_R + rr) * a.nt + i] = acc[r];
+      a.part[((int64_t)sp_i * B64_R + rr) * a.nt + i] = v;
     }
   }
 }
@@ -158,7 +166,7 @@ __global__ void b64_reduce_kernel(B64Args a) {
 __global__ void b64_charges_kernel(const double4_32a* __restrict__ pos, const double4_32a* __restrict__ aux,
                                    const int32_t* __restrict__ own, int64_t ns, const double2* __restrict__ x,
                                    int64_t ld_x, int nrhs, int r_base, double kap, int is_k,
-                                   double2* __restrict__ q) {
+                                   float4* __restrict__ q) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ns * B64_R) return;
   const int r = (int)(e % B64_R);
@@ -170,7 +178,7 @@ __global__ void b64_charges_kernel(const double4_32a* __restrict__ pos, const do
     const double2 p = x[(int64_t)rr * ld_x + own[j]];
     v = make_double2(sc * p.x, sc * p.y);
   }
-  q[e] = v;
+  q[e] = df_pack(v);
 }
 
 vsie_status b64_class(vsie_handle* h, const Sources& S, bool is_k, const double2* x, double2* y, int nrhs,
@@ -178,7 +186,7 @@ vsie_status b64_class(vsie_handle* h, const Sources& S, bool is_k, const double2
   const int64_t n = h->n;
   const size_t qn = (size_t)S.n * B64_R;
   if (h->batch.q64_elems < qn) {
-    double2* p = nullptr;
+    float4* p = nullptr;
     VSIE_TRY(dalloc_t(h, &p, qn));
     h->batch.q64 = p;
     h->batch.q64_elems = qn;

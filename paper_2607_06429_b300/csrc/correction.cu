@@ -12,10 +12,11 @@
 //     layer split as G = G_0 + (G - G_0), the Laplace part integrated exactly through the
 //     signed solid angle (Van Oosterom & Strackee), the bounded remainder by the
 //     three-point rule; a triangle on its own centroid takes the principal value 0.
-// Entry = accurate value - far-rule value.  Two value arrays are kept: val64 subtracts
-// the far-rule value from the FP64 coordinates (used with the FP64 far sum), val32 from
-// the FP32 coordinates the FP32 far sum sees (float(kappa x)), so that near-singular pairs cancel
-// to FP32 arithmetic error rather than to coordinate-rounding error.
+// Entry = accurate value - far-rule value, computed in FP64 and stored as double-float
+// pairs.  Two value arrays are kept: val64 subtracts the far-rule value from the FP64
+// coordinates (used with the FP64 far sum), val32 from the FP32 coordinates the FP32 far
+// sum sees (float(kappa x)), so that near-singular pairs cancel to FP32 arithmetic error
+// rather than to coordinate-rounding error.
 //
 // Neighbour search: uniform cell grids (cell >= radius) over tetrahedron and triangle
 // centroids, sorted by cell with thrust; each target scans its 27 neighbouring cells.
@@ -32,6 +33,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "dfloat.h"
 #include "vsie_internal.h"
 
 namespace vsie {
@@ -283,27 +285,51 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// y_i += m_i x_i + sum_k Delta_ik x_col(k); one warp per row, fixed summation order.
-__global__ void corr_apply_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                  const double2* __restrict__ val, const double* __restrict__ mass,
-                                  const double2* __restrict__ x, double2* __restrict__ y, int64_t n) {
+// The correction values are stored as double-float complex numbers (re.hi, im.hi, re.lo,
+// im.lo): 16 bytes per entry like complex128, about 48 significant bits, so that the
+// multiply-adds run on the FP32 pipe (dfloat.h) instead of B300's 1/64-rate FP64 pipe and
+// the SpMV becomes bound by HBM bandwidth.
+
+// complex128 -> double-float, in place (each 16-byte entry rewritten by the thread that reads it)
+__global__ void to_df_inplace_kernel(double2* __restrict__ v, int64_t m) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const float4 d = df_pack(v[i]);
+  reinterpret_cast<float4*>(v)[i] = d;
+}
+
+__global__ void to_df_kernel(const double2* __restrict__ x, float4* __restrict__ xd, int64_t m) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) xd[i] = df_pack(x[i]);
+}
+
+__device__ __forceinline__ float2 shfl_down2(float2 v, int o) {
+  return make_float2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
+}
+
+// y_i += m_i x_i + sum_k Delta_ik x_col(k); one warp per row, lanes strided over the row's
+// entries (coalesced value and column loads), double-float products and sums, a fixed
+// reduction order (deterministic); xd is x in double-float.
+__global__ void __launch_bounds__(256) corr_apply_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                         const float4* __restrict__ val, const double* __restrict__ mass,
+                                                         const float4* __restrict__ xd, const double2* __restrict__ x,
+                                                         double2* __restrict__ y, int64_t n) {
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
-  double ar = 0.0, ai = 0.0;
-  for (int64_t p = rp[row] + lane; p < rp[row + 1]; p += 32) {
-    const double2 v = val[p];
-    const double2 q = x[col[p]];
-    ar += v.x * q.x - v.y * q.y;
-    ai += v.x * q.y + v.y * q.x;
-  }
-  ar = warp_sum(ar);
-  ai = warp_sum(ai);
+  float2 S = make_float2(0.0f, 0.0f), C = S;
+  const int64_t pe = rp[row + 1];
+#pragma unroll 4
+  for (int64_t p = rp[row] + lane; p < pe; p += 32) df_cmac(S, C, val[p], xd[col[p]]);
+  df_renorm2(S, C);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) df_add2(S, C, shfl_down2(S, o), shfl_down2(C, o));
   if (lane == 0) {
+    const double2 d = df_value(S, C);
     const double m = mass[row];
     const double2 q = x[row];
     const double2 o = y[row];
-    y[row] = make_double2(o.x + m * q.x + ar, o.y + m * q.y + ai);
+    y[row] = make_double2(o.x + m * q.x + d.x, o.y + m * q.y + d.y);
   }
 }
 
@@ -320,26 +346,29 @@ __global__ void mass_adjoint_kernel(const double* __restrict__ mass, const doubl
 
 // x_col += conj(Delta_ik) lam_i (scatter with FP64 atomics)
 __global__ void corr_adjoint_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                    const double2* __restrict__ val, const double2* __restrict__ lam,
+                                    const float4* __restrict__ val, const double2* __restrict__ lam,
                                     double2* __restrict__ x, int64_t n) {
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   const double2 l = lam[row];
   for (int64_t p = rp[row] + lane; p < rp[row + 1]; p += 32) {
-    const double2 v = val[p];
+    const float4 d = val[p];
+    const double vr = (double)d.x + (double)d.z, vi = (double)d.y + (double)d.w;
     double* dst = reinterpret_cast<double*>(x + col[p]);
-    atomicAdd(dst, v.x * l.x + v.y * l.y);
-    atomicAdd(dst + 1, v.x * l.y - v.y * l.x);
+    atomicAdd(dst, vr * l.x + vi * l.y);
+    atomicAdd(dst + 1, vr * l.y - vi * l.x);
   }
 }
 
 vsie_status correction_apply(vsie_handle* h, const double2* x, double2* y, int precision,
                              cudaStream_t st) {
   const int64_t n = h->n;
-  const double2* val = precision == 32 ? h->C.val32 : h->C.val64;
+  if (n == 0) return VSIE_OK;
+  const float4* val = precision == 32 ? h->C.val32 : h->C.val64;
+  to_df_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, h->C.xd, n);
   const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
-  corr_apply_kernel<<<blocks, 256, 0, st>>>(h->C.row_ptr, h->C.col, val, h->mass, x, y, n);
+  corr_apply_kernel<<<blocks, 256, 0, st>>>(h->C.row_ptr, h->C.col, val, h->mass, h->C.xd, x, y, n);
   VSIE_CUDA(cudaGetLastError());
   return VSIE_OK;
 }
@@ -347,7 +376,7 @@ vsie_status correction_apply(vsie_handle* h, const double2* x, double2* y, int p
 vsie_status correction_adjoint(vsie_handle* h, const double2* lam, double2* x, int precision,
                                cudaStream_t st) {
   const int64_t n = h->n;
-  const double2* val = precision == 32 ? h->C.val32 : h->C.val64;
+  const float4* val = precision == 32 ? h->C.val32 : h->C.val64;
   mass_adjoint_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(h->mass, lam, x, n);
   corr_adjoint_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(h->C.row_ptr, h->C.col, val,
                                                                           lam, x, n);
@@ -357,23 +386,22 @@ vsie_status correction_adjoint(vsie_handle* h, const double2* lam, double2* x, i
 
 // ----------------------------------------------------------------- block application
 
-// xt[c][r] = x[r][c] for a block of up to 64 columns starting at column r_base: row-major,
-// 64 entries per row (zero past the block), as float2 (FP32 path) or double2 (FP64 path).
-// 32 x 32 tiles through shared memory, so both the reads and the writes are coalesced.
-template <class T2>
-__device__ __forceinline__ T2 to_t2(double2 v);
+// xt[c][r] = x[r][c] for a block of up to 64 columns: row-major, 64 entries per row (zero
+// past the block), as float2 (FP32 path) or double-float float4 (FP64 path).  32 x 32
+// tiles through shared memory, so both the reads and the writes are coalesced.
+template <class T>
+__device__ __forceinline__ T to_row(double2 v);
 template <>
-__device__ __forceinline__ float2 to_t2<float2>(double2 v) {
+__device__ __forceinline__ float2 to_row<float2>(double2 v) {
   return make_float2((float)v.x, (float)v.y);
 }
 template <>
-__device__ __forceinline__ double2 to_t2<double2>(double2 v) {
-  return v;
+__device__ __forceinline__ float4 to_row<float4>(double2 v) {
+  return df_pack(v);
 }
 
-template <class T2>
-__global__ void corr_transpose_kernel(const double2* __restrict__ x, int64_t n, int ncols,
-                                      T2* __restrict__ xt) {
+template <class T>
+__global__ void corr_transpose_kernel(const double2* __restrict__ x, int64_t n, int ncols, T* __restrict__ xt) {
   __shared__ double2 tile[32][33];
   const int64_t c0 = (int64_t)blockIdx.x * 32;
   const int r0 = blockIdx.y * 32;
@@ -385,16 +413,11 @@ __global__ void corr_transpose_kernel(const double2* __restrict__ x, int64_t n, 
   __syncthreads();
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
     const int64_t c = c0 + k;
-    if (c < n) xt[c * 64 + r0 + threadIdx.x] = to_t2<T2>(tile[threadIdx.x][k]);
+    if (c < n) xt[c * 64 + r0 + threadIdx.x] = to_row<T>(tile[threadIdx.x][k]);
   }
 }
 
-__global__ void to_float2_kernel(const double2* __restrict__ v, float2* __restrict__ o, int64_t m) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < m) o[i] = make_float2((float)v[i].x, (float)v[i].y);
-}
-
-// Kahan step for the (re, im) pair: s + c carries the sum, c the negated lost low part
+// Kahan step for the (re, im) pair: s - c carries the sum, c the lost low part
 __device__ __forceinline__ void kahan2(float2& s, float2& c, float2 p) {
   const float2 yv = __fadd2_rn(p, make_float2(-c.x, -c.y));
   const float2 t = __fadd2_rn(s, yv);
@@ -404,26 +427,27 @@ __device__ __forceinline__ void kahan2(float2& s, float2& c, float2 p) {
 
 // y[r][i] += m_i x[r][i] + sum_k Delta_ik x[r][col_k] for the ncols columns of a block:
 // one warp per row i, lane l owns columns l and l + 32.  The row's (value, column) pairs are
-// loaded 32 at a time (coalesced) and broadcast by shuffles; each nonzero then costs one
-// coalesced read of the charge row xt[col] (256 or 512 bytes, L2-resident for mid-size
-// meshes).  FP32 path: FP32 products, Kahan-compensated sums; FP64 path: FP64 throughout.
-template <class T2>
+// loaded 32 at a time (coalesced) and broadcast by shuffles; each entry then costs one
+// coalesced read of the charge row xt[col] (256 or 1024 bytes, L2-resident for mid-size
+// meshes).  FP32 path (T = float2): the values' high parts, FP32 products, Kahan-compensated
+// sums.  FP64 path (T = float4): double-float products and sums.
+template <class T>
 __global__ void __launch_bounds__(256) corr_block_kernel(const int64_t* __restrict__ rp,
                                                          const int32_t* __restrict__ col,
-                                                         const T2* __restrict__ val,
+                                                         const float4* __restrict__ val,
                                                          const double* __restrict__ mass,
-                                                         const T2* __restrict__ xt,
+                                                         const T* __restrict__ xt,
                                                          const double2* __restrict__ x,
                                                          double2* __restrict__ y, int64_t n, int ncols) {
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
-  constexpr bool kF32 = sizeof(T2) == 8;
-  T2 s0{}, s1{}, c0{}, c1{};
+  constexpr bool kDF = sizeof(T) == 16;
+  float2 s0 = make_float2(0.0f, 0.0f), s1 = s0, c0 = s0, c1 = s0;
   const int64_t pb = rp[row], pe = rp[row + 1];
   for (int64_t p0 = pb; p0 < pe; p0 += 32) {
     const int cnt = (int)min((int64_t)32, pe - p0);
-    T2 mv{};
+    float4 mv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     int32_t mc = 0;
     if (lane < cnt) {
       mv = val[p0 + lane];
@@ -431,20 +455,26 @@ __global__ void __launch_bounds__(256) corr_block_kernel(const int64_t* __restri
     }
 #pragma unroll 4
     for (int q = 0; q < cnt; ++q) {
-      T2 v;
+      float4 v;
       v.x = __shfl_sync(0xffffffffu, mv.x, q);
       v.y = __shfl_sync(0xffffffffu, mv.y, q);
+      if constexpr (kDF) {
+        v.z = __shfl_sync(0xffffffffu, mv.z, q);
+        v.w = __shfl_sync(0xffffffffu, mv.w, q);
+      }
       const int32_t cc = __shfl_sync(0xffffffffu, mc, q);
-      const T2 a = xt[(int64_t)cc * 64 + lane], b = xt[(int64_t)cc * 64 + lane + 32];
-      if constexpr (kF32) {
+      const T a = xt[(int64_t)cc * 64 + lane], b = xt[(int64_t)cc * 64 + lane + 32];
+      if constexpr (kDF) {
+        df_cmac(s0, c0, v, a);
+        df_cmac(s1, c1, v, b);
+      } else {
         kahan2(s0, c0, make_float2(fmaf(v.x, a.x, -v.y * a.y), fmaf(v.x, a.y, v.y * a.x)));
         kahan2(s1, c1, make_float2(fmaf(v.x, b.x, -v.y * b.y), fmaf(v.x, b.y, v.y * b.x)));
-      } else {
-        s0.x = fma(v.x, a.x, fma(-v.y, a.y, s0.x));
-        s0.y = fma(v.x, a.y, fma(v.y, a.x, s0.y));
-        s1.x = fma(v.x, b.x, fma(-v.y, b.y, s1.x));
-        s1.y = fma(v.x, b.y, fma(v.y, b.x, s1.y));
       }
+    }
+    if constexpr (kDF) {
+      df_renorm2(s0, c0);
+      df_renorm2(s1, c1);
     }
   }
   const double m = mass[row];
@@ -452,12 +482,12 @@ __global__ void __launch_bounds__(256) corr_block_kernel(const int64_t* __restri
   for (int h = 0; h < 2; ++h) {
     const int r = lane + 32 * h;
     if (r >= ncols) continue;
-    const T2 sv = h ? s1 : s0, cv = h ? c1 : c0;
-    const double ar = (double)sv.x - (double)cv.x, ai = (double)sv.y - (double)cv.y;
+    const float2 sv = h ? s1 : s0, cv = h ? c1 : c0;
+    const double2 d = kDF ? df_value(sv, cv) : make_double2((double)sv.x - (double)cv.x, (double)sv.y - (double)cv.y);
     const double2 q = x[(int64_t)r * n + row];
     double2* o = y + (int64_t)r * n + row;
     const double2 ov = *o;
-    *o = make_double2(ov.x + m * q.x + ar, ov.y + m * q.y + ai);
+    *o = make_double2(ov.x + m * q.x + d.x, ov.y + m * q.y + d.y);
   }
 }
 
@@ -465,17 +495,12 @@ vsie_status correction_apply_block(vsie_handle* h, const double2* x, double2* y,
                                    cudaStream_t st) {
   const int64_t n = h->n;
   if (n == 0 || ncols < 1) return VSIE_OK;
-  const size_t xt_bytes = (size_t)n * 64 * (precision == 32 ? sizeof(float2) : sizeof(double2));
+  const size_t xt_bytes = (size_t)n * 64 * (precision == 32 ? sizeof(float2) : sizeof(float4));
   if (h->batch.xt_bytes < xt_bytes) {
     unsigned char* p = nullptr;
     VSIE_TRY(dalloc_t(h, &p, xt_bytes));
     h->batch.xt = p;
     h->batch.xt_bytes = xt_bytes;
-  }
-  if (precision == 32 && !h->C.val32f && h->C.nnz > 0) {
-    VSIE_TRY(dalloc_t(h, &h->C.val32f, (size_t)h->C.nnz));
-    to_float2_kernel<<<(unsigned)((h->C.nnz + 255) / 256), 256, 0, st>>>(h->C.val32, h->C.val32f, h->C.nnz);
-    VSIE_CUDA(cudaGetLastError());
   }
   const dim3 tgrid((unsigned)((n + 31) / 32), 2), tblock(32, 8);
   const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
@@ -486,13 +511,13 @@ vsie_status correction_apply_block(vsie_handle* h, const double2* x, double2* y,
     if (precision == 32) {
       float2* xt = reinterpret_cast<float2*>(h->batch.xt);
       corr_transpose_kernel<float2><<<tgrid, tblock, 0, st>>>(xb, n, nc, xt);
-      corr_block_kernel<float2><<<blocks, 256, 0, st>>>(h->C.row_ptr, h->C.col, h->C.val32f, h->mass, xt, xb, yb,
+      corr_block_kernel<float2><<<blocks, 256, 0, st>>>(h->C.row_ptr, h->C.col, h->C.val32, h->mass, xt, xb, yb,
                                                          n, nc);
     } else {
-      double2* xt = reinterpret_cast<double2*>(h->batch.xt);
-      corr_transpose_kernel<double2><<<tgrid, tblock, 0, st>>>(xb, n, nc, xt);
-      corr_block_kernel<double2><<<blocks, 256, 0, st>>>(h->C.row_ptr, h->C.col, h->C.val64, h->mass, xt, xb,
-                                                          yb, n, nc);
+      float4* xt = reinterpret_cast<float4*>(h->batch.xt);
+      corr_transpose_kernel<float4><<<tgrid, tblock, 0, st>>>(xb, n, nc, xt);
+      corr_block_kernel<float4><<<blocks, 256, 0, st>>>(h->C.row_ptr, h->C.col, h->C.val64, h->mass, xt, xb, yb,
+                                                         n, nc);
     }
     VSIE_CUDA(cudaGetLastError());
   }
@@ -614,15 +639,23 @@ vsie_status build_correction(vsie_handle* h, const double4_32a* d_tet_cen, const
     return cuda_fail(e, "cudaMemcpy(nnz)", __FILE__, __LINE__);
   }
   h->C.nnz = nnz;
-  if ((s = dalloc_t(h, &h->C.col, (size_t)nnz)) != VSIE_OK ||
-      (s = dalloc_t(h, &h->C.val64, (size_t)nnz)) != VSIE_OK ||
-      (s = dalloc_t(h, &h->C.val32, (size_t)nnz)) != VSIE_OK) {
+  double2 *v64 = nullptr, *v32 = nullptr;
+  if ((s = dalloc_t(h, &h->C.col, (size_t)nnz)) != VSIE_OK || (s = dalloc_t(h, &v64, (size_t)nnz)) != VSIE_OK ||
+      (s = dalloc_t(h, &v32, (size_t)nnz)) != VSIE_OK || (s = dalloc_t(h, &h->C.xd, (size_t)n)) != VSIE_OK) {
     cleanup();
     return s;
   }
-  corr_rows_kernel<<<blocks, 128>>>(in, h->C.row_ptr, nullptr, h->C.col, h->C.val64, h->C.val32, 1);
+  corr_rows_kernel<<<blocks, 128>>>(in, h->C.row_ptr, nullptr, h->C.col, v64, v32, 1);
   e = cudaGetLastError();
+  if (e == cudaSuccess && nnz > 0) {
+    // the FP64 values become double-float pairs in place (16 bytes each either way)
+    to_df_inplace_kernel<<<(unsigned)((nnz + 255) / 256), 256>>>(v64, nnz);
+    to_df_inplace_kernel<<<(unsigned)((nnz + 255) / 256), 256>>>(v32, nnz);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  h->C.val64 = reinterpret_cast<float4*>(v64);
+  h->C.val32 = reinterpret_cast<float4*>(v32);
   cleanup();
   if (e != cudaSuccess) return cuda_fail(e, "corr_rows_kernel(fill)", __FILE__, __LINE__);
   return VSIE_OK;

@@ -508,15 +508,71 @@ extern "C" vsie_status vsie_apply_batched(vsie_handle* h, const void* d_x, void*
   cudaStream_t st = (cudaStream_t)stream;
   const double2* x = (const double2*)d_x;
   double2* y = (double2*)d_y;
-  if (precision == 32)
-    VSIE_TRY(far_batched_gk(h, x, y, nrhs, st));
-  else
-    VSIE_TRY(far_batched64_gk(h, x, y, nrhs, st));
+  if (precision == 32) {
+    VSIE_TRY(apply_batched_multi_launch(&h, 1, &x, &y, nrhs, st));
+    return batch_status(h, st);
+  }
+  VSIE_TRY(far_batched64_gk(h, x, y, nrhs, st));
   if (h->F.n)
     for (int r = 0; r < nrhs; ++r)
-      VSIE_TRY(far_sum_f_only(h, x + (size_t)r * h->n, y + (size_t)r * h->n, precision, st));
-  VSIE_TRY(correction_apply_block(h, x, y, nrhs, precision, st));
+      VSIE_TRY(far_sum_f_only(h, x + (size_t)r * h->n, y + (size_t)r * h->n, 64, st));
+  VSIE_TRY(correction_apply_block(h, x, y, nrhs, 64, st));
   VSIE_CUDA(cudaGetLastError());
-  if (precision == 64) return VSIE_OK;
-  return batch_status(h, st);
+  return VSIE_OK;
+}
+
+namespace vsie {
+
+vsie_status check_multi_args(vsie_handle* const* hs, int32_t nop, const void* const* x, void* const* y,
+                             int32_t nrhs, const char* who) {
+  if (!hs || !x || !y || nop < 1 || nrhs < 1) {
+    set_error(std::string(who) + ": null array, nop < 1 or nrhs < 1");
+    return VSIE_ERR_ARG;
+  }
+  for (int p = 0; p < nop; ++p) {
+    if (!hs[p] || !x[p] || !y[p] || x[p] == y[p]) {
+      set_error(std::string(who) + ": null handle or vector, or input aliasing output");
+      return VSIE_ERR_ARG;
+    }
+    const vsie_handle* a = hs[0];
+    const vsie_handle* b = hs[p];
+    if (b->n != a->n || b->G.n != a->G.n || b->K.n != a->K.n || b->F.n != a->F.n || b->device != a->device) {
+      set_error(std::string(who) + ": operators differ in size (collocation points or far-field "
+                "sources per class) or device");
+      return VSIE_ERR_ARG;
+    }
+    for (int q = 0; q < p; ++q)
+      if (hs[q] == hs[p]) {
+        set_error(std::string(who) + ": an operator appears twice (its scratch buffers would be shared)");
+        return VSIE_ERR_ARG;
+      }
+  }
+  return VSIE_OK;
+}
+
+vsie_status apply_batched_multi_launch(vsie_handle* const* hs, int nop, const double2* const* x,
+                                       double2* const* y, int nrhs, cudaStream_t st) {
+  VSIE_TRY(far_batched_gk_multi(hs, nop, x, y, nrhs, st));
+  for (int p = 0; p < nop; ++p) {
+    vsie_handle* h = hs[p];
+    if (h->F.n)
+      for (int r = 0; r < nrhs; ++r)
+        VSIE_TRY(far_sum_f_only(h, x[p] + (size_t)r * h->n, y[p] + (size_t)r * h->n, 32, st));
+    VSIE_TRY(correction_apply_block(h, x[p], y[p], nrhs, 32, st));
+  }
+  VSIE_CUDA(cudaGetLastError());
+  return VSIE_OK;
+}
+
+}  // namespace vsie
+
+extern "C" vsie_status vsie_apply_batched_multi(vsie_handle* const* hs, int32_t nop, const void* const* d_x,
+                                                void* const* d_y, int32_t nrhs, void* stream) {
+  clear_error();
+  VSIE_TRY(check_multi_args(hs, nop, d_x, d_y, nrhs, "vsie_apply_batched_multi"));
+  cudaStream_t st = (cudaStream_t)stream;
+  VSIE_TRY(apply_batched_multi_launch(hs, nop, reinterpret_cast<const double2* const*>(d_x),
+                                      reinterpret_cast<double2* const*>(d_y), nrhs, st));
+  for (int p = 0; p < nop; ++p) VSIE_TRY(batch_status(hs[p], st));
+  return VSIE_OK;
 }

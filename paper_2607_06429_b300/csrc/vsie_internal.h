@@ -68,9 +68,10 @@ struct Correction {
   int64_t nnz = 0;
   int64_t* row_ptr = nullptr;  // n + 1
   int32_t* col = nullptr;      // nnz
-  double2* val64 = nullptr;    // accurate - far-rule value (FP64 coordinates)
-  double2* val32 = nullptr;    // accurate - far-rule value (FP32-rounded coordinates)
-  float2* val32f = nullptr;    // val32 rounded to FP32 (block application, built on first use)
+  // accurate - far-rule value as double-float complex (re.hi, im.hi, re.lo, im.lo)
+  float4* val64 = nullptr;     // far rule from the FP64 coordinates
+  float4* val32 = nullptr;     // far rule from the FP32-rounded coordinates
+  float4* xd = nullptr;        // n: the applied vector in double-float (scratch)
 };
 
 // Per-call buffers of the adjoint far-field sum (allocated on the first adjoint call).
@@ -89,7 +90,7 @@ struct BatchBuffers {
   double* slots = nullptr;       // per-CTA FP64 accumulators / partial tiles of the fix-up
   size_t slot_elems = 0;
   int* status = nullptr;         // set by a timed-out mbarrier wait
-  double2* q64 = nullptr;        // FP64 multi-RHS charges [source][64]
+  float4* q64 = nullptr;         // FP64 multi-RHS charges [source][64] (double-float)
   size_t q64_elems = 0;
   double2* part64 = nullptr;     // FP64 multi-RHS partial sums of the source splits
   size_t part64_elems = 0;
@@ -181,7 +182,18 @@ vsie_status apply_one(vsie_handle* h, const double2* x, double2* y, int precisio
 // evaluation, three-term TF32 contraction); y is overwritten.  batch_status reads (and
 // clears) the timeout flag of those kernels, synchronising the stream.
 vsie_status far_batched_gk(vsie_handle* h, const double2* x, double2* y, int nrhs, cudaStream_t st);
+// The same for nop operators of equal work shape (one persistent launch per class and
+// 64-column block for up to 16 operators); x[p], y[p] are operator p's blocks.
+vsie_status far_batched_gk_multi(vsie_handle* const* hs, int nop, const double2* const* x, double2* const* y,
+                                 int nrhs, cudaStream_t st);
 vsie_status batch_status(vsie_handle* h, cudaStream_t st);
+// The FP32 multi-operator batched apply without the final timeout-flag check (no host
+// synchronisation, no allocation once the buffers exist: capturable in a CUDA graph), and
+// the argument check shared by its entry points.
+vsie_status check_multi_args(vsie_handle* const* hs, int32_t nop, const void* const* x, void* const* y,
+                             int32_t nrhs, const char* who);
+vsie_status apply_batched_multi_launch(vsie_handle* const* hs, int nop, const double2* const* x,
+                                       double2* const* y, int nrhs, cudaStream_t st);
 // The same sums in FP64 on the CUDA cores (each coefficient evaluated once per block of 64
 // columns); y is overwritten.
 vsie_status far_batched64_gk(vsie_handle* h, const double2* x, double2* y, int nrhs, cudaStream_t st);
