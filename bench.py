@@ -145,6 +145,7 @@ def solve_timing(torch, B, W, name="nested24_k10", tol=1e-8):
     both to the relative residual tol measured with the FP64 apply."""
     w = W.nested_k10(24, 4, 10.0)
     op = B.Operator.from_workload(w)
+    op.autotune()
     b = op.plane_wave_rhs([[1.0, 0.0, 0.0]])[0].contiguous()
     out = {"workload": name, "n": op.n, "n_far_sources": op.n_far_sources, "tol": tol}
     x = torch.empty_like(b)
@@ -235,6 +236,7 @@ def multifreq_timing(torch, B, W, mesh="nested24_k10", nfreq=8, ndir=64, steps=2
     dirs = W.fibonacci_dirs(ndir)
     xs = [op.plane_wave_rhs(dirs).contiguous() for op in ops]
     ys = [torch.empty_like(x) for x in xs]
+    ops[0].autotune(far=False, batched=True)  # the launch uses the leading operator's shape
     g = B.BatchedGraph(ops, xs, ys)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -305,6 +307,11 @@ def main():
     op = B.Operator.from_workload(w)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t0
+    # work shapes of the persistent kernels picked by timing candidates on this operator
+    t0 = time.perf_counter()
+    tuning = op.autotune(far=args.precision == 32, batched=args.precision == 32 and not args.no_batched) \
+        if args.precision == 32 else None
+    autotune_s = time.perf_counter() - t0
     n, nsrc = op.n, op.n_far_sources
     inter = float(n) * float(nsrc)
 
@@ -415,6 +422,7 @@ def main():
         "gpu_launches": launches * args.steps,
         "phase_ms": {k: float(np.mean([p[k] for p in phase_ms])) for k in phase_ms[0]},
         "create_s": create_s,
+        "autotune": tuning, "autotune_s": autotune_s,
         "roofline": rf, "peaks": pk_kind,
         "solve": solve,
         "batched": batched,

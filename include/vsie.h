@@ -161,6 +161,28 @@ vsie_status vsie_apply_noalloc(vsie_handle* h, const void* d_x, void* d_y, int32
 vsie_status vsie_apply_batched(vsie_handle* h, const void* d_x, void* d_y, int32_t nrhs,
                                int32_t precision, void* stream);
 
+/* Autotuning of the work shapes (the target-tile x source-chunk items of the persistent
+ * kernels) on this operator.  flags bit 0: the FP32 far-field sums of vsie_apply (sources
+ * per work item in {512, 1024, 2048, 4096} x resident blocks per SM in {max, 3/4 max,
+ * max/2}, per source class); bit 1: the tensor-core sums of vsie_apply_batched (32-source
+ * tiles per work item in {16, 32, 64, 128}).  Each candidate is timed (CUDA events, best
+ * of two runs after a warm-up) on a sample of the targets sized to a few tens of
+ * milliseconds, with pseudo-random charges; the fastest is kept in the handle and used
+ * by every later call (results change only by the summation order).  Allocates and frees
+ * temporary buffers (2 x n x 64 complex128 with bit 1); blocking.  report: NULL or the
+ * chosen shapes with their times and the built-in defaults' times on the same sample. */
+typedef struct {
+  int32_t far_chunk[3];          /* G, K, F classes: sources per work item (0: class absent) */
+  int32_t far_blocks_per_sm[3];  /* resident blocks per SM */
+  double far_ms[3];              /* chosen shape, ms on the tuning sample */
+  double far_default_ms[3];      /* built-in default shape (1024, max), same sample */
+  int32_t batch_chunk_tiles;     /* tensor-core sums: 32-source tiles per work item */
+  double batch_ms;               /* chosen, ms for G + K on the tuning sample (64 columns) */
+  double batch_default_ms;       /* built-in default (64 tiles) */
+  int32_t candidates;            /* configurations timed */
+} vsie_tuning;
+vsie_status vsie_autotune(vsie_handle* h, int32_t flags, vsie_tuning* report, void* stream);
+
 /* The precision-32 vsie_apply_batched of nop operators at once, operator p applied to its
  * own block d_x[p] -> d_y[p] (each n x nrhs): the persistent tensor-core launch of each
  * source class covers the items of up to 16 operators, so that several frequencies (or

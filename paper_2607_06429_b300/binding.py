@@ -28,6 +28,7 @@ EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_appl
            "vsie_adjoint_apply", "vsie_plane_wave_rhs", "vsie_far_field", "vsie_solve",
            "vsie_far_field_adjoint", "vsie_solve_batched", "vsie_apply_batched_multi",
            "vsie_graph_create_batched", "vsie_graph_launch", "vsie_graph_nodes", "vsie_graph_destroy",
+           "vsie_autotune",
            "vsie_last_error")
 
 
@@ -61,6 +62,13 @@ class _SolveOpts(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("inner_tol", ctypes.c_double), ("max_refinements", ctypes.c_int32),
                 ("adjoint", ctypes.c_int32)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("far_chunk", ctypes.c_int32 * 3), ("far_blocks_per_sm", ctypes.c_int32 * 3),
+                ("far_ms", ctypes.c_double * 3), ("far_default_ms", ctypes.c_double * 3),
+                ("batch_chunk_tiles", ctypes.c_int32), ("batch_ms", ctypes.c_double),
+                ("batch_default_ms", ctypes.c_double), ("candidates", ctypes.c_int32)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -114,6 +122,7 @@ def load_library(path: str = LIB_PATH):
     lib.vsie_graph_create_batched.argtypes = [ctypes.POINTER(P), I32, ctypes.POINTER(P), ctypes.POINTER(P),
                                               I32, ctypes.POINTER(P)]
     lib.vsie_graph_launch.argtypes = [P, P]
+    lib.vsie_autotune.argtypes = [P, I32, ctypes.POINTER(_Tuning), P]
     lib.vsie_graph_nodes.argtypes = [P, ctypes.POINTER(I64)]
     lib.vsie_graph_destroy.argtypes = [P]
     lib.vsie_graph_destroy.restype = None
@@ -234,6 +243,20 @@ class Operator:
         _check(_lib.vsie_apply_batched(self._h, _dev(x, "x"), _dev(y, "y"), nrhs, int(precision),
                                        _stream(stream)))
         return y
+
+    def autotune(self, far=True, batched=True, stream=None):
+        """Time candidate work shapes on this operator and keep the fastest (vsie_autotune);
+        returns the report as a dict."""
+        flags = (1 if far else 0) | (2 if batched else 0)
+        t = _Tuning()
+        _check(_lib.vsie_autotune(self._h, flags, ctypes.byref(t), _stream(stream)))
+        cls = ("G", "K", "F")
+        return {"far": {c: {"chunk": t.far_chunk[i], "blocks_per_sm": t.far_blocks_per_sm[i],
+                            "ms": t.far_ms[i], "default_ms": t.far_default_ms[i]}
+                        for i, c in enumerate(cls) if t.far_chunk[i]} if far else None,
+                "batched": {"chunk_tiles": t.batch_chunk_tiles, "ms": t.batch_ms,
+                            "default_ms": t.batch_default_ms} if batched else None,
+                "candidates": t.candidates}
 
     def apply_noalloc(self, x, y, precision=32, stream=None):
         """y = A x without any device allocation in the call (vsie_apply_noalloc); the

@@ -52,7 +52,7 @@ namespace vsie {
 constexpr int BT_M = 128;             // targets per CTA tile
 constexpr int BT_S = 32;              // sources per tile (MMA K = 8: four k-steps)
 constexpr int BT_R = 64;              // right-hand sides per launch
-constexpr int BT_CHUNK_TILES = 64;    // source tiles per work item (2048 sources)
+constexpr int BT_CHUNK_TILES = 64;    // source tiles per work item (2048 sources; default, autotuned)
 constexpr int BT_B_MAT = BT_R * BT_S * 4;        // 8 KB per B block (64 x 32 tf32)
 constexpr int BT_HDR = 6 * BT_S * 4;             // -x, -y, -z, nx, ny, nz of the 32 sources
 constexpr int BT_IMG = BT_HDR + 4 * BT_B_MAT;    // per-tile image in global memory
@@ -215,7 +215,8 @@ struct BatchArgs {
   int64_t nt;               // targets
   int64_t ntiles_src;       // source tiles
   int64_t ntile_t;          // target tiles
-  int64_t nchunk;           // chunks of BT_CHUNK_TILES source tiles
+  int64_t chunk_tiles;      // source tiles per work item
+  int64_t nchunk;           // chunks of chunk_tiles source tiles
   int64_t nitems;           // nprob * ntile_t * nchunk
   int64_t grid;
   int64_t ld_out;           // nt
@@ -288,8 +289,8 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
       bool pstarted = false, pdone = false;
       const unsigned char* pimg = nullptr;  // images of the current item's operator
       auto pitem = [&]() {
-        ps = (pk % a.nchunk) * BT_CHUNK_TILES;
-        pend = min(a.ntiles_src, ps + BT_CHUNK_TILES);
+        ps = (pk % a.nchunk) * a.chunk_tiles;
+        pend = min(a.ntiles_src, ps + a.chunk_tiles);
         pimg = a.img[(pk / a.nchunk) / a.ntile_t];
       };
       auto pnext = [&]() -> int64_t {
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
         const int64_t tile = k / a.nchunk;
         const int64_t c0 = k - tile * a.nchunk;
         const int64_t c1 = min(a.nchunk, c0 + (k1 - k));
-        const int64_t s_begin = c0 * BT_CHUNK_TILES, s_end = min(a.ntiles_src, c1 * BT_CHUNK_TILES);
+        const int64_t s_begin = c0 * a.chunk_tiles, s_end = min(a.ntiles_src, c1 * a.chunk_tiles);
         for (int64_t s = s_begin; s < s_end && !err; ++s, ++g) {
           const int sb = g % BT_NB;
           err = !mbar_wait(b_full + sb, (g / BT_NB) & 1) || !mbar_wait(a_full, g & 1);
@@ -452,7 +453,7 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
       const int64_t tile = k / a.nchunk;
       const int64_t c0 = k - tile * a.nchunk;
       const int64_t c1 = min(a.nchunk, c0 + (k1 - k));
-      const int64_t s_begin = c0 * BT_CHUNK_TILES, s_end = min(a.ntiles_src, c1 * BT_CHUNK_TILES);
+      const int64_t s_begin = c0 * a.chunk_tiles, s_end = min(a.ntiles_src, c1 * a.chunk_tiles);
       const int prob = (int)(tile / a.ntile_t);         // operator of this segment
       const int64_t ltile = tile - (int64_t)prob * a.ntile_t;
       const int64_t ti = ltile * BT_M + m;
@@ -709,7 +710,8 @@ static vsie_status tc_attributes(int device) {
 // r_base .. r_base + 63 of each operator's block x[p] -> y[p]: per-operator charge images,
 // then one persistent tensor-core launch over all operators' items and one fix-up launch.
 static vsie_status batch_class_multi(vsie_handle* const* hs, int nop, bool is_k, const double2* const* x,
-                                     double2* const* y, int nrhs, int r_base, int mode, cudaStream_t st) {
+                                     double2* const* y, int nrhs, int r_base, int mode, cudaStream_t st,
+                                     int64_t nt_limit = 0, int chunk_tiles = 0) {
   vsie_handle* h0 = hs[0];
   const Sources& S0 = is_k ? h0->K : h0->G;
   if (!S0.n || !h0->n) return VSIE_OK;
@@ -736,10 +738,12 @@ static vsie_status batch_class_multi(vsie_handle* const* hs, int nop, bool is_k,
     a.img[p] = h->batch.img;
     a.out[p] = y[p] + (int64_t)r_base * h->n;
   }
-  a.nt = h0->n;
+  a.nt = nt_limit > 0 ? std::min<int64_t>(nt_limit, h0->n) : h0->n;
   a.ntiles_src = ntiles;
-  a.ntile_t = (h0->n + BT_M - 1) / BT_M;
-  a.nchunk = (ntiles + BT_CHUNK_TILES - 1) / BT_CHUNK_TILES;
+  a.ntile_t = (a.nt + BT_M - 1) / BT_M;
+  if (chunk_tiles <= 0) chunk_tiles = h0->tune.bt_chunk_tiles > 0 ? h0->tune.bt_chunk_tiles : BT_CHUNK_TILES;
+  a.chunk_tiles = chunk_tiles;
+  a.nchunk = (ntiles + a.chunk_tiles - 1) / a.chunk_tiles;
   a.nitems = (int64_t)nop * a.ntile_t * a.nchunk;
   a.grid = std::max<int64_t>(1, std::min<int64_t>(h0->num_sms > 0 ? h0->num_sms : 148, a.nitems));
   a.ld_out = h0->n;
@@ -800,6 +804,60 @@ vsie_status far_batched_gk_multi(vsie_handle* const* hs, int nop, const double2*
 
 vsie_status far_batched_gk(vsie_handle* h, const double2* x, double2* y, int nrhs, cudaStream_t st) {
   return far_batched_gk_multi(&h, 1, &x, &y, nrhs, st);
+}
+
+// Picks the source tiles per work item of the tensor-core sums by timing 16, 32, 64 and 128
+// on a sample of the target tiles (sized to about 3e10 pair evaluations per class and
+// candidate) for one block of 64 columns x.
+vsie_status batch_autotune(vsie_handle* h, const double2* x, double2* y, cudaStream_t st, int* chunk_tiles,
+                           double ms_out[2], int* candidates) {
+  static const int cands[] = {16, 32, 64, 128};
+  const int64_t ns = h->G.n + h->K.n;
+  *chunk_tiles = 0;
+  ms_out[0] = ms_out[1] = 0.0;
+  if (!ns || !h->n) return VSIE_OK;
+  const int64_t nt = std::min<int64_t>(h->n, std::max<int64_t>((int64_t)BT_M * 2 * std::max(h->num_sms, 1),
+                                                               (int64_t)(3e10 / (double)ns)));
+  cudaEvent_t e0, e1;
+  VSIE_CUDA(cudaEventCreate(&e0));
+  VSIE_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f, dflt = 0.0f;
+  int best_c = BT_CHUNK_TILES;
+  vsie_status s = VSIE_OK;
+  for (int c : cands) {
+    float cbest = 1e30f;
+    for (int r = 0; r <= 2 && s == VSIE_OK; ++r) {  // the first run warms up
+      cudaEventRecord(e0, st);
+      int mode = 0;
+      if (h->G.n && s == VSIE_OK) {
+        s = batch_class_multi(&h, 1, false, &x, &y, 64, 0, mode, st, nt, c);
+        mode = 1;
+      }
+      if (h->K.n && s == VSIE_OK) s = batch_class_multi(&h, 1, true, &x, &y, 64, 0, mode, st, nt, c);
+      cudaEventRecord(e1, st);
+      if (s == VSIE_OK && cudaEventSynchronize(e1) == cudaSuccess && r > 0) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cbest = std::min(cbest, ms);
+      }
+    }
+    if (s != VSIE_OK) break;
+    ++*candidates;
+    if (c == BT_CHUNK_TILES) dflt = cbest;
+    if (cbest < best) {
+      best = cbest;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  VSIE_TRY(s);
+  VSIE_TRY(batch_status(h, st));
+  h->tune.bt_chunk_tiles = best_c;
+  *chunk_tiles = best_c;
+  ms_out[0] = best;
+  ms_out[1] = dflt;
+  return VSIE_OK;
 }
 
 vsie_status batch_status(vsie_handle* h, cudaStream_t st) {

@@ -40,7 +40,7 @@ namespace vsie {
 constexpr int kBlock = 128;                 // threads per block, sources per smem tile
 constexpr int kT = 4;                       // targets per thread
 constexpr int kTile = kBlock * kT;          // targets per work item
-constexpr int kChunk = 8 * kBlock;          // sources per work item
+constexpr int kChunk = 8 * kBlock;          // sources per work item (default; the autotuner may pick another)
 constexpr double kTwoPi = 2.0 * kPi;
 
 template <class R>
@@ -535,6 +535,7 @@ struct PolK2 {
 
 struct StreamK {
   int64_t nt, ns;
+  int64_t chunk;                 // sources per work item (a multiple of kBlock)
   int64_t ntile, nchunk, nitems;
   int64_t grid;
 };
@@ -560,8 +561,8 @@ __global__ void __launch_bounds__(kBlock) nbody_kernel(P p, StreamK sk, double2*
     p.load_targets(tile * kTile + tid, sk.nt, tg);
 #pragma unroll
     for (int t = 0; t < kT; ++t) acc[t].zero();
-    const int64_t j_begin = c0 * kChunk;
-    const int64_t j_end = min(sk.ns, c1 * kChunk);
+    const int64_t j_begin = c0 * sk.chunk;
+    const int64_t j_end = min(sk.ns, c1 * sk.chunk);
     for (int64_t j0 = j_begin; j0 < j_end; j0 += kBlock) {
       const int64_t j = j0 + tid;
       p.stage(sm, j, j < j_end, tid);
@@ -635,7 +636,7 @@ __global__ void __launch_bounds__(kTile) fixup_kernel(StreamK sk, const double2*
 // ----------------------------------------------------------------- launch planning
 
 template <class R, class P>
-static int resident_blocks(const vsie_handle* h) {
+static int resident_per_sm() {
   static int cached = 0;  // per instantiation; identical on every B300
   if (!cached) {
     int per_sm = 0;
@@ -644,18 +645,26 @@ static int resident_blocks(const vsie_handle* h) {
       per_sm = 1;
     cached = per_sm;
   }
-  return cached * (h->num_sms > 0 ? h->num_sms : 148);
+  return cached;
 }
 
+// Work decomposition of one class sum: target tiles x source chunks, a persistent grid.
+// FP32 sums of class cls (0 G, 1 K, 2 F) take the autotuned chunk and blocks per SM when
+// set; explicit chunk / bps arguments (> 0) override both (the autotuner's candidates).
 template <class R, class P>
-static StreamK plan_sk(const vsie_handle* h, int64_t nt, int64_t ns) {
+static StreamK plan_sk(const vsie_handle* h, int64_t nt, int64_t ns, int cls = -1, int chunk = 0, int bps = 0) {
   StreamK s;
   s.nt = nt;
   s.ns = ns;
+  const bool tuned = sizeof(R) == 4 && cls >= 0;
+  if (chunk <= 0) chunk = (tuned && h->tune.chunk[cls] > 0) ? h->tune.chunk[cls] : kChunk;
+  if (bps <= 0) bps = (tuned && h->tune.bps[cls] > 0) ? h->tune.bps[cls] : resident_per_sm<R, P>();
+  bps = std::min(bps, resident_per_sm<R, P>());
+  s.chunk = chunk;
   s.ntile = (nt + kTile - 1) / kTile;
-  s.nchunk = (ns + kChunk - 1) / kChunk;
+  s.nchunk = (ns + s.chunk - 1) / s.chunk;
   s.nitems = s.ntile * s.nchunk;
-  int64_t C = resident_blocks<R, P>(h);
+  int64_t C = (int64_t)bps * (h->num_sms > 0 ? h->num_sms : 148);
   if (h->tile_override > 0) C = h->tile_override;
   s.grid = std::max<int64_t>(1, std::min<int64_t>(C, s.nitems));
   return s;
@@ -845,9 +854,9 @@ static ForwardPlans forward_plans(const vsie_handle* h, int precision) {
   ForwardPlans P;
   const int64_t n = h->n;
   if (precision == 32) {
-    P.g = plan_sk<float, PolG2>(h, n, h->G.n);
-    P.k = plan_sk<float, PolK2>(h, n, h->K.n);
-    P.f = plan_sk<float, PerTarget<float, PolF<float>>>(h, n, h->F.n);
+    P.g = plan_sk<float, PolG2>(h, n, h->G.n, 0);
+    P.k = plan_sk<float, PolK2>(h, n, h->K.n, 1);
+    P.f = plan_sk<float, PerTarget<float, PolF<float>>>(h, n, h->F.n, 2);
   } else {
     P.g = plan_sk<double, PerTarget<double, PolG<double>>>(h, n, h->G.n);
     P.k = plan_sk<double, PerTarget<double, PolK<double>>>(h, n, h->K.n);
@@ -953,6 +962,86 @@ vsie_status far_apply(vsie_handle* h, const double2* x, double2* y, int precisio
                       cudaStream_t st) {
   VSIE_TRY(far_prescale(h, x, precision, st, nullptr));
   return forward(h, y, precision, nullptr, st, 7, nullptr);
+}
+
+// ----------------------------------------------------------------- autotuning
+
+// Times the FP32 sum of class cls (records already prescaled) on the first nt targets with
+// a candidate work shape (sources per item, blocks per SM): the best of `reps` runs.
+template <class P>
+static vsie_status time_class(vsie_handle* h, const P& p, int64_t nt, int64_t ns, int chunk, int bps,
+                              double2* out, cudaStream_t st, int reps, float* best_ms) {
+  const StreamK sk = plan_sk<float, P>(h, nt, ns, -1, chunk, bps);
+  double2* slots = nullptr;
+  VSIE_TRY(handle_slots(h, slot_elems(sk), &slots));
+  cudaEvent_t e0, e1;
+  VSIE_CUDA(cudaEventCreate(&e0));
+  VSIE_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  vsie_status s = VSIE_OK;
+  for (int r = 0; r <= reps && s == VSIE_OK; ++r) {  // the first run warms up
+    cudaEventRecord(e0, st);
+    s = run_nbody<float, P>(p, sk, out, 0, slots, st, nullptr);
+    cudaEventRecord(e1, st);
+    if (s == VSIE_OK && cudaEventSynchronize(e1) == cudaSuccess && r > 0) {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best = std::min(best, ms);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *best_ms = best;
+  return s;
+}
+
+// Picks sources per work item and blocks per SM of each FP32 class sum by timing the
+// candidates on a sample of the targets (sized to about 4e10 pair evaluations per run, so
+// a candidate costs tens of milliseconds at any mesh size), with x a random vector.
+vsie_status far_autotune(vsie_handle* h, const double2* x, double2* scratch, cudaStream_t st, int cand_out[3][2],
+                         double ms_out[3][2], int* candidates) {
+  VSIE_TRY(far_prescale(h, x, 32, st, nullptr));
+  static const int chunks[] = {512, 1024, 2048, 4096};
+  for (int cls = 0; cls < 3; ++cls) {
+    const int64_t ns = cls == 0 ? h->G.n : cls == 1 ? h->K.n : h->F.n;
+    cand_out[cls][0] = cand_out[cls][1] = 0;
+    ms_out[cls][0] = ms_out[cls][1] = 0.0;
+    if (!ns || !h->n) continue;
+    const int64_t want = std::max<int64_t>((int64_t)kTile * 2 * std::max(h->num_sms, 1),
+                                           (int64_t)(4e10 / (double)ns));
+    const int64_t nt = std::min<int64_t>(h->n, want);
+    const int maxb = cls == 0 ? resident_per_sm<float, PolG2>()
+                              : cls == 1 ? resident_per_sm<float, PolK2>()
+                                         : resident_per_sm<float, PerTarget<float, PolF<float>>>();
+    int bps_c[3] = {maxb, std::max(1, maxb / 2), std::max(1, (3 * maxb) / 4)};
+    float best = 1e30f, dflt = 0.0f;
+    int best_chunk = kChunk, best_bps = maxb;
+    for (int c : chunks)
+      for (int bi = 0; bi < 3; ++bi) {
+        if (bi > 0 && bps_c[bi] == bps_c[0]) continue;
+        float ms = 0.0f;
+        if (cls == 0)
+          VSIE_TRY(time_class(h, make_g<float>(h), nt, ns, c, bps_c[bi], scratch, st, 2, &ms));
+        else if (cls == 1)
+          VSIE_TRY(time_class(h, make_k<float>(h), nt, ns, c, bps_c[bi], scratch, st, 2, &ms));
+        else
+          VSIE_TRY(time_class(h, make_f<float>(h), nt, ns, c, bps_c[bi], scratch, st, 2, &ms));
+        ++*candidates;
+        if (c == kChunk && bi == 0) dflt = ms;
+        if (ms < best) {
+          best = ms;
+          best_chunk = c;
+          best_bps = bps_c[bi];
+        }
+      }
+    h->tune.chunk[cls] = best_chunk;
+    h->tune.bps[cls] = best_bps;
+    cand_out[cls][0] = best_chunk;
+    cand_out[cls][1] = best_bps;
+    ms_out[cls][0] = best;
+    ms_out[cls][1] = dflt;
+  }
+  return VSIE_OK;
 }
 
 vsie_status far_sum_f_only(vsie_handle* h, const double2* x, double2* y, int precision, cudaStream_t st) {

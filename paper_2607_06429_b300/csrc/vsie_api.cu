@@ -566,6 +566,71 @@ vsie_status apply_batched_multi_launch(vsie_handle* const* hs, int nop, const do
 
 }  // namespace vsie
 
+namespace vsie {
+
+// deterministic pseudo-random complex values in [-1, 1) (a 64-bit integer hash of i + seed)
+__global__ void random_fill_kernel(double2* __restrict__ v, int64_t m, uint64_t seed) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + seed;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  const double a = (double)(z >> 32) * (1.0 / 2147483648.0) - 1.0;
+  const double b = (double)(z & 0xFFFFFFFFull) * (1.0 / 2147483648.0) - 1.0;
+  v[i] = make_double2(a, b);
+}
+
+}  // namespace vsie
+
+extern "C" vsie_status vsie_autotune(vsie_handle* h, int32_t flags, vsie_tuning* report, void* stream) {
+  clear_error();
+  if (!h || (flags & ~3) || !flags) {
+    set_error("vsie_autotune: null handle or flags outside {1, 2, 3}");
+    return VSIE_ERR_ARG;
+  }
+  vsie_tuning rep{};
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = h->n;
+  const size_t cols = (flags & 2) ? 64 : 1;
+  double2 *x = nullptr, *y = nullptr;
+  cudaError_t e = cudaMalloc(&x, sizeof(double2) * std::max<size_t>(1, n * cols));
+  if (e == cudaSuccess) e = cudaMalloc(&y, sizeof(double2) * std::max<size_t>(1, n * cols));
+  if (e != cudaSuccess) {
+    cudaFree(x);
+    return cuda_fail(e, "cudaMalloc(autotune buffers)", __FILE__, __LINE__);
+  }
+  auto run = [&]() -> vsie_status {
+    if (n == 0) return VSIE_OK;
+    random_fill_kernel<<<(unsigned)((n * cols + 255) / 256), 256, 0, st>>>(x, (int64_t)(n * cols), 12345);
+    VSIE_CUDA(cudaGetLastError());
+    if (flags & 1) {
+      int cand[3][2];
+      double ms[3][2];
+      VSIE_TRY(far_autotune(h, x, y, st, cand, ms, &rep.candidates));
+      for (int c = 0; c < 3; ++c) {
+        rep.far_chunk[c] = cand[c][0];
+        rep.far_blocks_per_sm[c] = cand[c][1];
+        rep.far_ms[c] = ms[c][0];
+        rep.far_default_ms[c] = ms[c][1];
+      }
+    }
+    if (flags & 2) {
+      double ms[2];
+      VSIE_TRY(batch_autotune(h, x, y, st, &rep.batch_chunk_tiles, ms, &rep.candidates));
+      rep.batch_ms = ms[0];
+      rep.batch_default_ms = ms[1];
+    }
+    VSIE_CUDA(cudaStreamSynchronize(st));
+    return VSIE_OK;
+  };
+  const vsie_status s = run();
+  cudaFree(x);
+  cudaFree(y);
+  if (report) *report = rep;
+  return s;
+}
+
 extern "C" vsie_status vsie_apply_batched_multi(vsie_handle* const* hs, int32_t nop, const void* const* d_x,
                                                 void* const* d_y, int32_t nrhs, void* stream) {
   clear_error();

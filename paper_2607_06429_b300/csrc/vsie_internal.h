@@ -125,6 +125,12 @@ struct vsie_handle {
   size_t split_elems = 0;
   vsie::AdjRecords adj;
   vsie::BatchBuffers batch;
+  // work shapes chosen by vsie_autotune (0 = built-in default)
+  struct {
+    int chunk[3] = {0, 0, 0};  // FP32 far sums (G, K, F): sources per work item
+    int bps[3] = {0, 0, 0};    // FP32 far sums: resident blocks per SM
+    int bt_chunk_tiles = 0;    // tensor-core batched sums: 32-source tiles per work item
+  } tune;
 
   std::vector<void*> allocs;  // every device allocation, freed by vsie_destroy
 };
@@ -197,6 +203,14 @@ vsie_status apply_batched_multi_launch(vsie_handle* const* hs, int nop, const do
 // The same sums in FP64 on the CUDA cores (each coefficient evaluated once per block of 64
 // columns); y is overwritten.
 vsie_status far_batched64_gk(vsie_handle* h, const double2* x, double2* y, int nrhs, cudaStream_t st);
+// Autotuning of the FP32 far sums' work shapes (sets h->tune; x is a random vector,
+// scratch holds n values): chosen (chunk, blocks per SM) and (chosen, default) times per class.
+vsie_status far_autotune(vsie_handle* h, const double2* x, double2* scratch, cudaStream_t st, int cand_out[3][2],
+                         double ms_out[3][2], int* candidates);
+// The same for the tensor-core batched sums' source tiles per work item (x: a block of 64
+// random columns, y: n x 64 scratch).
+vsie_status batch_autotune(vsie_handle* h, const double2* x, double2* y, cudaStream_t st, int* chunk_tiles,
+                           double ms_out[2], int* candidates);
 // Far-field sum of the F class only (added into y), for one column.
 vsie_status far_sum_f_only(vsie_handle* h, const double2* x, double2* y, int precision, cudaStream_t st);
 
