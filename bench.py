@@ -150,7 +150,7 @@ def solve_timing(torch, B, W, name="nested24_k10", tol=1e-8):
     out = {"workload": name, "n": op.n, "n_far_sources": op.n_far_sources, "tol": tol}
     x = torch.empty_like(b)
     y = torch.empty_like(b)
-    for prec in (32, 64):
+    for prec in (32, 48, 64):
         op.apply(b, y, precision=prec)
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -68,4 +68,139 @@ __device__ __forceinline__ double2 df_value(float2 S, float2 C) {
   return make_double2((double)S.x + (double)C.x, (double)S.y + (double)C.y);
 }
 
+// ----------------------------------------------------------------- scalar double-float
+// Real double-float numbers (h + l, |l| <= ulp(h)/2) for the FP64-accuracy far-field sums.
+// All operations use the _rn intrinsics so the compiler never contracts or reorders them.
+
+struct dfs {
+  float h, l;
+};
+
+__device__ __forceinline__ dfs dfs_make(double v) {
+  const float h = __double2float_rn(v);
+  return dfs{h, __double2float_rn(v - (double)h)};
+}
+__device__ __forceinline__ double dfs_value(dfs a) { return (double)a.h + (double)a.l; }
+
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ dfs dfs_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  return dfs{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z))};
+}
+// s + e = a + b exactly when |a| >= |b| or a = 0 (Dekker)
+__device__ __forceinline__ dfs dfs_fast_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return dfs{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfs dfs_add(dfs a, dfs b) {
+  const dfs s = dfs_two_sum(a.h, b.h);
+  return dfs_fast_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ dfs dfs_neg(dfs a) { return dfs{-a.h, -a.l}; }
+__device__ __forceinline__ dfs dfs_sub(dfs a, dfs b) { return dfs_add(a, dfs_neg(b)); }
+__device__ __forceinline__ dfs dfs_addf(dfs a, float b) {
+  const dfs s = dfs_two_sum(a.h, b);
+  return dfs_fast_sum(s.h, __fadd_rn(s.l, a.l));
+}
+// products: the high product's error by FMA (TwoProduct), plus the cross terms
+__device__ __forceinline__ dfs dfs_mul(dfs a, dfs b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return dfs_fast_sum(p, e);
+}
+__device__ __forceinline__ dfs dfs_mulf(dfs a, float b) {
+  const float p = __fmul_rn(a.h, b);
+  float e = __fmaf_rn(a.h, b, -p);
+  e = __fmaf_rn(a.l, b, e);
+  return dfs_fast_sum(p, e);
+}
+__device__ __forceinline__ dfs dfs_sqr(dfs a) {
+  const float p = __fmul_rn(a.h, a.h);
+  float e = __fmaf_rn(a.h, a.h, -p);
+  e = __fmaf_rn(__fmul_rn(2.0f, a.h), a.l, e);
+  return dfs_fast_sum(p, e);
+}
+
+// 1/sqrt(a) for a > 0: the hardware estimate, one FP32 Newton step, then one Newton step
+// whose residual 1 - a y^2 is formed exactly enough in double-float (quadratic convergence
+// from ~2^-24 to ~2^-47).
+__device__ __forceinline__ dfs dfs_rsqrt(dfs a) {
+  float y = rsqrtf(a.h);
+  y = __fmul_rn(y, __fmaf_rn(__fmul_rn(-0.5f, a.h), __fmul_rn(y, y), 1.5f));
+  const float q = __fmul_rn(y, y);
+  const dfs y2{q, __fmaf_rn(y, y, -q)};
+  const dfs w = dfs_mul(a, y2);
+  const float res = __fsub_rn(__fsub_rn(1.0f, w.h), w.l);  // 1 - w.h is exact (w.h near 1)
+  return dfs_fast_sum(y, __fmul_rn(__fmul_rn(0.5f, y), res));
+}
+
+// Double-float constants: the float nearest to the value and the float nearest to the rest.
+#define VSIE_DFC(name, hi, lo) __device__ __forceinline__ dfs name() { return dfs{hi, lo}; }
+VSIE_DFC(dfc_two_pi, 0x1.921fb6p+2f, -0x1.777a5cp-23f)
+VSIE_DFC(dfc_sqrt_half, 0x1.6a09e6p-1f, 0x1.9fcef4p-27f)
+VSIE_DFC(dfc_inv3, 0x1.555556p-3f, -0x1.555556p-28f)    // 1/3!
+VSIE_DFC(dfc_inv4, 0x1.555556p-5f, -0x1.555556p-30f)    // 1/4!
+VSIE_DFC(dfc_inv5, 0x1.111112p-7f, -0x1.dddddep-32f)     // 1/5!
+VSIE_DFC(dfc_inv6, 0x1.6c16c2p-10f, -0x1.27d27ep-35f)   // 1/6!
+VSIE_DFC(dfc_inv7, 0x1.a01a02p-13f, -0x1.7f97fap-39f)   // 1/7!
+VSIE_DFC(dfc_inv8, 0x1.a01a02p-16f, -0x1.7f97fap-42f)   // 1/8!
+VSIE_DFC(dfc_inv9, 0x1.71de3ap-19f, 0x1.55b1ccp-45f)    // 1/9!
+#undef VSIE_DFC
+
+// (cos, sin)(2 pi f) for a double-float f with |f| <= 1/2 (plus rounding).  Reduction to
+// the nearest multiple m of 1/8 (exact in float), g = f - m/8 with |2 pi g| <= pi/8, Taylor
+// series of sin and cos in x = (2 pi g)^2 (terms through x^7: truncation below 2e-18),
+// the terms below 1e-10 in plain float and the others in double-float Horner steps, then
+// rotation by m pi/4 (a sum/difference scaled by sqrt(1/2) for odd m, a quarter-turn
+// permutation with sign changes).
+__device__ __forceinline__ void dfs_cossin_2pi(dfs f, dfs& c, dfs& s) {
+  const float m = rintf(__fmul_rn(8.0f, f.h));
+  const dfs g = dfs_two_sum(__fmaf_rn(-0.125f, m, f.h), f.l);
+  const dfs th = dfs_mul(g, dfc_two_pi());
+  const dfs x = dfs_sqr(th);
+  const float xh = x.h;
+  // sin(th) = th (1 - x/3! + x^2/5! - x^3/7! + x^4/9! - x^5/11! + x^6/13! - x^7/15!)
+  const float ts = __fmul_rn(xh, __fmaf_rn(xh, __fmaf_rn(xh, -7.6471636e-13f, 1.6059044e-10f), -2.5052108e-08f));
+  dfs p = dfs_addf(dfc_inv9(), ts);
+  p = dfs_sub(dfs_mul(p, x), dfc_inv7());
+  p = dfs_add(dfs_mul(p, x), dfc_inv5());
+  p = dfs_sub(dfs_mul(p, x), dfc_inv3());
+  p = dfs_addf(dfs_mul(p, x), 1.0f);
+  const dfs sn = dfs_mul(p, th);
+  // cos(th) = 1 - x/2! + x^2/4! - x^3/6! + x^4/8! - x^5/10! + x^6/12! - x^7/14!
+  const float tc = __fmul_rn(xh, __fmaf_rn(xh, __fmaf_rn(xh, -1.1470745e-11f, 2.0876756e-09f), -2.7557320e-07f));
+  dfs q = dfs_addf(dfc_inv8(), tc);
+  q = dfs_sub(dfs_mul(q, x), dfc_inv6());
+  q = dfs_add(dfs_mul(q, x), dfc_inv4());
+  q = dfs_addf(dfs_mul(q, x), -0.5f);
+  q = dfs_addf(dfs_mul(q, x), 1.0f);
+  dfs cs = q;
+  dfs sv = sn;
+  const int mi = (int)m;  // -4 .. 4
+  if (mi & 1) {  // rotate by pi/4: (c - s, c + s) sqrt(1/2)
+    const dfs a = dfs_mul(dfs_sub(cs, sv), dfc_sqrt_half());
+    const dfs b = dfs_mul(dfs_add(cs, sv), dfc_sqrt_half());
+    cs = a;
+    sv = b;
+  }
+  const int qd = ((mi - (mi & 1)) / 2) & 3;  // remaining quarter turns
+  if (qd == 1) {
+    const dfs t = cs;
+    cs = dfs_neg(sv);
+    sv = t;
+  } else if (qd == 2) {
+    cs = dfs_neg(cs);
+    sv = dfs_neg(sv);
+  } else if (qd == 3) {
+    const dfs t = cs;
+    cs = sv;
+    sv = dfs_neg(t);
+  }
+  c = cs;
+  s = sv;
+}
+
 }  // namespace vsie

@@ -33,6 +33,7 @@
 
 #include <algorithm>
 
+#include "dfloat.h"
 #include "vsie_internal.h"
 
 namespace vsie {
@@ -531,6 +532,150 @@ struct PolK2 {
   }
 };
 
+// ----------------------------------------------------------------- double-float policies
+// Precision 48: FP64-class accuracy (about 2^-47 per operation) with every operation on the
+// FP32 pipe, for the residuals of iterative refinement (B300's FP64 pipe runs at 1/64 of
+// the FP32 rate).  Positions (kappa-scaled), charges and normals are double-float records;
+// d = x~ - y~, r^2, 1/r (hardware estimate + Newton steps), the phase t = r (revolutions),
+// f = t - round(t) and (cos, sin)(2 pi f) (Taylor series after an octant reduction,
+// dfloat.h) are double-float; each pair's coefficient times its charge is accumulated by
+// the packed double-float complex multiply-add.  The partial sum of a 128-source tile is
+// converted to FP64 and added to the target's FP64 accumulator.
+
+struct DTgt {
+  dfs x, y, z;
+};
+
+// d = t - y~ (y~ from records a = (x.h, y.h, z.h, *), b = (x.l, y.l, z.l, *)); rinv = 1/|d|
+// (0 at d = 0), tt = |d| (revolutions), (cs, sn) = (cos, sin)(2 pi tt)
+__device__ __forceinline__ void df_geometry(const DTgt& t, const float4& a, const float4& b, dfs& dx, dfs& dy,
+                                            dfs& dz, dfs& rinv, dfs& tt, dfs& cs, dfs& sn) {
+  dx = dfs_sub(t.x, dfs{a.x, b.x});
+  dy = dfs_sub(t.y, dfs{a.y, b.y});
+  dz = dfs_sub(t.z, dfs{a.z, b.z});
+  const dfs r2 = dfs_add(dfs_add(dfs_sqr(dx), dfs_sqr(dy)), dfs_sqr(dz));
+  const bool zero = !(r2.h > 0.0f);
+  rinv = dfs_rsqrt(zero ? dfs{1.0f, 0.0f} : r2);
+  if (zero) rinv = dfs{0.0f, 0.0f};
+  tt = dfs_mul(r2, rinv);
+  const float n = rintf(tt.h);
+  const dfs f = dfs_two_sum(__fsub_rn(tt.h, n), tt.l);
+  dfs_cossin_2pi(f, cs, sn);
+}
+
+__device__ __forceinline__ float4 df_c4(dfs re, dfs im) { return make_float4(re.h, im.h, re.l, im.l); }
+
+template <int NREC>
+struct DfBase {
+  struct Smem {
+    float4 r[NREC][kBlock];
+  };
+  struct Src {
+    float4 r[NREC];
+  };
+  struct Tgts {
+    DTgt t[kT];
+  };
+  struct Part {
+    float2 S[kT], C[kT];
+  };
+  const float4* __restrict__ tgt;  // 2 records per target
+  const float4* __restrict__ src;  // NREC records per source
+
+  __device__ __forceinline__ void load_targets(int64_t i0, int64_t nt, Tgts& tg) const {
+#pragma unroll
+    for (int t = 0; t < kT; ++t) {
+      const int64_t i = i0 + (int64_t)t * kBlock;
+      float4 a = make_float4(0, 0, 0, 0), b = a;
+      if (i < nt) {
+        a = tgt[2 * i];
+        b = tgt[2 * i + 1];
+      }
+      tg.t[t] = DTgt{dfs{a.x, b.x}, dfs{a.y, b.y}, dfs{a.z, b.z}};
+    }
+  }
+  __device__ __forceinline__ void stage(Smem& sm, int64_t j, bool ok, int tid) const {
+#pragma unroll
+    for (int q = 0; q < NREC; ++q) sm.r[q][tid] = ok ? src[(int64_t)NREC * j + q] : make_float4(0, 0, 0, 0);
+  }
+  __device__ __forceinline__ Src get(const Smem& sm, int jj) const {
+    Src s;
+#pragma unroll
+    for (int q = 0; q < NREC; ++q) s.r[q] = sm.r[q][jj];
+    return s;
+  }
+  __device__ __forceinline__ void zero(Part& q) const {
+#pragma unroll
+    for (int t = 0; t < kT; ++t) q.S[t] = q.C[t] = make_float2(0.0f, 0.0f);
+  }
+  __device__ __forceinline__ void unpack(Part& q, double* ar, double* ai) const {
+#pragma unroll
+    for (int t = 0; t < kT; ++t) {
+      df_renorm2(q.S[t], q.C[t]);
+      const double2 v = df_value(q.S[t], q.C[t]);
+      ar[t] = v.x;
+      ai[t] = v.y;
+    }
+  }
+};
+
+// G: records (x.h, y.h, z.h, q.re.h) (x.l, y.l, z.l, q.re.l) (q.im.h, q.im.l, 0, 0);
+//    y += e^{2 pi i t} rinv q~
+struct PolGdf : DfBase<3> {
+  __device__ __forceinline__ void accumulate(const Src& s, const Tgts& tg, Part& q) const {
+    const float4 qv = make_float4(s.r[0].w, s.r[2].x, s.r[1].w, s.r[2].y);
+#pragma unroll
+    for (int t = 0; t < kT; ++t) {
+      dfs dx, dy, dz, rinv, tt, cs, sn;
+      df_geometry(tg.t[t], s.r[0], s.r[1], dx, dy, dz, rinv, tt, cs, sn);
+      df_cmac(q.S[t], q.C[t], df_c4(dfs_mul(cs, rinv), dfs_mul(sn, rinv)), qv);
+    }
+  }
+};
+
+// K: records (x.h, y.h, z.h, c.re.h) (x.l, y.l, z.l, c.re.l) (nx.h, ny.h, nz.h, c.im.h)
+//    (nx.l, ny.l, nz.l, c.im.l);  y += e^{2 pi i t}(2 pi i t - 1)(d~ . n) rinv^3 c~
+struct PolKdf : DfBase<4> {
+  __device__ __forceinline__ void accumulate(const Src& s, const Tgts& tg, Part& q) const {
+    const float4 cv = make_float4(s.r[0].w, s.r[2].w, s.r[1].w, s.r[3].w);
+    const dfs nx{s.r[2].x, s.r[3].x}, ny{s.r[2].y, s.r[3].y}, nz{s.r[2].z, s.r[3].z};
+#pragma unroll
+    for (int t = 0; t < kT; ++t) {
+      dfs dx, dy, dz, rinv, tt, cs, sn;
+      df_geometry(tg.t[t], s.r[0], s.r[1], dx, dy, dz, rinv, tt, cs, sn);
+      const dfs dn = dfs_add(dfs_add(dfs_mul(dx, nx), dfs_mul(dy, ny)), dfs_mul(dz, nz));
+      const dfs g3 = dfs_mul(dfs_mul(dfs_sqr(rinv), rinv), dn);
+      const dfs kr = dfs_mul(tt, dfc_two_pi());
+      const dfs A = dfs_add(cs, dfs_mul(kr, sn));  // cos + kr sin
+      const dfs Q = dfs_sub(dfs_mul(kr, cs), sn);  // kr cos - sin
+      df_cmac(q.S[t], q.C[t], df_c4(dfs_neg(dfs_mul(g3, A)), dfs_mul(g3, Q)), cv);
+    }
+  }
+};
+
+// F: records (x.h, y.h, z.h, q.re.h) (x.l, y.l, z.l, q.re.l) (q.im.h, q.im.l, ux.re.h, ux.re.l)
+//    (ux.im.h, ux.im.l, uy.re.h, uy.re.l) (uy.im.h, uy.im.l, uz.re.h, uz.re.l) (uz.im.h, uz.im.l, 0, 0);
+//    y += e^{2 pi i t} rinv [q~ + (2 pi i t - 1)(d~ . u~) rinv^2]
+struct PolFdf : DfBase<6> {
+  __device__ __forceinline__ void accumulate(const Src& s, const Tgts& tg, Part& q) const {
+    const dfs qr{s.r[0].w, s.r[1].w}, qi{s.r[2].x, s.r[2].y};
+    const dfs uxr{s.r[2].z, s.r[2].w}, uxi{s.r[3].x, s.r[3].y}, uyr{s.r[3].z, s.r[3].w};
+    const dfs uyi{s.r[4].x, s.r[4].y}, uzr{s.r[4].z, s.r[4].w}, uzi{s.r[5].x, s.r[5].y};
+#pragma unroll
+    for (int t = 0; t < kT; ++t) {
+      dfs dx, dy, dz, rinv, tt, cs, sn;
+      df_geometry(tg.t[t], s.r[0], s.r[1], dx, dy, dz, rinv, tt, cs, sn);
+      const dfs dur = dfs_add(dfs_add(dfs_mul(dx, uxr), dfs_mul(dy, uyr)), dfs_mul(dz, uzr));
+      const dfs dui = dfs_add(dfs_add(dfs_mul(dx, uxi), dfs_mul(dy, uyi)), dfs_mul(dz, uzi));
+      const dfs ri2 = dfs_sqr(rinv);
+      const dfs fi = dfs_mul(dfs_mul(tt, dfc_two_pi()), ri2);  // 2 pi t rinv^2
+      const dfs inr = dfs_sub(dfs_sub(qr, dfs_mul(ri2, dur)), dfs_mul(fi, dui));
+      const dfs ini = dfs_add(dfs_sub(qi, dfs_mul(ri2, dui)), dfs_mul(fi, dur));
+      df_cmac(q.S[t], q.C[t], df_c4(dfs_mul(cs, rinv), dfs_mul(sn, rinv)), df_c4(inr, ini));
+    }
+  }
+};
+
 // ----------------------------------------------------------------- persistent driver
 
 struct StreamK {
@@ -764,6 +909,66 @@ __global__ void prescale_f_kernel(const double4_32a* __restrict__ ps, const doub
   }
 }
 
+// double-float records of the precision-48 sums (layouts as in PolGdf / PolKdf / PolFdf)
+__device__ __forceinline__ float2 split_hl(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+__global__ void prescale_g_df_kernel(const double4_32a* __restrict__ ps, const int32_t* __restrict__ own,
+                                     const double2* __restrict__ p, int64_t n, double kap, float4* __restrict__ r) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double4_32a y = ps[j];
+  const double2 pe = p[own[j]];
+  const double sc = -kap * y.w / kFourPi;
+  const float2 x = split_hl(kap * y.x), yy = split_hl(kap * y.y), z = split_hl(kap * y.z);
+  const float2 qr = split_hl(sc * pe.x), qi = split_hl(sc * pe.y);
+  r[3 * j] = make_float4(x.x, yy.x, z.x, qr.x);
+  r[3 * j + 1] = make_float4(x.y, yy.y, z.y, qr.y);
+  r[3 * j + 2] = make_float4(qi.x, qi.y, 0.0f, 0.0f);
+}
+
+__global__ void prescale_k_df_kernel(const double4_32a* __restrict__ ps, const double4_32a* __restrict__ nrm,
+                                     const int32_t* __restrict__ own, const double2* __restrict__ p, int64_t n,
+                                     double kap, float4* __restrict__ r) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double4_32a y = ps[j];
+  const double4_32a nn = nrm[j];
+  const double2 pe = p[own[j]];
+  const double sc = kap * kap * nn.w / kFourPi;
+  const float2 x = split_hl(kap * y.x), yy = split_hl(kap * y.y), z = split_hl(kap * y.z);
+  const float2 cr = split_hl(sc * pe.x), ci = split_hl(sc * pe.y);
+  const float2 nx = split_hl(nn.x), ny = split_hl(nn.y), nz = split_hl(nn.z);
+  r[4 * j] = make_float4(x.x, yy.x, z.x, cr.x);
+  r[4 * j + 1] = make_float4(x.y, yy.y, z.y, cr.y);
+  r[4 * j + 2] = make_float4(nx.x, ny.x, nz.x, ci.x);
+  r[4 * j + 3] = make_float4(nx.y, ny.y, nz.y, ci.y);
+}
+
+__global__ void prescale_f_df_kernel(const double4_32a* __restrict__ ps, const double4_32a* __restrict__ vv,
+                                     const int32_t* __restrict__ own, const double2* __restrict__ p, int64_t n,
+                                     double kap, float4* __restrict__ r) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double4_32a y = ps[j];
+  const double4_32a v = vv[j];
+  const double2 pe = p[own[j]];
+  const double sc = -kap * y.w / kFourPi, vs = kap * kap / kFourPi;
+  const float2 x = split_hl(kap * y.x), yy = split_hl(kap * y.y), z = split_hl(kap * y.z);
+  const float2 qr = split_hl(sc * pe.x), qi = split_hl(sc * pe.y);
+  const float2 uxr = split_hl(vs * v.x * pe.x), uxi = split_hl(vs * v.x * pe.y);
+  const float2 uyr = split_hl(vs * v.y * pe.x), uyi = split_hl(vs * v.y * pe.y);
+  const float2 uzr = split_hl(vs * v.z * pe.x), uzi = split_hl(vs * v.z * pe.y);
+  r[6 * j] = make_float4(x.x, yy.x, z.x, qr.x);
+  r[6 * j + 1] = make_float4(x.y, yy.y, z.y, qr.y);
+  r[6 * j + 2] = make_float4(qi.x, qi.y, uxr.x, uxr.y);
+  r[6 * j + 3] = make_float4(uxi.x, uxi.y, uyr.x, uyr.y);
+  r[6 * j + 4] = make_float4(uyi.x, uyi.y, uzr.x, uzr.y);
+  r[6 * j + 5] = make_float4(uzi.x, uzi.y, 0.0f, 0.0f);
+}
+
 // collocation records for the adjoint: c~ = kappa conj(lam)/(4 pi) at kappa x
 __global__ void prescale_colloc_kernel(const double4_32a* __restrict__ tgt, const double2* __restrict__ lam,
                                        int64_t n, double kap, int prec, float4* __restrict__ a32,
@@ -825,6 +1030,14 @@ vsie_status far_prescale(vsie_handle* h, const double2* x, int precision, cudaSt
   Sources& G = h->G;
   Sources& F = h->F;
   Sources& K = h->K;
+  if (precision == 48) {
+    if (G.n) prescale_g_df_kernel<<<nblk(G.n), 256, 0, st>>>(G.pos_s, G.owner, x, G.n, kap, G.rdf);
+    if (K.n) prescale_k_df_kernel<<<nblk(K.n), 256, 0, st>>>(K.pos_s, K.aux, K.owner, x, K.n, kap, K.rdf);
+    if (F.n) prescale_f_df_kernel<<<nblk(F.n), 256, 0, st>>>(F.pos_s, F.vvec, F.owner, x, F.n, kap, F.rdf);
+    if (launches) *launches += (G.n > 0) + (K.n > 0) + (F.n > 0);
+    VSIE_CUDA(cudaGetLastError());
+    return VSIE_OK;
+  }
   if (G.n) {
     prescale_g_kernel<<<nblk(G.n), 256, 0, st>>>(G.pos_s, G.owner, x, G.n, kap, precision, G.r32a,
                                                  G.r32b, G.r64a, G.r64b);
@@ -853,7 +1066,11 @@ struct ForwardPlans {
 static ForwardPlans forward_plans(const vsie_handle* h, int precision) {
   ForwardPlans P;
   const int64_t n = h->n;
-  if (precision == 32) {
+  if (precision == 48) {
+    P.g = plan_sk<double, PolGdf>(h, n, h->G.n);
+    P.k = plan_sk<double, PolKdf>(h, n, h->K.n);
+    P.f = plan_sk<double, PolFdf>(h, n, h->F.n);
+  } else if (precision == 32) {
     P.g = plan_sk<float, PolG2>(h, n, h->G.n, 0);
     P.k = plan_sk<float, PolK2>(h, n, h->K.n, 1);
     P.f = plan_sk<float, PerTarget<float, PolF<float>>>(h, n, h->F.n, 2);
@@ -940,12 +1157,35 @@ static vsie_status forward_sums(vsie_handle* h, double2* y, const ForwardPlans& 
   return VSIE_OK;
 }
 
+static vsie_status forward_sums_df(vsie_handle* h, double2* y, const ForwardPlans& P, double2* slots,
+                                   cudaStream_t st, int phase_mask, int* launches) {
+  int mode = 0;
+  if (h->G.n) {
+    if (phase_mask & 1)
+      VSIE_TRY((run_nbody<double, PolGdf>(PolGdf{{h->tgtdf, h->G.rdf}}, P.g, y, mode, slots, st, launches)));
+    mode = 1;
+  }
+  if (h->K.n) {
+    if (phase_mask & 2)
+      VSIE_TRY((run_nbody<double, PolKdf>(PolKdf{{h->tgtdf, h->K.rdf}}, P.k, y, mode, slots, st, launches)));
+    mode = 1;
+  }
+  if (h->F.n) {
+    if (phase_mask & 4)
+      VSIE_TRY((run_nbody<double, PolFdf>(PolFdf{{h->tgtdf, h->F.rdf}}, P.f, y, mode, slots, st, launches)));
+    mode = 1;
+  }
+  if (!mode && (phase_mask & 1)) VSIE_CUDA(cudaMemsetAsync(y, 0, sizeof(double2) * h->n, st));
+  return VSIE_OK;
+}
+
 static vsie_status forward(vsie_handle* h, double2* y, int precision, double2* slots_given,
                            cudaStream_t st, int phase_mask, int* launches) {
   const ForwardPlans P = forward_plans(h, precision);
   double2* slots = slots_given;
   if (!slots) VSIE_TRY(handle_slots(h, P.slots, &slots));
   if (precision == 32) return forward_sums<float>(h, y, P, slots, st, phase_mask, launches);
+  if (precision == 48) return forward_sums_df(h, y, P, slots, st, phase_mask, launches);
   return forward_sums<double>(h, y, P, slots, st, phase_mask, launches);
 }
 
@@ -1051,7 +1291,7 @@ vsie_status far_sum_f_only(vsie_handle* h, const double2* x, double2* y, int pre
 }
 
 size_t far_split_elems(const vsie_handle* h) {
-  return std::max(forward_plans(h, 32).slots, forward_plans(h, 64).slots);
+  return std::max(std::max(forward_plans(h, 32).slots, forward_plans(h, 64).slots), forward_plans(h, 48).slots);
 }
 
 vsie_status far_sums_into(vsie_handle* h, double2* y, int precision, double2* scratch,

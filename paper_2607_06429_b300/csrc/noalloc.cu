@@ -61,8 +61,8 @@ extern "C" vsie_status vsie_apply_noalloc(vsie_handle* h, const void* d_x, void*
     set_error("vsie_apply_noalloc: null handle or vector");
     return VSIE_ERR_ARG;
   }
-  if (nrhs < 1 || (precision != 32 && precision != 64) || d_x == d_y) {
-    set_error("vsie_apply_noalloc: nrhs must be >= 1, precision 32 or 64, x and y distinct");
+  if (nrhs < 1 || (precision != 32 && precision != 48 && precision != 64) || d_x == d_y) {
+    set_error("vsie_apply_noalloc: nrhs must be >= 1, precision 32, 48 or 64, x and y distinct");
     return VSIE_ERR_ARG;
   }
   const size_t need = far_split_elems(h);

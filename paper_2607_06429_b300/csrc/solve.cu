@@ -339,8 +339,9 @@ extern "C" vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
         inf.fp32_applies += applies;
       else
         inf.fp64_applies += applies;
-      // true residual with the FP64 apply
-      VSIE_TRY(op_apply(h, adjoint, x, S.t, 64, st));
+      // true residual with an FP64-accuracy apply: the double-float sums (precision 48) in
+      // the refinement of a forward solve, plain FP64 otherwise
+      VSIE_TRY(op_apply(h, adjoint, x, S.t, (opts->mode == 32 && !adjoint) ? 48 : 64, st));
       inf.fp64_applies += 1;
       sub_kernel<<<nb256(n), 256, 0, st>>>(b, S.t, S.r, n);
       VSIE_CUDA(cudaGetLastError());

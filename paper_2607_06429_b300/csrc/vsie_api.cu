@@ -276,8 +276,21 @@ static vsie_status create_impl(const vsie_mesh* mesh, const vsie_material* mat, 
   for (int64_t i = 0; i < h->n; ++i)
     tgt32[i] = make_float4((float)(kap * tgt[i].x), (float)(kap * tgt[i].y), (float)(kap * tgt[i].z), 0.0f);
 
+  // double-float copies of kappa x for the precision-48 sums: (hi x3, 0) (lo x3, 0)
+  std::vector<float4> tgtdf(2 * (size_t)h->n);
+  for (int64_t i = 0; i < h->n; ++i) {
+    const double v[3] = {kap * tgt[i].x, kap * tgt[i].y, kap * tgt[i].z};
+    float hi[3], lo[3];
+    for (int d = 0; d < 3; ++d) {
+      hi[d] = (float)v[d];
+      lo[d] = (float)(v[d] - (double)hi[d]);
+    }
+    tgtdf[2 * i] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+    tgtdf[2 * i + 1] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+  }
   VSIE_TRY(upload(h, &h->tgt64, tgt));
   VSIE_TRY(upload(h, &h->tgt32, tgt32));
+  VSIE_TRY(upload(h, &h->tgtdf, tgtdf));
   VSIE_TRY(upload(h, &h->mass, mass));
 
   auto setup_class = [&](Sources& S, const std::vector<double4_32a>& ps, const std::vector<double4_32a>* vv,
@@ -298,6 +311,7 @@ static vsie_status create_impl(const vsie_mesh* mesh, const vsie_material* mat, 
       VSIE_TRY(dalloc_t(h, &S.r32b, (size_t)S.n));
       VSIE_TRY(dalloc_t(h, &S.r64b, (size_t)S.n));
     }
+    VSIE_TRY(dalloc_t(h, &S.rdf, (size_t)(recs == 1 ? 3 : recs == 2 ? 4 : 6) * S.n));
     return VSIE_OK;
   };
   VSIE_TRY(setup_class(h->G, g_ps, nullptr, nullptr, g_own, g_first, g_elem, 1));
@@ -402,8 +416,8 @@ static vsie_status check_apply_args(vsie_handle* h, const void* x, const void* y
     set_error(std::string(who) + ": nrhs must be >= 1");
     return VSIE_ERR_ARG;
   }
-  if (precision != 32 && precision != 64) {
-    set_error(std::string(who) + ": precision must be 32 or 64");
+  if (precision != 32 && precision != 48 && precision != 64) {
+    set_error(std::string(who) + ": precision must be 32, 48 or 64");
     return VSIE_ERR_ARG;
   }
   if (x == y) {
@@ -449,6 +463,10 @@ extern "C" vsie_status vsie_adjoint_apply(vsie_handle* h, const void* d_y, void*
                                           int32_t nrhs, int32_t precision, void* stream) {
   clear_error();
   VSIE_TRY(check_apply_args(h, d_y, d_x, nrhs, precision, "vsie_adjoint_apply"));
+  if (precision == 48) {
+    set_error("vsie_adjoint_apply: precision must be 32 or 64");
+    return VSIE_ERR_ARG;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const double2* lam = (const double2*)d_y;
   double2* x = (double2*)d_x;
@@ -505,6 +523,10 @@ extern "C" vsie_status vsie_apply_batched(vsie_handle* h, const void* d_x, void*
                                           int32_t precision, void* stream) {
   clear_error();
   VSIE_TRY(check_apply_args(h, d_x, d_y, nrhs, precision, "vsie_apply_batched"));
+  if (precision == 48) {
+    set_error("vsie_apply_batched: precision must be 32 or 64");
+    return VSIE_ERR_ARG;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const double2* x = (const double2*)d_x;
   double2* y = (double2*)d_y;

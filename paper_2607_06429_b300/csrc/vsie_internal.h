@@ -55,6 +55,7 @@ struct Sources {
   int64_t n_elem = 0;
   float4* r32a = nullptr;
   float* r32b = nullptr;
+  float4* rdf = nullptr;          // double-float records of the precision-48 sums (3 G, 4 K, 6 F)
   double4_32a* r64a = nullptr;
   double* r64b = nullptr;
   // adjoint target records (built on first adjoint call): (kappa y, s), (kappa v, 0)
@@ -112,6 +113,7 @@ struct vsie_handle {
 
   double4_32a* tgt64 = nullptr;   // (x, y, z, 0) collocation points, FP64
   float4* tgt32 = nullptr;    // FP32 copies of kappa * x (kappa = k0/(2 pi))
+  float4* tgtdf = nullptr;    // double-float kappa * x: (hi, hi, hi, 0) (lo, lo, lo, 0) per point
   double* mass = nullptr;     // mass function m at the collocation points
 
   vsie::Sources G, K, F;

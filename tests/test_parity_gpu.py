@@ -1,7 +1,8 @@
 """Parity of the CUDA library (through the C ABI) with the FP64 CPU oracle.
 
 Tolerances: relative L2 error <= 1e-5 for the FP32 far-field path and <= 1e-12 for the
-FP64 path (full vectors on the small workloads, seeded sampled rows at full size)."""
+FP64 path and the double-float path (precision 48) (full vectors on the small workloads,
+seeded sampled rows at full size)."""
 import numpy as np
 import pytest
 
@@ -61,8 +62,10 @@ def test_apply_full_vector(small_case):
     ref = A @ x
     xd = _cuda(x)
     y64 = op.apply(xd, precision=64).cpu().numpy()
+    y48 = op.apply(xd, precision=48).cpu().numpy()
     y32 = op.apply(xd, precision=32).cpu().numpy()
     assert rel(y64, ref) <= TOL64, (name, rel(y64, ref))
+    assert rel(y48, ref) <= TOL64, (name, rel(y48, ref))  # double-float sums
     assert rel(y32, ref) <= TOL32, (name, rel(y32, ref))
     # repeat: deterministic launch configuration gives bitwise-identical results
     y32b = op.apply(xd, precision=32).cpu().numpy()
@@ -145,6 +148,7 @@ def test_apply_sampled_rows_mid_size(maker, count):
     ref = D.apply_rows(x, rows)
     xd = _cuda(x)
     assert rel(op.apply(xd, precision=64).cpu().numpy()[rows], ref) <= TOL64
+    assert rel(op.apply(xd, precision=48).cpu().numpy()[rows], ref) <= TOL64
     assert rel(op.apply(xd, precision=32).cpu().numpy()[rows], ref) <= TOL32
 
 
@@ -218,6 +222,10 @@ def test_apply_sampled_rows_full_size(name, count):
     D = O.Discretisation.from_workload(w)
     rows = _sample_rows(w, count, 21)
     x = W.random_vector(w.n, 23)
-    y = op.apply(_cuda(x), precision=32).cpu().numpy()
+    xd = _cuda(x)
+    y = op.apply(xd, precision=32).cpu().numpy()
     ref = D.apply_rows(x, rows)
     assert rel(y[rows], ref) <= TOL32, rel(y[rows], ref)
+    if name == "perturbed40_k6":  # per-element contrast: the double-float sums at full size
+        y48 = op.apply(xd, precision=48).cpu().numpy()
+        assert rel(y48[rows], ref) <= TOL64, rel(y48[rows], ref)
