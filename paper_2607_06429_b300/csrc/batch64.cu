@@ -4,7 +4,9 @@
 //
 // Same sums as the FP64 single-column path (Eq. vsie; G and K source classes, positions
 // scaled by kappa = k0/(2 pi), phase in revolutions), but each kernel coefficient C(x_i, y_j)
-// is evaluated once (in FP64) and applied to a block of up to 64 right-hand sides:
+// is evaluated once (in double-float arithmetic on the FP32 pipe, about 2^-47 per
+// operation, the same evaluator as the precision-48 sums) and applied to a block of up
+// to 64 right-hand sides:
 //     Y[i, r] = sum_j C(x_i, y_j) q_j^(r).
 // One block owns 32 targets x 64 right-hand sides; per tile of 32 sources its 256 threads
 // evaluate the 1024 coefficients into shared memory (4 per thread, own target), then each
@@ -32,9 +34,9 @@ constexpr int B64_S = 32;        // sources per tile
 constexpr int B64_R = 64;        // right-hand sides per launch
 constexpr int B64_THREADS = 256;
 constexpr int B64_RPT = B64_R / (B64_THREADS / B64_T);  // right-hand sides per thread (8)
-// shared memory: source positions and normals, then the coefficient tile [S][T], then the
-// charge tile [S][R]
-constexpr size_t B64_SMEM_P = sizeof(double4_32a) * 2 * B64_S;
+// shared memory: source positions and normals (double-float: hi and lo records), then the
+// coefficient tile [S][T], then the charge tile [S][R]
+constexpr size_t B64_SMEM_P = sizeof(float4) * 4 * B64_S;
 constexpr size_t B64_SMEM_C = sizeof(float4) * B64_S * B64_T;
 constexpr size_t B64_SMEM_Q = sizeof(float4) * B64_S * B64_R;
 constexpr size_t B64_SMEM = B64_SMEM_P + B64_SMEM_C + B64_SMEM_Q;
@@ -55,41 +57,20 @@ struct B64Args {
   double2* part;            // [nsplit][B64_R][nt] when nsplit > 1
 };
 
-// coefficient of a G source: e^{2 pi i t} / |d~|;  K source: e^{2 pi i t}(2 pi i t - 1)(d~ . n)/|d~|^3
-template <bool IsK>
-__device__ __forceinline__ double2 coef64(double tx, double ty, double tz, const double4_32a& p,
-                                          const double4_32a& nv) {
-  const double dx = tx - p.x, dy = ty - p.y, dz = tz - p.z;
-  const double r2 = dx * dx + dy * dy + dz * dz;
-  const double rinv = (r2 > 0.0) ? rsqrt(r2) : 0.0;
-  const double t = r2 * rinv;
-  const double f = t - rint(t);
-  double sn, cs;
-  sincospi(2.0 * f, &sn, &cs);
-  if (!IsK) return make_double2(cs * rinv, sn * rinv);
-  const double dn = dx * nv.x + dy * nv.y + dz * nv.z;
-  const double g3 = rinv * rinv * rinv * dn;
-  const double kr = t * 6.28318530717958647692;
-  return make_double2((-cs - kr * sn) * g3, (kr * cs - sn) * g3);
-}
-
 template <bool IsK>
 __global__ void __launch_bounds__(B64_THREADS, 2) b64_kernel(B64Args a) {
   extern __shared__ __align__(16) unsigned char sm[];
-  double4_32a* sp = reinterpret_cast<double4_32a*>(sm);                  // kappa-scaled positions
-  double4_32a* sn = sp + B64_S;                                           // normals (K)
+  float4* sp = reinterpret_cast<float4*>(sm);  // [4][S]: kappa y hi, lo; normal hi, lo (K)
   float4* sC = reinterpret_cast<float4*>(sm + B64_SMEM_P);               // [S][T] coefficients (double-float)
   float4* sQ = reinterpret_cast<float4*>(sm + B64_SMEM_P + B64_SMEM_C);  // [S][R] charges (double-float)
   const int tid = threadIdx.x;
   const int t = tid & (B64_T - 1), rg = tid / B64_T;
   const int64_t i = (int64_t)blockIdx.x * B64_T + t;
   const bool tok = i < a.nt;
-  double tx = 0.0, ty = 0.0, tz = 0.0;
+  DTgt tg{dfs{0.0f, 0.0f}, dfs{0.0f, 0.0f}, dfs{0.0f, 0.0f}};
   if (tok) {
     const double4_32a p = a.tgt[i];
-    tx = p.x * a.kap;
-    ty = p.y * a.kap;
-    tz = p.z * a.kap;
+    tg = DTgt{dfs_make(p.x * a.kap), dfs_make(p.y * a.kap), dfs_make(p.z * a.kap)};
   }
   float2 accS[B64_RPT], accC[B64_RPT];  // double-float sums: hi parts, collected rounding errors
 #pragma unroll
@@ -101,14 +82,23 @@ __global__ void __launch_bounds__(B64_THREADS, 2) b64_kernel(B64Args a) {
     const int64_t j0 = tile * B64_S;
     if (tid < B64_S) {
       const int64_t j = j0 + tid;
-      double4_32a p = make_double4_32a(0, 0, 0, 0), nv = make_double4_32a(0, 0, 0, 0);
+      float4 ph = make_float4(0, 0, 0, 0), pl = ph, nh = ph, nl = ph;
       if (j < a.ns) {
         const double4_32a q = a.pos[j];
-        p = make_double4_32a(q.x * a.kap, q.y * a.kap, q.z * a.kap, 0.0);
-        if (IsK) nv = a.nrm[j];
+        const dfs x = dfs_make(q.x * a.kap), y = dfs_make(q.y * a.kap), z = dfs_make(q.z * a.kap);
+        ph = make_float4(x.h, y.h, z.h, 0.0f);
+        pl = make_float4(x.l, y.l, z.l, 0.0f);
+        if (IsK) {
+          const double4_32a nv = a.nrm[j];
+          const dfs nx = dfs_make(nv.x), ny = dfs_make(nv.y), nz = dfs_make(nv.z);
+          nh = make_float4(nx.h, ny.h, nz.h, 0.0f);
+          nl = make_float4(nx.l, ny.l, nz.l, 0.0f);
+        }
       }
-      sp[tid] = p;
-      sn[tid] = nv;
+      sp[tid] = ph;
+      sp[B64_S + tid] = pl;
+      sp[2 * B64_S + tid] = nh;
+      sp[3 * B64_S + tid] = nl;
     }
     for (int e = tid; e < B64_S * B64_R; e += B64_THREADS) {
       const int64_t j = j0 + e / B64_R;
@@ -118,7 +108,13 @@ __global__ void __launch_bounds__(B64_THREADS, 2) b64_kernel(B64Args a) {
 #pragma unroll 2
     for (int q = 0; q < B64_S / (B64_THREADS / B64_T); ++q) {
       const int jj = rg + (B64_THREADS / B64_T) * q;
-      sC[jj * B64_T + t] = df_pack(coef64<IsK>(tx, ty, tz, sp[jj], sn[jj]));
+      if (IsK) {
+        const float4 nh = sp[2 * B64_S + jj], nl = sp[3 * B64_S + jj];
+        sC[jj * B64_T + t] =
+            df_coef_k(tg, sp[jj], sp[B64_S + jj], dfs{nh.x, nl.x}, dfs{nh.y, nl.y}, dfs{nh.z, nl.z});
+      } else {
+        sC[jj * B64_T + t] = df_coef_g(tg, sp[jj], sp[B64_S + jj]);
+      }
     }
     __syncthreads();
 #pragma unroll 1

@@ -203,4 +203,46 @@ __device__ __forceinline__ void dfs_cossin_2pi(dfs f, dfs& c, dfs& s) {
   s = sv;
 }
 
+struct DTgt {
+  dfs x, y, z;
+};
+
+// d = t - y~ (y~ from records a = (x.h, y.h, z.h, *), b = (x.l, y.l, z.l, *)); rinv = 1/|d|
+// (0 at d = 0), tt = |d| (revolutions), (cs, sn) = (cos, sin)(2 pi tt)
+__device__ __forceinline__ void df_geometry(const DTgt& t, const float4& a, const float4& b, dfs& dx, dfs& dy,
+                                            dfs& dz, dfs& rinv, dfs& tt, dfs& cs, dfs& sn) {
+  dx = dfs_sub(t.x, dfs{a.x, b.x});
+  dy = dfs_sub(t.y, dfs{a.y, b.y});
+  dz = dfs_sub(t.z, dfs{a.z, b.z});
+  const dfs r2 = dfs_add(dfs_add(dfs_sqr(dx), dfs_sqr(dy)), dfs_sqr(dz));
+  const bool zero = !(r2.h > 0.0f);
+  rinv = dfs_rsqrt(zero ? dfs{1.0f, 0.0f} : r2);
+  if (zero) rinv = dfs{0.0f, 0.0f};
+  tt = dfs_mul(r2, rinv);
+  const float n = rintf(tt.h);
+  const dfs f = dfs_two_sum(__fsub_rn(tt.h, n), tt.l);
+  dfs_cossin_2pi(f, cs, sn);
+}
+
+__device__ __forceinline__ float4 df_c4(dfs re, dfs im) { return make_float4(re.h, im.h, re.l, im.l); }
+
+// G coefficient e^{2 pi i t} / |d~|  and K coefficient e^{2 pi i t}(2 pi i t - 1)(d~ . n)/|d~|^3
+// as double-float complex numbers (re.hi, im.hi, re.lo, im.lo)
+__device__ __forceinline__ float4 df_coef_g(const DTgt& t, const float4& a, const float4& b) {
+  dfs dx, dy, dz, rinv, tt, cs, sn;
+  df_geometry(t, a, b, dx, dy, dz, rinv, tt, cs, sn);
+  return df_c4(dfs_mul(cs, rinv), dfs_mul(sn, rinv));
+}
+__device__ __forceinline__ float4 df_coef_k(const DTgt& t, const float4& a, const float4& b, dfs nx, dfs ny,
+                                            dfs nz) {
+  dfs dx, dy, dz, rinv, tt, cs, sn;
+  df_geometry(t, a, b, dx, dy, dz, rinv, tt, cs, sn);
+  const dfs dn = dfs_add(dfs_add(dfs_mul(dx, nx), dfs_mul(dy, ny)), dfs_mul(dz, nz));
+  const dfs g3 = dfs_mul(dfs_mul(dfs_sqr(rinv), rinv), dn);
+  const dfs kr = dfs_mul(tt, dfc_two_pi());
+  const dfs A = dfs_add(cs, dfs_mul(kr, sn));  // cos + kr sin
+  const dfs Q = dfs_sub(dfs_mul(kr, cs), sn);  // kr cos - sin
+  return df_c4(dfs_neg(dfs_mul(g3, A)), dfs_mul(g3, Q));
+}
+
 }  // namespace vsie

@@ -542,29 +542,6 @@ struct PolK2 {
 // the packed double-float complex multiply-add.  The partial sum of a 128-source tile is
 // converted to FP64 and added to the target's FP64 accumulator.
 
-struct DTgt {
-  dfs x, y, z;
-};
-
-// d = t - y~ (y~ from records a = (x.h, y.h, z.h, *), b = (x.l, y.l, z.l, *)); rinv = 1/|d|
-// (0 at d = 0), tt = |d| (revolutions), (cs, sn) = (cos, sin)(2 pi tt)
-__device__ __forceinline__ void df_geometry(const DTgt& t, const float4& a, const float4& b, dfs& dx, dfs& dy,
-                                            dfs& dz, dfs& rinv, dfs& tt, dfs& cs, dfs& sn) {
-  dx = dfs_sub(t.x, dfs{a.x, b.x});
-  dy = dfs_sub(t.y, dfs{a.y, b.y});
-  dz = dfs_sub(t.z, dfs{a.z, b.z});
-  const dfs r2 = dfs_add(dfs_add(dfs_sqr(dx), dfs_sqr(dy)), dfs_sqr(dz));
-  const bool zero = !(r2.h > 0.0f);
-  rinv = dfs_rsqrt(zero ? dfs{1.0f, 0.0f} : r2);
-  if (zero) rinv = dfs{0.0f, 0.0f};
-  tt = dfs_mul(r2, rinv);
-  const float n = rintf(tt.h);
-  const dfs f = dfs_two_sum(__fsub_rn(tt.h, n), tt.l);
-  dfs_cossin_2pi(f, cs, sn);
-}
-
-__device__ __forceinline__ float4 df_c4(dfs re, dfs im) { return make_float4(re.h, im.h, re.l, im.l); }
-
 template <int NREC>
 struct DfBase {
   struct Smem {
@@ -626,9 +603,7 @@ struct PolGdf : DfBase<3> {
     const float4 qv = make_float4(s.r[0].w, s.r[2].x, s.r[1].w, s.r[2].y);
 #pragma unroll
     for (int t = 0; t < kT; ++t) {
-      dfs dx, dy, dz, rinv, tt, cs, sn;
-      df_geometry(tg.t[t], s.r[0], s.r[1], dx, dy, dz, rinv, tt, cs, sn);
-      df_cmac(q.S[t], q.C[t], df_c4(dfs_mul(cs, rinv), dfs_mul(sn, rinv)), qv);
+      df_cmac(q.S[t], q.C[t], df_coef_g(tg.t[t], s.r[0], s.r[1]), qv);
     }
   }
 };
@@ -641,14 +616,7 @@ struct PolKdf : DfBase<4> {
     const dfs nx{s.r[2].x, s.r[3].x}, ny{s.r[2].y, s.r[3].y}, nz{s.r[2].z, s.r[3].z};
 #pragma unroll
     for (int t = 0; t < kT; ++t) {
-      dfs dx, dy, dz, rinv, tt, cs, sn;
-      df_geometry(tg.t[t], s.r[0], s.r[1], dx, dy, dz, rinv, tt, cs, sn);
-      const dfs dn = dfs_add(dfs_add(dfs_mul(dx, nx), dfs_mul(dy, ny)), dfs_mul(dz, nz));
-      const dfs g3 = dfs_mul(dfs_mul(dfs_sqr(rinv), rinv), dn);
-      const dfs kr = dfs_mul(tt, dfc_two_pi());
-      const dfs A = dfs_add(cs, dfs_mul(kr, sn));  // cos + kr sin
-      const dfs Q = dfs_sub(dfs_mul(kr, cs), sn);  // kr cos - sin
-      df_cmac(q.S[t], q.C[t], df_c4(dfs_neg(dfs_mul(g3, A)), dfs_mul(g3, Q)), cv);
+      df_cmac(q.S[t], q.C[t], df_coef_k(tg.t[t], s.r[0], s.r[1], nx, ny, nz), cv);
     }
   }
 };
