@@ -401,6 +401,49 @@ def far_field_matrix(D: Discretisation, dirs) -> np.ndarray:
     return F / FOUR_PI
 
 
+def far_source_points(D):
+    """The far-rule source points y_j of the discretisation and their owning unknowns:
+    tetrahedron centroids (or the four points of the degree-2 rule when far_points == 4),
+    then the three interior points of every interface triangle."""
+    if D.far_points == 4:
+        tp = D.tet_pts.reshape(-1, 3)
+        town = np.repeat(np.arange(D.n_tet), 4)
+    else:
+        tp = D.tet_cen
+        town = np.arange(D.n_tet)
+    sp = D.tri_pts.reshape(-1, 3)
+    sown = D.n_tet + np.repeat(np.arange(D.n_tri), 3)
+    return np.concatenate([tp, sp], axis=0), np.concatenate([town, sown])
+
+
+def gradient_channels(D, lam, points):
+    """Derivative channels of the operator's columns with respect to the source weights,
+    for an adjoint state lam: at every point y_j
+        Phi_j = sum_i conj(G(x_i, y_j)) lam_i,   Psi_j = sum_i conj(grad_x G(x_i, y_j)) lam_i,
+    over all collocation points x_i (terms with x_i = y_j vanish), G = e^{ikr}/(4 pi r)
+    (Eq. greens_function), grad_x G = G (i k r - 1)(x - y)/r^2.  With the pair coefficient
+    C = -G s + grad_x G . v of a source point (pair_kernel), sum_i conj(dC/ds) lam_i = -Phi
+    and sum_i conj(dC/dv) lam_i = Psi.  Returns (Phi (m,), Psi (m, 3))."""
+    points = np.asarray(points, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.complex128)
+    k = D.k0
+    m = points.shape[0]
+    phi = np.zeros(m, dtype=np.complex128)
+    psi = np.zeros((m, 3), dtype=np.complex128)
+    step = max(1, int(2.0e6 // max(D.n, 1)))
+    for a in range(0, m, step):
+        Y = points[a:a + step]
+        d = D.targets[None, :, :] - Y[:, None, :]          # x_i - y_j
+        r2 = np.einsum("jil,jil->ji", d, d)
+        ok = r2 > 0.0
+        r = np.sqrt(np.where(ok, r2, 1.0))
+        G = np.where(ok, green(r, k), 0.0)
+        phi[a:a + step] = np.conj(G) @ lam
+        g = np.where(ok, G * (1j * k * r - 1.0) / (r * r), 0.0)
+        psi[a:a + step] = np.einsum("ji,jil,i->jl", np.conj(g), d, lam)
+    return phi, psi
+
+
 def misfit_and_gradient(w, dirs, target, direction):
     """L = 1/2 sum_d |p_inf(xhat_d) - t_d|^2 for the solution of A p = p_inc, and dL/drho_e,
     dL/dc_e for every tetrahedron (piecewise-constant density inside each element, interface

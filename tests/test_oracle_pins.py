@@ -420,3 +420,75 @@ def test_misfit_gradient_vs_finite_differences():
         # element-wise constant density without a density-gradient term: the element's
         # column scales as 1/rho_e and p_e absorbs it, so dL/drho_e vanishes
         assert abs(fdr) <= 1e-6 * np.max(np.abs(gc)) and abs(grho[e]) <= 1e-10 * np.max(np.abs(gc))
+
+
+# ----------------------------------------------------------------- gradient channels
+
+def test_gradient_channels_against_assembled_columns():
+    """Phi and Psi (derivative channels of the columns with respect to the source weights)
+    against the oracle's own assembled operator: the column of an element assembled with
+    unit weights (unit single-layer weight, or unit grad(alpha) along one axis, or unit
+    interface jump) contracted with an adjoint state that vanishes on the element's self
+    and near rows equals the weighted sum of the channels over the element's points."""
+    import copy
+    w = W.single_ball(4, 1, 2.0)              # four-point rule on every tetrahedron
+    D = O.Discretisation.from_workload(w)
+    pts, own = O.far_source_points(D)
+    rng = np.random.default_rng(3)
+    lam = rng.normal(size=D.n) + 1j * rng.normal(size=D.n)
+
+    def unit(sd=None, ga=None, om=None):
+        U = copy.copy(D)
+        U.sdens = np.zeros(D.n_tet) if sd is None else sd
+        U.grad_alpha = np.zeros((D.n_tet, 3)) if ga is None else ga
+        U.tri_omega = np.zeros(D.n_tri) if om is None else om
+        U.mass = np.zeros(D.n)
+        return U.matrix_rows(np.arange(D.n))
+
+    e = 7
+    lam_e = lam.copy()
+    lam_e[e] = 0.0                            # the self row holds the ball self term
+    phi, psi = O.gradient_channels(D, lam_e, pts)
+    sel = own == e
+    w4 = D.tet_vol[e] / 4.0
+    ind = np.zeros(D.n_tet)
+    ind[e] = 1.0
+    lhs = np.vdot(unit(sd=ind)[:, e], lam_e)
+    assert abs(lhs - (-w4 * phi[sel].sum())) <= 1e-12 * abs(lhs)
+    for c in range(3):
+        ga = np.zeros((D.n_tet, 3))
+        ga[e, c] = 1.0
+        lhs = np.vdot(unit(ga=ga)[:, e], lam_e)
+        assert abs(lhs - w4 * psi[sel, c].sum()) <= 1e-12 * abs(lhs)
+
+    t = 5
+    d = D.targets - D.tri_cen[t]
+    near = np.einsum("ij,ij->i", d, d) < D.tri_near_radius ** 2
+    near[D.n_tet + t] = True
+    lam_t = lam.copy()
+    lam_t[near] = 0.0
+    phi, psi = O.gradient_channels(D, lam_t, pts)
+    sel = own == D.n_tet + t
+    om = np.zeros(D.n_tri)
+    om[t] = 1.0
+    lhs = np.vdot(unit(om=om)[:, D.n_tet + t], lam_t)   # v = -omega n w
+    rhs = (D.tri_area[t] / 3.0) * (-(psi[sel] @ D.tri_nrm[t])).sum()
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_gradient_channel_psi_is_minus_gradient_of_phi():
+    """Psi = -grad_y Phi (grad_x G = -grad_y G): central differences of Phi in the point."""
+    w = W.single_ball(4, 1, 2.0)
+    D = O.Discretisation.from_workload(w)
+    rng = np.random.default_rng(8)
+    lam = rng.normal(size=D.n) + 1j * rng.normal(size=D.n)
+    y = np.array([[0.31, -0.17, 0.52], [1.4, 0.2, -0.3]])   # inside and outside the ball
+    _, psi = O.gradient_channels(D, lam, y)
+    h = 1e-5
+    for c in range(3):
+        e = np.zeros(3)
+        e[c] = h
+        fp, _ = O.gradient_channels(D, lam, y + e)
+        fm, _ = O.gradient_channels(D, lam, y - e)
+        fd = -(fp - fm) / (2 * h)
+        assert np.allclose(fd, psi[:, c], rtol=1e-7, atol=1e-9 * np.abs(psi).max())
