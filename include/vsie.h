@@ -272,6 +272,25 @@ vsie_status vsie_solve_batched(vsie_handle* h, const void* d_b, void* d_x, int32
 vsie_status vsie_far_field_adjoint(vsie_handle* h, const void* d_r, int32_t nrhs,
                                    const double* h_dirs, int32_t ndir, void* d_x, void* stream);
 
+/* Gradient channels of an adjoint state lam (device complex128, n): for every far-field
+ * source point y_j (the order of vsie_source_points)
+ *   phi_j = sum_i conj(G(x_i, y_j)) lam_i,   psi_j = sum_i conj(grad_x G(x_i, y_j)) lam_i,
+ * over all collocation points x_i (terms with x_i = y_j vanish), G = e^{ik0 r}/(4 pi r)
+ * (Eq. greens_function), grad_x G = G (i k0 r - 1)(x - y)/r^2.  A source point's pair
+ * coefficient is C = -G s + grad_x G . v (Eq. vsie), so sum_i conj(dC/ds) lam_i = -phi_j
+ * and sum_i conj(dC/dv) lam_i = psi_j: the far-field parts of the derivative of
+ * lam^H A p with respect to the source weights s_j and v_j.  d_phi: device complex128
+ * n_far; d_psi: device complex128 3 n_far (x, y, z per point).  precision 32 or 64.
+ * Asynchronous; the first call allocates the adjoint buffers. */
+vsie_status vsie_gradient_channels(vsie_handle* h, const void* d_lam, int32_t precision, void* d_phi,
+                                   void* d_psi, void* stream);
+
+/* The far-field source points in the library's order (volume points with grad(alpha) = 0,
+ * interface points, volume points with grad(alpha) != 0): h_xyz 3 n_far doubles (may be
+ * NULL), h_owner n_far owning unknowns (may be NULL), h_class n_far class indices 0, 1, 2
+ * (may be NULL).  Host arrays, caller-owned; blocking. */
+vsie_status vsie_source_points(const vsie_handle* h, double* h_xyz, int32_t* h_owner, int32_t* h_class);
+
 /* Thread-local description of the last error ("" if none). */
 const char* vsie_last_error(void);
 

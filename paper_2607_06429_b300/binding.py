@@ -28,7 +28,7 @@ EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_appl
            "vsie_adjoint_apply", "vsie_plane_wave_rhs", "vsie_far_field", "vsie_solve",
            "vsie_far_field_adjoint", "vsie_solve_batched", "vsie_apply_batched_multi",
            "vsie_graph_create_batched", "vsie_graph_launch", "vsie_graph_nodes", "vsie_graph_destroy",
-           "vsie_autotune",
+           "vsie_autotune", "vsie_gradient_channels", "vsie_source_points",
            "vsie_last_error")
 
 
@@ -123,6 +123,8 @@ def load_library(path: str = LIB_PATH):
                                               I32, ctypes.POINTER(P)]
     lib.vsie_graph_launch.argtypes = [P, P]
     lib.vsie_autotune.argtypes = [P, I32, ctypes.POINTER(_Tuning), P]
+    lib.vsie_gradient_channels.argtypes = [P, P, I32, P, P, P]
+    lib.vsie_source_points.argtypes = [P, P, P, P]
     lib.vsie_graph_nodes.argtypes = [P, ctypes.POINTER(I64)]
     lib.vsie_graph_destroy.argtypes = [P]
     lib.vsie_graph_destroy.restype = None
@@ -243,6 +245,26 @@ class Operator:
         _check(_lib.vsie_apply_batched(self._h, _dev(x, "x"), _dev(y, "y"), nrhs, int(precision),
                                        _stream(stream)))
         return y
+
+    def source_points(self):
+        """(positions (n_far, 3), owners (n_far,), classes (n_far,)) of the far-field source
+        points in the library's order (vsie_source_points)."""
+        xyz = np.empty((self.n_far_sources, 3), dtype=np.float64)
+        own = np.empty(self.n_far_sources, dtype=np.int32)
+        cls = np.empty(self.n_far_sources, dtype=np.int32)
+        _check(_lib.vsie_source_points(self._h, _ptr(xyz), _ptr(own), _ptr(cls)))
+        return xyz, own, cls
+
+    def gradient_channels(self, lam, precision=64, stream=None):
+        """(phi (n_far,), psi (n_far, 3)) of an adjoint state lam (vsie_gradient_channels)."""
+        import torch
+        if lam.dim() != 1 or lam.shape[0] != self.n:
+            raise ValueError("lam must have shape (n,)")
+        phi = torch.empty(self.n_far_sources, dtype=torch.complex128, device=lam.device)
+        psi = torch.empty((self.n_far_sources, 3), dtype=torch.complex128, device=lam.device)
+        _check(_lib.vsie_gradient_channels(self._h, _dev(lam, "lam"), int(precision), _dev(phi, "phi"),
+                                           _dev(psi, "psi"), _stream(stream)))
+        return phi, psi
 
     def autotune(self, far=True, batched=True, stream=None):
         """Time candidate work shapes on this operator and keep the fastest (vsie_autotune);

@@ -1269,31 +1269,41 @@ vsie_status far_sums_into(vsie_handle* h, double2* y, int precision, double2* sc
 
 // ----------------------------------------------------------------- adjoint apply
 
+// Per-point target records and collocation-record buffers of the adjoint sums (built on
+// the first adjoint call).
+static vsie_status adjoint_buffers(vsie_handle* h, cudaStream_t st) {
+  const int64_t n = h->n;
+  const double kap = h->k0 / kTwoPi;
+  AdjRecords* A = &h->adj;
+  Sources* cls[3] = {&h->G, &h->K, &h->F};
+  if (A->w) return VSIE_OK;
+  int64_t maxn = 1;
+  for (Sources* S : cls) maxn = std::max<int64_t>(maxn, S->n);
+  for (Sources* S : cls) {
+    VSIE_TRY(dalloc_t(h, &S->adj_p32, (size_t)S->n));
+    VSIE_TRY(dalloc_t(h, &S->adj_v32, (size_t)S->n));
+    VSIE_TRY(dalloc_t(h, &S->adj_p64, (size_t)S->n));
+    VSIE_TRY(dalloc_t(h, &S->adj_v64, (size_t)S->n));
+    if (S->n)
+      point_records_kernel<<<nblk(S->n), 256, 0, st>>>(S->pos_s, S->vvec, S->n, kap, S->adj_p32, S->adj_v32,
+                                                        S->adj_p64, S->adj_v64);
+  }
+  VSIE_TRY(dalloc_t(h, &A->c_a32, (size_t)n));
+  VSIE_TRY(dalloc_t(h, &A->c_b32, (size_t)n));
+  VSIE_TRY(dalloc_t(h, &A->c_a64, (size_t)n));
+  VSIE_TRY(dalloc_t(h, &A->c_b64, (size_t)n));
+  VSIE_TRY(dalloc_t(h, &A->w, (size_t)maxn));
+  VSIE_CUDA(cudaGetLastError());
+  return VSIE_OK;
+}
+
 vsie_status far_adjoint(vsie_handle* h, const double2* lam, double2* x, int precision,
                         cudaStream_t st) {
   const int64_t n = h->n;
   const double kap = h->k0 / kTwoPi;
   AdjRecords* A = &h->adj;
   Sources* cls[3] = {&h->G, &h->K, &h->F};
-  if (!A->w) {
-    int64_t maxn = 1;
-    for (Sources* S : cls) maxn = std::max<int64_t>(maxn, S->n);
-    for (Sources* S : cls) {
-      VSIE_TRY(dalloc_t(h, &S->adj_p32, (size_t)S->n));
-      VSIE_TRY(dalloc_t(h, &S->adj_v32, (size_t)S->n));
-      VSIE_TRY(dalloc_t(h, &S->adj_p64, (size_t)S->n));
-      VSIE_TRY(dalloc_t(h, &S->adj_v64, (size_t)S->n));
-      if (S->n)
-        point_records_kernel<<<nblk(S->n), 256, 0, st>>>(S->pos_s, S->vvec, S->n, kap, S->adj_p32,
-                                                          S->adj_v32, S->adj_p64, S->adj_v64);
-    }
-    VSIE_TRY(dalloc_t(h, &A->c_a32, (size_t)n));
-    VSIE_TRY(dalloc_t(h, &A->c_b32, (size_t)n));
-    VSIE_TRY(dalloc_t(h, &A->c_a64, (size_t)n));
-    VSIE_TRY(dalloc_t(h, &A->c_b64, (size_t)n));
-    VSIE_TRY(dalloc_t(h, &A->w, (size_t)maxn));
-    VSIE_CUDA(cudaGetLastError());
-  }
+  VSIE_TRY(adjoint_buffers(h, st));
   prescale_colloc_kernel<<<nblk(n), 256, 0, st>>>(h->tgt64, lam, n, kap, precision, A->c_a32, A->c_b32,
                                                   A->c_a64, A->c_b64);
   VSIE_CUDA(cudaGetLastError());
@@ -1349,6 +1359,92 @@ vsie_status far_adjoint(vsie_handle* h, const double2* lam, double2* x, int prec
     }
   }
   VSIE_CUDA(cudaGetLastError());
+  return VSIE_OK;
+}
+
+// ----------------------------------------------------------------- gradient channels
+
+// Target records of one channel pass over the source points of a class: (kappa y, s') with
+// s' = -1 for Phi (the adjoint sum then equals sum_i e^{ikr}/(4 pi r) conj(lam_i)), else 0,
+// and v' = the unit vector of axis ch - 1 (not scaled by kappa) for Psi.
+__global__ void channel_records_kernel(const double4_32a* __restrict__ ps, int64_t n, double kap, int ch,
+                                       float4* __restrict__ p32, float4* __restrict__ v32,
+                                       double4_32a* __restrict__ p64, double4_32a* __restrict__ v64) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double4_32a y = ps[j];
+  const double s = ch == 0 ? -1.0 : 0.0;
+  const double vx = ch == 1 ? 1.0 : 0.0, vy = ch == 2 ? 1.0 : 0.0, vz = ch == 3 ? 1.0 : 0.0;
+  p32[j] = make_float4((float)(kap * y.x), (float)(kap * y.y), (float)(kap * y.z), (float)s);
+  v32[j] = make_float4((float)vx, (float)vy, (float)vz, 0.0f);
+  p64[j] = make_double4_32a(kap * y.x, kap * y.y, kap * y.z, s);
+  v64[j] = make_double4_32a(vx, vy, vz, 0.0);
+}
+
+// Phi_j = conj(w_j);  Psi_j[ch - 1] = conj(kappa w_j) (the unit v' carried 1/kappa)
+__global__ void channel_out_kernel(const double2* __restrict__ w, int64_t n, int ch, double kap,
+                                   double2* __restrict__ phi, double2* __restrict__ psi) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double2 v = w[j];
+  if (ch == 0)
+    phi[j] = make_double2(v.x, -v.y);
+  else
+    psi[3 * j + ch - 1] = make_double2(kap * v.x, -kap * v.y);
+}
+
+vsie_status gradient_channels(vsie_handle* h, const double2* lam, int precision, double2* phi, double2* psi,
+                              cudaStream_t st) {
+  const int64_t n = h->n;
+  const double kap = h->k0 / kTwoPi;
+  AdjRecords* A = &h->adj;
+  VSIE_TRY(adjoint_buffers(h, st));
+  Sources* cls[3] = {&h->G, &h->K, &h->F};
+  int64_t maxn = 1;
+  for (Sources* S : cls) maxn = std::max<int64_t>(maxn, S->n);
+  if (!A->ch_p32) {
+    VSIE_TRY(dalloc_t(h, &A->ch_p32, (size_t)maxn));
+    VSIE_TRY(dalloc_t(h, &A->ch_v32, (size_t)maxn));
+    VSIE_TRY(dalloc_t(h, &A->ch_p64, (size_t)maxn));
+    VSIE_TRY(dalloc_t(h, &A->ch_v64, (size_t)maxn));
+  }
+  prescale_colloc_kernel<<<nblk(n), 256, 0, st>>>(h->tgt64, lam, n, kap, precision, A->c_a32, A->c_b32,
+                                                  A->c_a64, A->c_b64);
+  VSIE_CUDA(cudaGetLastError());
+  int64_t off = 0;
+  for (int c = 0; c < 3; ++c) {
+    Sources& S = *cls[c];
+    if (!S.n) continue;
+    for (int ch = 0; ch < 4; ++ch) {
+      channel_records_kernel<<<nblk(S.n), 256, 0, st>>>(S.pos_s, S.n, kap, ch, A->ch_p32, A->ch_v32, A->ch_p64,
+                                                         A->ch_v64);
+      double2* slots = nullptr;
+      if (precision == 32) {
+        using PA = PerTarget<float, PolAF<float>>;
+        const StreamK sk = plan_sk<float, PA>(h, S.n, n);
+        VSIE_TRY(handle_slots(h, slot_elems(sk), &slots));
+        PA p;
+        p.tps = A->ch_p32;
+        p.tv = A->ch_v32;
+        p.sa = A->c_a32;
+        p.sb = A->c_b32;
+        VSIE_TRY((run_nbody<float, PA>(p, sk, A->w, 0, slots, st, nullptr)));
+      } else {
+        using PA = PerTarget<double, PolAF<double>>;
+        const StreamK sk = plan_sk<double, PA>(h, S.n, n);
+        VSIE_TRY(handle_slots(h, slot_elems(sk), &slots));
+        PA p;
+        p.tps = A->ch_p64;
+        p.tv = A->ch_v64;
+        p.sa = A->c_a64;
+        p.sb = A->c_b64;
+        VSIE_TRY((run_nbody<double, PA>(p, sk, A->w, 0, slots, st, nullptr)));
+      }
+      channel_out_kernel<<<nblk(S.n), 256, 0, st>>>(A->w, S.n, ch, kap, phi + off, psi + 3 * off);
+      VSIE_CUDA(cudaGetLastError());
+    }
+    off += S.n;
+  }
   return VSIE_OK;
 }
 

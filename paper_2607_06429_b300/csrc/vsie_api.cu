@@ -588,6 +588,46 @@ vsie_status apply_batched_multi_launch(vsie_handle* const* hs, int nop, const do
 
 }  // namespace vsie
 
+extern "C" vsie_status vsie_gradient_channels(vsie_handle* h, const void* d_lam, int32_t precision, void* d_phi,
+                                              void* d_psi, void* stream) {
+  clear_error();
+  if (!h || !d_lam || !d_phi || !d_psi || (precision != 32 && precision != 64)) {
+    set_error("vsie_gradient_channels: null argument or precision not 32 / 64");
+    return VSIE_ERR_ARG;
+  }
+  return gradient_channels(h, (const double2*)d_lam, precision, (double2*)d_phi, (double2*)d_psi,
+                           (cudaStream_t)stream);
+}
+
+extern "C" vsie_status vsie_source_points(const vsie_handle* h, double* h_xyz, int32_t* h_owner,
+                                          int32_t* h_class) {
+  clear_error();
+  if (!h) {
+    set_error("vsie_source_points: null handle");
+    return VSIE_ERR_ARG;
+  }
+  const Sources* cls[3] = {&h->G, &h->K, &h->F};
+  int64_t off = 0;
+  for (int c = 0; c < 3; ++c) {
+    const Sources& S = *cls[c];
+    if (!S.n) continue;
+    if (h_xyz) {
+      std::vector<double4_32a> ps((size_t)S.n);
+      VSIE_CUDA(cudaMemcpy(ps.data(), S.pos_s, sizeof(double4_32a) * S.n, cudaMemcpyDeviceToHost));
+      for (int64_t j = 0; j < S.n; ++j) {
+        h_xyz[3 * (off + j)] = ps[j].x;
+        h_xyz[3 * (off + j) + 1] = ps[j].y;
+        h_xyz[3 * (off + j) + 2] = ps[j].z;
+      }
+    }
+    if (h_owner) VSIE_CUDA(cudaMemcpy(h_owner + off, S.owner, sizeof(int32_t) * S.n, cudaMemcpyDeviceToHost));
+    if (h_class)
+      for (int64_t j = 0; j < S.n; ++j) h_class[off + j] = c;
+    off += S.n;
+  }
+  return VSIE_OK;
+}
+
 namespace vsie {
 
 // deterministic pseudo-random complex values in [-1, 1) (a 64-bit integer hash of i + seed)

@@ -82,6 +82,11 @@ struct AdjRecords {
   double4_32a* c_a64 = nullptr;
   double* c_b64 = nullptr;
   double2* w = nullptr;      // per-source-point sums
+  // target records of the gradient-channel passes (built per pass)
+  float4* ch_p32 = nullptr;
+  float4* ch_v32 = nullptr;
+  double4_32a* ch_p64 = nullptr;
+  double4_32a* ch_v64 = nullptr;
 };
 
 // Buffers of the tensor-core multi-RHS path (grown on demand).
@@ -179,6 +184,10 @@ vsie_status correction_apply(vsie_handle* h, const double2* x, double2* y, int p
 // time with one pass over the correction matrix per 64 columns
 vsie_status correction_apply_block(vsie_handle* h, const double2* x, double2* y, int ncols, int precision,
                                    cudaStream_t st);
+// Gradient channels at every far-field source point (classes G, K, F in order):
+// phi_j = sum_i conj(G(x_i, y_j)) lam_i, psi_j = sum_i conj(grad_x G(x_i, y_j)) lam_i (3 per point)
+vsie_status gradient_channels(vsie_handle* h, const double2* lam, int precision, double2* phi, double2* psi,
+                              cudaStream_t st);
 // x += conj(m) lam + Delta^H lam
 vsie_status correction_adjoint(vsie_handle* h, const double2* lam, double2* x,
                                int precision, cudaStream_t st);
