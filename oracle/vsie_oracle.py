@@ -153,6 +153,58 @@ def ball_green_integral(a, k: float):
     return (np.exp(1j * k * a) * (1.0 - 1j * k * a) - 1.0) / (k * k)
 
 
+# ------------------------------------------------------------------ density gradient
+
+def face_neighbours(tet, dom):
+    """For every tetrahedron the tetrahedra that share one of its faces and lie in the
+    same subdomain."""
+    tet = np.asarray(tet, dtype=np.int64)
+    owner = {}
+    for e in range(tet.shape[0]):
+        for f in range(4):
+            key = tuple(sorted(int(v) for j, v in enumerate(tet[e]) if j != f))
+            owner.setdefault(key, []).append(e)
+    nb = [[] for _ in range(tet.shape[0])]
+    for es in owner.values():
+        if len(es) == 2 and dom[es[0]] == dom[es[1]]:
+            nb[es[0]].append(es[1])
+            nb[es[1]].append(es[0])
+    return nb
+
+
+def lsq_grad_alpha(vert, tet, dom, alpha):
+    """grad(alpha) of an element-wise alpha by least squares over face neighbours in the
+    same subdomain (the reading for per-element density): g_e minimises
+    sum_f (alpha_f - alpha_e - g . (c_f - c_e))^2, c the centroids; the minimum-norm
+    minimiser (numpy.linalg.lstsq) when the neighbours span fewer than three directions,
+    0 without neighbours.  g is linear in alpha: returns (g (n_tet, 3), W) with W the
+    sparse (3 n_tet) x n_tet matrix, g.ravel() = W alpha."""
+    import scipy.sparse as sp
+    vert = np.asarray(vert, dtype=np.float64)
+    tet = np.asarray(tet, dtype=np.int64)
+    cen = vert[tet].mean(axis=1)
+    nb = face_neighbours(tet, dom)
+    alpha = np.asarray(alpha, dtype=np.float64)
+    g = np.zeros((tet.shape[0], 3))
+    rows, cols, vals = [], [], []
+    for e in range(tet.shape[0]):
+        if not nb[e]:
+            continue
+        Dm = cen[nb[e]] - cen[e]                      # (k, 3)
+        P = np.linalg.pinv(Dm, rcond=1e-10)           # (3, k): g = P (alpha_f - alpha_e)
+        g[e] = P @ (alpha[nb[e]] - alpha[e])
+        for c in range(3):
+            for q, f in enumerate(nb[e]):
+                rows.append(3 * e + c)
+                cols.append(f)
+                vals.append(P[c, q])
+            rows.append(3 * e + c)
+            cols.append(e)
+            vals.append(-P[c].sum())
+    W = sp.csr_matrix((vals, (rows, cols)), shape=(3 * tet.shape[0], tet.shape[0]))
+    return g, W
+
+
 # ------------------------------------------------------------------ discretisation
 
 class Discretisation:
@@ -215,7 +267,10 @@ class Discretisation:
 
     @classmethod
     def from_workload(cls, w):
-        return cls(w.vert, w.tet, w.tri, w.rho, w.c, w.grad_alpha, w.tri_rho_in,
+        ga = w.grad_alpha
+        if getattr(w, "grad_alpha_lsq", False):
+            ga, _ = lsq_grad_alpha(w.vert, w.tet, w.tet_domain, w.rho0 / np.asarray(w.rho) - 1.0)
+        return cls(w.vert, w.tet, w.tri, w.rho, w.c, ga, w.tri_rho_in,
                    w.tri_rho_out, w.k0, w.rho0, w.c0, w.tet_far_points, w.near_radius,
                    w.tri_near_radius)
 
@@ -446,8 +501,9 @@ def gradient_channels(D, lam, points):
 
 def misfit_and_gradient(w, dirs, target, direction):
     """L = 1/2 sum_d |p_inf(xhat_d) - t_d|^2 for the solution of A p = p_inc, and dL/drho_e,
-    dL/dc_e for every tetrahedron (piecewise-constant density inside each element, interface
-    densities fixed), by the adjoint method:
+    dL/dc_e for every tetrahedron (element-wise density, interface densities fixed; with
+    w.grad_alpha_lsq the density gradient of the least-squares reading, which carries
+    rho into neighbouring columns), by the adjoint method:
         A^H lam = F^H r,  r = F p - t,
         dL/dtheta = Re[r^H (dF/dtheta) p] - Re[lam^H (dA/dtheta) p].
     A and F depend on (rho_e, c_e) only through the single-layer weight
@@ -480,4 +536,22 @@ def misfit_and_gradient(w, dirs, target, direction):
     ds_drho = -D.sdens / rho
     ds_dc = -2.0 * k0 ** 2 * (rho0 / rho) * c0 ** 2 / c ** 3
     dm_drho = -rho0 / rho ** 2
-    return L, dLds * ds_drho + dLdm * dm_drho, dLds * ds_dc, p
+    dLdrho = dLds * ds_drho + dLdm * dm_drho
+    if getattr(w, "grad_alpha_lsq", False):
+        # grad(alpha) = W alpha (least squares over face neighbours) depends on rho through
+        # alpha = rho0/rho - 1: dL/dalpha = W^T dL/dgrad(alpha), with dA/dgrad(alpha)_{e,c}
+        # the column of the operator assembled with unit grad(alpha) along axis c
+        _, Wst = lsq_grad_alpha(w.vert, w.tet, w.tet_domain, rho0 / rho - 1.0)
+        gv = np.zeros((D.n_tet, 3))
+        for ax in range(3):
+            V = Discretisation.from_workload(w)
+            V.sdens = np.zeros_like(V.sdens)
+            V.grad_alpha = np.zeros_like(V.grad_alpha)
+            V.grad_alpha[:, ax] = 1.0
+            V.tri_omega = np.zeros_like(V.tri_omega)
+            V.mass = np.zeros_like(V.mass)
+            Av = V.assemble()[:, :D.n_tet]
+            Fv = far_field_matrix(V, dirs)[:, :D.n_tet]
+            gv[:, ax] = ((np.conj(r) @ Fv) * pt).real - ((np.conj(lam) @ Av) * pt).real
+        dLdrho = dLdrho + (Wst.T @ gv.ravel()) * (-rho0 / rho ** 2)
+    return L, dLdrho, dLds * ds_dc, p

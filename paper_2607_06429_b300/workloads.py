@@ -52,6 +52,8 @@ class Workload:
     R1: float = 1.0
     R2: float = 0.0
     layers: dict = dataclasses.field(default_factory=dict)
+    tet_domain: Optional[np.ndarray] = None  # subdomain (1 outer, 2 inner) of every tetrahedron
+    grad_alpha_lsq: bool = False             # grad(alpha) from the least-squares reading (consumers compute it)
 
     @property
     def n_tet(self) -> int:
@@ -230,7 +232,8 @@ def nested_sphere(n_grid: int, R1: float, R2: float, subdiv1: int, subdiv2: Opti
         tri_rho_in=np.concatenate(rin).astype(np.float64),
         tri_rho_out=np.concatenate(rout).astype(np.float64),
         k0=float(k0), rho0=rho0, c0=c0, tet_far_points=int(tet_far_points),
-        near_radius=near, tri_near_radius=tri_near_factor * max_edge, h=h, R1=R1, R2=R2, layers=layers or {})
+        near_radius=near, tri_near_radius=tri_near_factor * max_edge, h=h, R1=R1, R2=R2, layers=layers or {},
+        tet_domain=dom)
 
 
 def _const(v1, v2=None):
@@ -303,10 +306,13 @@ def nested_k25(n_grid=128, subdiv=7, k0=25.0, seed=0) -> Workload:
                          tet_far_points=1, name=f"nested{n_grid}_k{k0:g}")
 
 
-def nested_perturbed(n_grid=40, subdiv=5, k0=6.0, seed=0, sigma=0.05) -> Workload:
+def nested_perturbed(n_grid=40, subdiv=5, k0=6.0, seed=0, sigma=0.05, lsq=False) -> Workload:
     """Nested spheres r=1 / r=0.5 at k0=6 with per-element multiplicative perturbations
-    rho_e = rho_layer (1 + d_rho), c_e = c_layer (1 + d_c), d ~ N(0, sigma^2) seeded."""
+    rho_e = rho_layer (1 + d_rho), c_e = c_layer (1 + d_c), d ~ N(0, sigma^2) seeded.
+    lsq: grad(alpha) from the least-squares reading over face neighbours (computed by the
+    consumers from rho), else element-wise constant density (grad(alpha) = 0)."""
     w = nested_k10(n_grid, subdiv, k0, seed)
+    w.grad_alpha_lsq = bool(lsq)
     rng_r = np.random.default_rng(seed)
     rng_c = np.random.default_rng(seed + 1)
     w.rho = w.rho * (1.0 + sigma * rng_r.normal(size=w.n_tet))

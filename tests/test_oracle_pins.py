@@ -492,3 +492,46 @@ def test_gradient_channel_psi_is_minus_gradient_of_phi():
         fm, _ = O.gradient_channels(D, lam, y - e)
         fd = -(fp - fm) / (2 * h)
         assert np.allclose(fd, psi[:, c], rtol=1e-7, atol=1e-9 * np.abs(psi).max())
+
+
+# ----------------------------------------------------------------- least-squares grad(alpha)
+
+def test_lsq_grad_alpha_exact_for_linear_alpha():
+    """For alpha linear in each subdomain the least-squares gradient is exact on every
+    tetrahedron whose same-subdomain face neighbours span three directions; the returned
+    stencil reproduces it (W alpha)."""
+    w = W.nested_perturbed(6, 1, 2.0, lsq=True)
+    cen = w.vert[w.tet].mean(axis=1)
+    g_true = {1: np.array([0.3, -0.2, 0.1]), 2: np.array([-0.15, 0.25, 0.4])}
+    a0 = {1: 0.1, 2: -0.3}
+    alpha = np.array([a0[d] + cen[e] @ g_true[d] for e, d in enumerate(w.tet_domain)])
+    g, Wst = O.lsq_grad_alpha(w.vert, w.tet, w.tet_domain, alpha)
+    nb = O.face_neighbours(w.tet, w.tet_domain)
+    full = [e for e in range(w.n_tet)
+            if len(nb[e]) >= 3 and np.linalg.matrix_rank(cen[nb[e]] - cen[e]) == 3]
+    assert len(full) > w.n_tet // 2
+    err = max(np.abs(g[e] - g_true[w.tet_domain[e]]).max() for e in full)
+    assert err <= 1e-12
+    assert np.allclose(Wst @ alpha, g.ravel(), atol=1e-14)
+
+
+def test_oracle_gradient_with_lsq_density_matches_finite_differences():
+    """With the least-squares density gradient the density enters neighbouring columns;
+    the oracle's adjoint gradient against central differences of its own loss."""
+    w = W.nested_perturbed(5, 1, 2.0, lsq=True)
+    dirs = W.fibonacci_dirs(12)
+    rng = np.random.default_rng(2)
+    t = rng.normal(size=12) + 1j * rng.normal(size=12)
+    L, grho, gc, _ = O.misfit_and_gradient(w, dirs, t, [0.0, 0.0, 1.0])
+    assert np.abs(grho).max() > 1e-3 * np.abs(gc).max()   # the density now matters
+    for e in rng.choice(w.n_tet, size=3, replace=False):
+        for arr, g in ((w.rho, grho), (w.c, gc)):
+            h = 1e-6 * arr[e]
+            old = arr[e]
+            arr[e] = old + h
+            Lp = O.misfit_and_gradient(w, dirs, t, [0.0, 0.0, 1.0])[0]
+            arr[e] = old - h
+            Lm = O.misfit_and_gradient(w, dirs, t, [0.0, 0.0, 1.0])[0]
+            arr[e] = old
+            fd = (Lp - Lm) / (2 * h)
+            assert abs(fd - g[e]) <= 1e-6 * np.abs(g).max() + 1e-7 * abs(g[e]), (e, fd, g[e])
