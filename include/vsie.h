@@ -272,6 +272,22 @@ vsie_status vsie_solve_batched(vsie_handle* h, const void* d_b, void* d_x, int32
 vsie_status vsie_far_field_adjoint(vsie_handle* h, const void* d_r, int32_t nrhs,
                                    const double* h_dirs, int32_t ndir, void* d_x, void* stream);
 
+/* Density gradient of an element-wise density, the least-squares reading: for every
+ * tetrahedron e, g_e minimises sum_f (alpha_f - alpha_e - g . (c_f - c_e))^2 over the
+ * tetrahedra f sharing a face with e in the same subdomain (c: centroids); the
+ * minimum-norm minimiser when those neighbours span fewer than three directions
+ * (singular values below 1e-6 of the largest dropped), 0 without neighbours.  It feeds
+ * the adjoint double layer (grad(alpha) of Eq. vsie) through vsie_material.grad_alpha.
+ * tet_domain: n_tet subdomain labels or NULL (one subdomain); alpha = rho0/rho - 1
+ * (n_tet); grad_alpha: 3 n_tet output (x, y, z per tetrahedron).  Host arrays only, no
+ * device work; VSIE_ERR_MESH on an out-of-range vertex index. */
+vsie_status vsie_lsq_grad_alpha(const vsie_mesh* mesh, const int8_t* tet_domain, const double* alpha,
+                                double* grad_alpha);
+/* Its adjoint: grad_alpha = W alpha is linear in alpha; d_alpha = W^T d_grad (the chain rule
+ * of a gradient with respect to grad_alpha back to alpha).  d_grad: 3 n_tet, d_alpha: n_tet. */
+vsie_status vsie_lsq_grad_alpha_adjoint(const vsie_mesh* mesh, const int8_t* tet_domain, const double* d_grad,
+                                        double* d_alpha);
+
 /* Gradient channels of an adjoint state lam (device complex128, n): for every far-field
  * source point y_j (the order of vsie_source_points)
  *   phi_j = sum_i conj(G(x_i, y_j)) lam_i,   psi_j = sum_i conj(grad_x G(x_i, y_j)) lam_i,

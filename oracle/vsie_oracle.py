@@ -176,8 +176,8 @@ def lsq_grad_alpha(vert, tet, dom, alpha):
     """grad(alpha) of an element-wise alpha by least squares over face neighbours in the
     same subdomain (the reading for per-element density): g_e minimises
     sum_f (alpha_f - alpha_e - g . (c_f - c_e))^2, c the centroids; the minimum-norm
-    minimiser (numpy.linalg.lstsq) when the neighbours span fewer than three directions,
-    0 without neighbours.  g is linear in alpha: returns (g (n_tet, 3), W) with W the
+    minimiser (numpy pseudo-inverse, singular values below 1e-6 of the largest dropped)
+    when the neighbours span fewer than three directions, 0 without neighbours.  g is linear in alpha: returns (g (n_tet, 3), W) with W the
     sparse (3 n_tet) x n_tet matrix, g.ravel() = W alpha."""
     import scipy.sparse as sp
     vert = np.asarray(vert, dtype=np.float64)
@@ -191,7 +191,7 @@ def lsq_grad_alpha(vert, tet, dom, alpha):
         if not nb[e]:
             continue
         Dm = cen[nb[e]] - cen[e]                      # (k, 3)
-        P = np.linalg.pinv(Dm, rcond=1e-10)           # (3, k): g = P (alpha_f - alpha_e)
+        P = np.linalg.pinv(Dm, rcond=1e-6)            # (3, k): g = P (alpha_f - alpha_e)
         g[e] = P @ (alpha[nb[e]] - alpha[e])
         for c in range(3):
             for q, f in enumerate(nb[e]):

@@ -20,6 +20,14 @@ with s_e = 0 (c_e = c0) are not supported (their single-layer column vanishes).
 Without a density-gradient term (piecewise-constant density per element, grad(alpha) = 0)
 the column of element e scales as 1/rho_e as a whole, so p_e absorbs rho_e and the far field
 does not depend on it: dL/drho vanishes identically in this discrete model.
+
+With the least-squares density gradient (workload flag grad_alpha_lsq), grad(alpha) = W alpha
+over face neighbours (the library's stencil), so rho_e also enters the adjoint double layer
+of its neighbours.  The backward pass then takes per-unit-weight channels from operators of
+the same mesh carrying one unit weight (s = 1, or grad(alpha) along one axis) on every
+tetrahedron: every column is linear in its element's weights, so their adjoint applies and
+far-field adjoints give dL/ds_e and dL/dgrad(alpha)_e exactly (near and self corrections
+included), and dL/dalpha = W^T dL/dgrad(alpha) (vsie_lsq_grad_alpha_adjoint).
 """
 from __future__ import annotations
 
@@ -35,8 +43,11 @@ class FarFieldMisfit(torch.autograd.Function):
     @staticmethod
     def forward(ctx, rho, c, workload, dirs, target, direction, solve_kw):
         w = workload
-        op = B.Operator(w.vert, w.tet, w.tri, rho.detach().numpy(), c.detach().numpy(), w.tri_rho_in,
-                        w.tri_rho_out, w.k0, w.rho0, w.c0, None, w.tet_far_points, w.near_radius,
+        lsq = bool(getattr(w, "grad_alpha_lsq", False))
+        rho_np = rho.detach().numpy()
+        ga = B.lsq_grad_alpha(w.vert, w.tet, w.tet_domain, w.rho0 / rho_np - 1.0) if lsq else None
+        op = B.Operator(w.vert, w.tet, w.tri, rho_np, c.detach().numpy(), w.tri_rho_in,
+                        w.tri_rho_out, w.k0, w.rho0, w.c0, ga, w.tet_far_points, w.near_radius,
                         w.tri_near_radius)
         b = op.plane_wave_rhs([direction])[0].contiguous()
         p, _ = op.solve(b, **solve_kw)
@@ -46,6 +57,7 @@ class FarFieldMisfit(torch.autograd.Function):
         loss = 0.5 * float((r.abs() ** 2).sum().item())
         ctx.op, ctx.p, ctx.r, ctx.dirs, ctx.solve_kw = op, p, r, dirs, solve_kw
         ctx.k0, ctx.rho0, ctx.c0, ctx.n_tet = w.k0, w.rho0, w.c0, w.n_tet
+        ctx.w, ctx.lsq = w, lsq
         ctx.save_for_backward(rho, c)
         return torch.tensor(loss, dtype=torch.float64)
 
@@ -56,21 +68,57 @@ class FarFieldMisfit(torch.autograd.Function):
         g = op.far_field_adjoint(r, ctx.dirs)
         lam, _ = op.solve(g.contiguous(), adjoint=True, **ctx.solve_kw)
         prec = 64 if ctx.solve_kw.get("mode", 32) == 64 else 32
-        ahl = op.adjoint_apply(lam, precision=prec)
         rho_d = rho.to(device=p.device)
         c_d = c.to(device=p.device)
         m = ctx.rho0 / rho_d
         s = ctx.k0 ** 2 * (ctx.rho0 / rho_d) * ((ctx.c0 / c_d) ** 2 - 1.0)
-        w = ahl[:nt] - m * lam[:nt]
-        dLds = (torch.conj(g[:nt] - w) * p[:nt]).real / s
         dLdm = -(torch.conj(lam[:nt]) * p[:nt]).real
         ds_drho = -s / rho_d
         ds_dc = -2.0 * ctx.k0 ** 2 * (ctx.rho0 / rho_d) * ctx.c0 ** 2 / c_d ** 3
         dm_drho = -ctx.rho0 / rho_d ** 2
-        grad_rho = (dLds * ds_drho + dLdm * dm_drho).cpu() * grad_loss
+        if not ctx.lsq:
+            ahl = op.adjoint_apply(lam, precision=prec)
+            w = ahl[:nt] - m * lam[:nt]
+            dLds = (torch.conj(g[:nt] - w) * p[:nt]).real / s
+            grad_rho = dLds * ds_drho + dLdm * dm_drho
+        else:
+            chans = _unit_channels(ctx.w, lam, r, p, ctx.dirs, prec)
+            dLds = chans[0]
+            dLdga = torch.stack(chans[1:], dim=1).cpu().numpy()          # dL/dgrad(alpha)
+            dLda = B.lsq_grad_alpha_adjoint(ctx.w.vert, ctx.w.tet, ctx.w.tet_domain, dLdga)
+            dLda = torch.as_tensor(dLda, dtype=torch.float64, device=p.device)
+            grad_rho = dLds * ds_drho + dLdm * dm_drho + dLda * dm_drho    # d alpha/d rho = d m/d rho
         grad_c = (dLds * ds_dc).cpu() * grad_loss
+        grad_rho = grad_rho.cpu() * grad_loss
         op.close()
         return grad_rho, grad_c, None, None, None, None, None
+
+
+def _unit_channels(w, lam, r, p, dirs, prec):
+    """Per-unit-weight derivative channels Re[conj(F_u^H r - (A_u^H lam - lam)) p] on the
+    tetrahedra for the unit single-layer weight (s = 1) and the unit density gradient along
+    x, y, z: A_u, F_u are the operator and far-field map of the same mesh with that unit
+    weight on every tetrahedron, no interface jump and unit mass (rho = rho0), so that every
+    column carries exactly d(column)/d(weight), near and self corrections included."""
+    import torch
+    nt = w.n_tet
+    one = np.full(nt, w.rho0)
+    tri_one = np.full(w.n_tri, w.rho0)
+    c_s = np.full(nt, w.c0 / np.sqrt(1.0 + 1.0 / w.k0 ** 2))   # s = k0^2((c0/c)^2 - 1) = 1
+    variants = [(c_s, None)]
+    for ax in range(3):
+        ga = np.zeros((nt, 3))
+        ga[:, ax] = 1.0
+        variants.append((np.full(nt, w.c0), ga))                 # s = 0, grad(alpha) = e_ax
+    out = []
+    for cv, ga in variants:
+        u = B.Operator(w.vert, w.tet, w.tri, one, cv, tri_one, tri_one, w.k0, w.rho0, w.c0, ga,
+                       w.tet_far_points, w.near_radius, w.tri_near_radius)
+        wu = u.adjoint_apply(lam, precision=prec) - lam
+        gu = u.far_field_adjoint(r, dirs)
+        out.append((torch.conj(gu[:nt] - wu[:nt]) * p[:nt]).real)
+        u.close()
+    return out
 
 
 def far_field_misfit(rho, c, workload, dirs, target, direction=(1.0, 0.0, 0.0), **solve_kw):

@@ -29,6 +29,7 @@ EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_appl
            "vsie_far_field_adjoint", "vsie_solve_batched", "vsie_apply_batched_multi",
            "vsie_graph_create_batched", "vsie_graph_launch", "vsie_graph_nodes", "vsie_graph_destroy",
            "vsie_autotune", "vsie_gradient_channels", "vsie_source_points",
+           "vsie_lsq_grad_alpha", "vsie_lsq_grad_alpha_adjoint",
            "vsie_last_error")
 
 
@@ -125,6 +126,8 @@ def load_library(path: str = LIB_PATH):
     lib.vsie_autotune.argtypes = [P, I32, ctypes.POINTER(_Tuning), P]
     lib.vsie_gradient_channels.argtypes = [P, P, I32, P, P, P]
     lib.vsie_source_points.argtypes = [P, P, P, P]
+    lib.vsie_lsq_grad_alpha.argtypes = [ctypes.POINTER(_Mesh), P, P, P]
+    lib.vsie_lsq_grad_alpha_adjoint.argtypes = [ctypes.POINTER(_Mesh), P, P, P]
     lib.vsie_graph_nodes.argtypes = [P, ctypes.POINTER(I64)]
     lib.vsie_graph_destroy.argtypes = [P]
     lib.vsie_graph_destroy.restype = None
@@ -200,8 +203,11 @@ class Operator:
 
     @classmethod
     def from_workload(cls, w, **kw):
+        ga = w.grad_alpha
+        if getattr(w, "grad_alpha_lsq", False):
+            ga = lsq_grad_alpha(w.vert, w.tet, w.tet_domain, w.rho0 / np.asarray(w.rho) - 1.0)
         return cls(w.vert, w.tet, w.tri, w.rho, w.c, w.tri_rho_in, w.tri_rho_out, w.k0,
-                   w.rho0, w.c0, w.grad_alpha, w.tet_far_points, w.near_radius,
+                   w.rho0, w.c0, ga, w.tet_far_points, w.near_radius,
                    w.tri_near_radius, **kw)
 
     def close(self):
@@ -444,3 +450,32 @@ class BatchedGraph:
             self.close()
         except Exception:
             pass
+
+
+def _tet_mesh(vert, tet):
+    v = _f64(vert).reshape(-1)
+    t = _i32(tet).reshape(-1)
+    return _Mesh(v.shape[0] // 3, _ptr(v), t.shape[0] // 4, _ptr(t), 0, None), (v, t)
+
+
+def lsq_grad_alpha(vert, tet, tet_domain, alpha):
+    """grad(alpha) (n_tet, 3) of an element-wise alpha by the library's least-squares
+    stencil over same-subdomain face neighbours (vsie_lsq_grad_alpha)."""
+    lib = load_library()
+    mesh, keep = _tet_mesh(vert, tet)
+    dom = None if tet_domain is None else np.ascontiguousarray(tet_domain, dtype=np.int8)
+    a = _f64(alpha)
+    out = np.empty((a.shape[0], 3), dtype=np.float64)
+    _check(lib.vsie_lsq_grad_alpha(ctypes.byref(mesh), _ptr(dom), _ptr(a), _ptr(out)))
+    return out
+
+
+def lsq_grad_alpha_adjoint(vert, tet, tet_domain, d_grad):
+    """W^T d_grad for grad(alpha) = W alpha (vsie_lsq_grad_alpha_adjoint); d_grad (n_tet, 3)."""
+    lib = load_library()
+    mesh, keep = _tet_mesh(vert, tet)
+    dom = None if tet_domain is None else np.ascontiguousarray(tet_domain, dtype=np.int8)
+    g = _f64(d_grad).reshape(-1)
+    out = np.empty(g.shape[0] // 3, dtype=np.float64)
+    _check(lib.vsie_lsq_grad_alpha_adjoint(ctypes.byref(mesh), _ptr(dom), _ptr(g), _ptr(out)))
+    return out
