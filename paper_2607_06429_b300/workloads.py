@@ -363,5 +363,6 @@ CONFIGS = {
     "nested24_k10": lambda: nested_k10(24, 4, 10.0),
     "nested80_k10": lambda: nested_k10(80, 6, 10.0),
     "perturbed40_k6": lambda: nested_perturbed(40, 5, 6.0),
+    "perturbed40_k6_lsq": lambda: nested_perturbed(40, 5, 6.0, lsq=True),
     "nested128_k25": lambda: nested_k25(128, 7, 25.0),
 }

@@ -212,10 +212,13 @@ def test_invalid_mesh_reports_error():
         _op(w)
 
 
-@pytest.mark.parametrize("name,count", [("perturbed40_k6", 24), ("nested128_k25", 12)])
+@pytest.mark.parametrize("name,count", [("perturbed40_k6", 24), ("perturbed40_k6_lsq", 16),
+                                         ("nested128_k25", 12)])
 def test_apply_sampled_rows_full_size(name, count):
-    """Full-size workloads (k0 = 6 with per-element contrast; k0 = 25 with 7.25M unknowns
-    and 8.56M far-field source points): FP32 apply vs the oracle on seeded rows."""
+    """Full-size workloads (k0 = 6 with per-element contrast, with grad(alpha) = 0 and with
+    the least-squares density gradient, which puts every tetrahedron in the heterogeneous
+    class; k0 = 25 with 7.25M unknowns and 8.56M far-field source points): FP32 apply vs the
+    oracle on seeded rows."""
     _torch()
     w = W.CONFIGS[name]()
     op = _op(w)
@@ -226,6 +229,6 @@ def test_apply_sampled_rows_full_size(name, count):
     y = op.apply(xd, precision=32).cpu().numpy()
     ref = D.apply_rows(x, rows)
     assert rel(y[rows], ref) <= TOL32, rel(y[rows], ref)
-    if name == "perturbed40_k6":  # per-element contrast: the double-float sums at full size
+    if name.startswith("perturbed40"):  # per-element contrast: the double-float sums at full size
         y48 = op.apply(xd, precision=48).cpu().numpy()
         assert rel(y48[rows], ref) <= TOL64, rel(y48[rows], ref)
