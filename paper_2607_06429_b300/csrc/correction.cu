@@ -279,11 +279,6 @@ __global__ void corr_rows_kernel(CorrInputs in, const int64_t* __restrict__ row_
 
 // ----------------------------------------------------------------- application
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // The correction values are stored as double-float complex numbers (re.hi, im.hi, re.lo,
 // im.lo): 16 bytes per entry like complex128, about 48 significant bits, so that the

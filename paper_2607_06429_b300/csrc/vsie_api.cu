@@ -503,7 +503,7 @@ extern "C" vsie_status vsie_apply_timed(vsie_handle* h, const void* d_x, void* d
     VSIE_TRY(far_sum_f(h, y, precision, st, &n_launch));
     VSIE_CUDA(cudaEventRecord(ev[3], st));
     VSIE_TRY(correction_apply(h, x, y, precision, st));
-    ++n_launch;
+    n_launch += (h->n > 0) ? 2 : 0;  // x to double-float, then the CSR correction + mass
     VSIE_CUDA(cudaEventRecord(ev[4], st));
     VSIE_CUDA(cudaEventSynchronize(ev[4]));
     for (int i = 0; i < 4; ++i) {
