@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "dfloat.h"
 #include "vsie_internal.h"
@@ -559,6 +560,25 @@ struct DfBase {
   const float4* __restrict__ tgt;  // 2 records per target
   const float4* __restrict__ src;  // NREC records per source
 
+  // One pair evaluation is several hundred instructions: the driver does not unroll the
+  // source loop, and accumulate() walks the targets with one copy of the evaluation by
+  // rotating them (and their sums) through slot 0, so the loop body stays small enough for
+  // the instruction cache while every register index is a compile-time constant.
+  static constexpr int kSrcUnroll = 1;
+  __device__ __forceinline__ static void rotate(Tgts& tg, Part& q) {
+    const DTgt t0 = tg.t[0];
+    const float2 s0 = q.S[0], c0 = q.C[0];
+#pragma unroll
+    for (int t = 0; t + 1 < kT; ++t) {
+      tg.t[t] = tg.t[t + 1];
+      q.S[t] = q.S[t + 1];
+      q.C[t] = q.C[t + 1];
+    }
+    tg.t[kT - 1] = t0;
+    q.S[kT - 1] = s0;
+    q.C[kT - 1] = c0;
+  }
+
   __device__ __forceinline__ void load_targets(int64_t i0, int64_t nt, Tgts& tg) const {
 #pragma unroll
     for (int t = 0; t < kT; ++t) {
@@ -599,11 +619,12 @@ struct DfBase {
 // G: records (x.h, y.h, z.h, q.re.h) (x.l, y.l, z.l, q.re.l) (q.im.h, q.im.l, 0, 0);
 //    y += e^{2 pi i t} rinv q~
 struct PolGdf : DfBase<3> {
-  __device__ __forceinline__ void accumulate(const Src& s, const Tgts& tg, Part& q) const {
+  __device__ __forceinline__ void accumulate(const Src& s, Tgts& tg, Part& q) const {
     const float4 qv = make_float4(s.r[0].w, s.r[2].x, s.r[1].w, s.r[2].y);
-#pragma unroll
+#pragma unroll 1
     for (int t = 0; t < kT; ++t) {
-      df_cmac(q.S[t], q.C[t], df_coef_g(tg.t[t], s.r[0], s.r[1]), qv);
+      df_cmac(q.S[0], q.C[0], df_coef_g(tg.t[0], s.r[0], s.r[1]), qv);
+      rotate(tg, q);
     }
   }
 };
@@ -611,12 +632,13 @@ struct PolGdf : DfBase<3> {
 // K: records (x.h, y.h, z.h, c.re.h) (x.l, y.l, z.l, c.re.l) (nx.h, ny.h, nz.h, c.im.h)
 //    (nx.l, ny.l, nz.l, c.im.l);  y += e^{2 pi i t}(2 pi i t - 1)(d~ . n) rinv^3 c~
 struct PolKdf : DfBase<4> {
-  __device__ __forceinline__ void accumulate(const Src& s, const Tgts& tg, Part& q) const {
+  __device__ __forceinline__ void accumulate(const Src& s, Tgts& tg, Part& q) const {
     const float4 cv = make_float4(s.r[0].w, s.r[2].w, s.r[1].w, s.r[3].w);
     const dfs nx{s.r[2].x, s.r[3].x}, ny{s.r[2].y, s.r[3].y}, nz{s.r[2].z, s.r[3].z};
-#pragma unroll
+#pragma unroll 1
     for (int t = 0; t < kT; ++t) {
-      df_cmac(q.S[t], q.C[t], df_coef_k(tg.t[t], s.r[0], s.r[1], nx, ny, nz), cv);
+      df_cmac(q.S[0], q.C[0], df_coef_k(tg.t[0], s.r[0], s.r[1], nx, ny, nz), cv);
+      rotate(tg, q);
     }
   }
 };
@@ -625,23 +647,34 @@ struct PolKdf : DfBase<4> {
 //    (ux.im.h, ux.im.l, uy.re.h, uy.re.l) (uy.im.h, uy.im.l, uz.re.h, uz.re.l) (uz.im.h, uz.im.l, 0, 0);
 //    y += e^{2 pi i t} rinv [q~ + (2 pi i t - 1)(d~ . u~) rinv^2]
 struct PolFdf : DfBase<6> {
-  __device__ __forceinline__ void accumulate(const Src& s, const Tgts& tg, Part& q) const {
+  __device__ __forceinline__ void accumulate(const Src& s, Tgts& tg, Part& q) const {
     const dfs qr{s.r[0].w, s.r[1].w}, qi{s.r[2].x, s.r[2].y};
     const dfs uxr{s.r[2].z, s.r[2].w}, uxi{s.r[3].x, s.r[3].y}, uyr{s.r[3].z, s.r[3].w};
     const dfs uyi{s.r[4].x, s.r[4].y}, uzr{s.r[4].z, s.r[4].w}, uzi{s.r[5].x, s.r[5].y};
-#pragma unroll
+#pragma unroll 1
     for (int t = 0; t < kT; ++t) {
       dfs dx, dy, dz, rinv, tt, cs, sn;
-      df_geometry(tg.t[t], s.r[0], s.r[1], dx, dy, dz, rinv, tt, cs, sn);
+      df_geometry(tg.t[0], s.r[0], s.r[1], dx, dy, dz, rinv, tt, cs, sn);
       const dfs dur = dfs_add(dfs_add(dfs_mul(dx, uxr), dfs_mul(dy, uyr)), dfs_mul(dz, uzr));
       const dfs dui = dfs_add(dfs_add(dfs_mul(dx, uxi), dfs_mul(dy, uyi)), dfs_mul(dz, uzi));
       const dfs ri2 = dfs_sqr(rinv);
       const dfs fi = dfs_mul(dfs_mul(tt, dfc_two_pi()), ri2);  // 2 pi t rinv^2
       const dfs inr = dfs_sub(dfs_sub(qr, dfs_mul(ri2, dur)), dfs_mul(fi, dui));
       const dfs ini = dfs_add(dfs_sub(qi, dfs_mul(ri2, dui)), dfs_mul(fi, dur));
-      df_cmac(q.S[t], q.C[t], df_c4(dfs_mul(cs, rinv), dfs_mul(sn, rinv)), df_c4(inr, ini));
+      df_cmac(q.S[0], q.C[0], df_c4(dfs_mul(cs, rinv), dfs_mul(sn, rinv)), df_c4(inr, ini));
+      rotate(tg, q);
     }
   }
+};
+
+// source-loop unroll factor of the driver: the policy's kSrcUnroll where it sets one, else 4
+template <class P, class = void>
+struct SrcUnroll {
+  static constexpr int value = 4;
+};
+template <class P>
+struct SrcUnroll<P, std::void_t<decltype(P::kSrcUnroll)>> {
+  static constexpr int value = P::kSrcUnroll;
 };
 
 // ----------------------------------------------------------------- persistent driver
@@ -682,7 +715,7 @@ __global__ void __launch_bounds__(kBlock) nbody_kernel(P p, StreamK sk, double2*
       __syncthreads();
       typename P::Part part;
       p.zero(part);
-#pragma unroll 4
+#pragma unroll(SrcUnroll<P>::value)
       for (int jj = 0; jj < kBlock; ++jj) p.accumulate(p.get(sm, jj), tg, part);
       __syncthreads();
       R ar[kT], ai[kT];
