@@ -209,8 +209,18 @@ def batched_timing(torch, op, W, nrhs=64, steps=2, fp64=False):
     # agreement with the per-column FP32 apply on two columns
     err = max(float(torch.linalg.norm(Y[r] - op.apply(X[r], precision=32)) / torch.linalg.norm(Y[r]))
               for r in (0, nrhs - 1))
-    out = {"nrhs": nrhs, "seconds_per_block": t, "interactions_per_s": op.n * op.n_far_sources * nrhs / t,
-           "max_rel_diff_vs_per_column_fp32": err}
+    rate = op.n * op.n_far_sources * nrhs / t
+    # tensor roofline: TF32 dense peak = the measured BF16 peak x the nominal TF32/BF16 ratio
+    # (1.1 / 2.25 PFLOP/s); algorithmic work 8 real FLOP per pair and right-hand side (one
+    # complex multiply-add), executed 24 (three split TF32 products of it)
+    pk, pk_kind = peaks()
+    tf32_peak = pk["bf16_tflops"] * 1.1 / 2.25
+    out = {"nrhs": nrhs, "seconds_per_block": t, "interactions_per_s": rate,
+           "max_rel_diff_vs_per_column_fp32": err,
+           "roofline": {"bound": "tensor", "achieved": rate * 8 / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
+                        "frac": rate * 8 / 1e12 / tf32_peak, "executed_tflops": rate * 24 / 1e12,
+                        "executed_frac": rate * 24 / 1e12 / tf32_peak,
+                        "peak_basis": f"{pk_kind} BF16 {pk['bf16_tflops']} TFLOP/s x 1.1/2.25 (TF32 vs BF16 nominal)"}}
     if fp64:
         # the FP64 multi-RHS apply (the residual operator of the batched solve)
         op.apply_batched(X, Y, precision=64)
