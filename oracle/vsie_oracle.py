@@ -279,9 +279,17 @@ class Discretisation:
         """Rows ``rows`` of the collocation matrix A (len(rows), n), from the plain
         element-by-element definition (no far/near splitting, no correction matrix)."""
         rows = np.asarray(rows, dtype=np.int64)
-        R = rows.shape[0]
+        A = self.integral_rows(self.targets[rows], rows)
+        A[np.arange(rows.shape[0]), rows] += self.mass[rows]
+        return A
+
+    def integral_rows(self, X, rows=None) -> np.ndarray:
+        """The integral terms of Eq. (vsie) at the points X (m, 3) as rows (m, n): the far
+        rule, the near rules for elements within the near radii of a point, and, when X are
+        the collocation points ``rows``, the self terms; no mass term."""
+        X = np.asarray(X, dtype=np.float64)
+        R = X.shape[0]
         k = self.k0
-        X = self.targets[rows]
         A = np.zeros((R, self.n), dtype=np.complex128)
 
         # volume columns
@@ -305,7 +313,7 @@ class Discretisation:
                     acc += pair_kernel(dq, s4[ee], g4[ee], k)
                 A[rr, ee] = acc
         # self terms: sphere of equal volume for the single layer; adjoint double layer 0
-        own = rows < self.n_tet
+        own = rows < self.n_tet if rows is not None else np.zeros(R, dtype=bool)
         if own.any():
             e = rows[own]
             A[np.nonzero(own)[0], e] = -self.sdens[e] * ball_green_integral(self.a_eq[e], k)
@@ -327,11 +335,10 @@ class Discretisation:
                     X[rr], self.tri_P[tt], self.tri_nrm[tt], self.tri_area[tt], k)
                 # a triangle on its own centroid: principal value 0 (the jump -1/2 is
                 # part of the mass function, Eqs. jump_g1, jump_g2)
-                own_t = rows[rr] == self.n_tet + tt
-                acc[rr[own_t], tt[own_t]] = 0.0
+                if rows is not None:
+                    own_t = rows[rr] == self.n_tet + tt
+                    acc[rr[own_t], tt[own_t]] = 0.0
             A[:, self.n_tet:] = acc
-
-        A[np.arange(R), rows] += self.mass[rows]
         return A
 
     def _chunk(self) -> int:
@@ -432,6 +439,14 @@ def gmres(matvec, b: np.ndarray, tol: float = 1e-5, maxiter: int = 1000):
 
 
 # ------------------------------------------------------------------ far-field misfit gradient
+
+def scattered_field(D, p, points):
+    """Scattered pressure at points of the exterior domain Omega_0, from Eq. (vsie) read as a
+    representation formula with m = 1 outside the body (the mass function of Omega_0):
+    p(x) + sum_e [integral terms of column e at x] p_e = p_inc(x), so
+    p_s(x) = p(x) - p_inc(x) = -(integral rows at x) p.  p: (n,) or (n, nrhs)."""
+    return -(D.integral_rows(points) @ p)
+
 
 def far_field_matrix(D: Discretisation, dirs) -> np.ndarray:
     """F with (F p)_d = p_inf(xhat_d) of ``Discretisation.far_field``: columns summed over the

@@ -535,3 +535,25 @@ def test_oracle_gradient_with_lsq_density_matches_finite_differences():
             arr[e] = old
             fd = (Lp - Lm) / (2 * h)
             assert abs(fd - g[e]) <= 1e-6 * np.abs(g).max() + 1e-7 * abs(g[e]), (e, fd, g[e])
+
+
+# ----------------------------------------------------------------- exterior field
+
+def test_exterior_field_against_mie_and_far_field():
+    """The scattered field at exterior points (representation formula) for the penetrable
+    ball: against the Mie series at radii 1.5-3 (discretisation level, as the far-field
+    pin), and against the oracle's own far-field pattern at a large radius R, where
+    R e^{-ikR} p_s(R xhat) -> p_inf(xhat) with an O(k |y|^2 / R) error."""
+    w = W.single_ball(12, 3, 2.0)
+    D = O.Discretisation.from_workload(w)
+    d = np.array([0.0, 0.0, 1.0])
+    p = np.linalg.solve(D.assemble(), D.plane_wave(d))
+    xhat = W.fibonacci_dirs(24)
+    pts = np.concatenate([1.5 * xhat, 3.0 * xhat])
+    ps = O.scattered_field(D, p, pts)
+    ref = S.layered_sphere_field(pts, d, D.k0, [1.0], [1.5], [0.7]) - np.exp(1j * D.k0 * (pts @ d))
+    assert np.linalg.norm(ps - ref) / np.linalg.norm(ref) < 0.04
+    R = 1.0e4
+    far = O.scattered_field(D, p, R * xhat) * R * np.exp(-1j * D.k0 * R)
+    pinf = D.far_field(p, xhat)
+    assert np.linalg.norm(far - pinf) / np.linalg.norm(pinf) < 1e-3
