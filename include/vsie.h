@@ -272,6 +272,19 @@ vsie_status vsie_solve_batched(vsie_handle* h, const void* d_b, void* d_x, int32
 vsie_status vsie_far_field_adjoint(vsie_handle* h, const void* d_r, int32_t nrhs,
                                    const double* h_dirs, int32_t ndir, void* d_x, void* stream);
 
+/* Scattered field at m points outside the scatterer (Sec. 2, Eq. vsie, where the mass
+ * function is 1): p_s(X) = p(X) - p_inc(X) = -sum_e I_e(X) p_e, I(X) the integral part of
+ * the operator row at X -- the far rule over all far-field source points, with the near
+ * rules of the create-time radii (four-point tetrahedron rule; the solid-angle split of the
+ * double layer) for elements whose centroids lie within those radii of X.  X must lie
+ * outside every tetrahedron (no self term is formed; a point inside gets a meaningless
+ * value, not an error).  p: device complex128 n x nrhs (the solved collocation values);
+ * points: host 3 m doubles (x, y, z per point, finite); out: device complex128 m x nrhs.
+ * precision 32 (FP32 far sums), 48 (double-float) or 64.  Allocates temporaries (the
+ * points and their near rows) and blocks until done.  VSIE_ERR_ARG on a bad argument. */
+vsie_status vsie_scattered_field(vsie_handle* h, const void* d_p, int32_t nrhs, const double* h_points,
+                                 int64_t m, int32_t precision, void* d_out, void* stream);
+
 /* Density gradient of an element-wise density, the least-squares reading: for every
  * tetrahedron e, g_e minimises sum_f (alpha_f - alpha_e - g . (c_f - c_e))^2 over the
  * tetrahedra f sharing a face with e in the same subdomain (c: centroids); the

@@ -29,7 +29,7 @@ EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_appl
            "vsie_far_field_adjoint", "vsie_solve_batched", "vsie_apply_batched_multi",
            "vsie_graph_create_batched", "vsie_graph_launch", "vsie_graph_nodes", "vsie_graph_destroy",
            "vsie_autotune", "vsie_gradient_channels", "vsie_source_points",
-           "vsie_lsq_grad_alpha", "vsie_lsq_grad_alpha_adjoint",
+           "vsie_lsq_grad_alpha", "vsie_lsq_grad_alpha_adjoint", "vsie_scattered_field",
            "vsie_last_error")
 
 
@@ -115,6 +115,7 @@ def load_library(path: str = LIB_PATH):
     lib.vsie_plane_wave_rhs.argtypes = [P, P, I32, P, P]
     lib.vsie_far_field.argtypes = [P, P, I32, P, I32, P, P]
     lib.vsie_far_field_adjoint.argtypes = [P, P, I32, P, I32, P, P]
+    lib.vsie_scattered_field.argtypes = [P, P, I32, P, I64, I32, P, P]
     lib.vsie_solve.argtypes = [P, P, P, ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), P]
     lib.vsie_solve_batched.argtypes = [P, P, P, ctypes.c_int32, ctypes.POINTER(_SolveOpts),
                                        ctypes.POINTER(_SolveInfo), P]
@@ -345,6 +346,18 @@ class Operator:
         out = torch.empty((nrhs, d.shape[0]), dtype=torch.complex128, device="cuda")
         _check(_lib.vsie_far_field(self._h, _dev(p, "p"), nrhs, _ptr(d), d.shape[0],
                                    _dev(out, "out"), _stream(stream)))
+        return out[0] if p.dim() == 1 else out
+
+    def scattered_field(self, p, points, precision=64, stream=None):
+        """Scattered field p_s = p - p_inc at points outside the scatterer
+        (vsie_scattered_field); p: (n,) or (nrhs, n), points: (m, 3); returns (m,) or
+        (nrhs, m)."""
+        import torch
+        nrhs = self._nrhs(p)
+        X = _f64(points).reshape(-1, 3)
+        out = torch.empty((nrhs, X.shape[0]), dtype=torch.complex128, device="cuda")
+        _check(_lib.vsie_scattered_field(self._h, _dev(p, "p"), nrhs, _ptr(X), X.shape[0], int(precision),
+                                         _dev(out, "out"), _stream(stream)))
         return out[0] if p.dim() == 1 else out
 
     def far_field_adjoint(self, r, dirs, stream=None):

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libvsie.so")
-SOURCES = ["vsie_api.cu", "nbody.cu", "correction.cu", "solve.cu", "farfield.cu", "noalloc.cu", "batch.cu", "batch64.cu", "solve_batched.cu", "graph.cu", "lsq_gradient.cu"]
+SOURCES = ["vsie_api.cu", "nbody.cu", "correction.cu", "solve.cu", "farfield.cu", "noalloc.cu", "batch.cu", "batch64.cu", "solve_batched.cu", "graph.cu", "lsq_gradient.cu", "field.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-ftz=true", "--expt-extended-lambda",
          "-Xcompiler", "-fPIC,-O2", "-shared", "-cudart", "static"]

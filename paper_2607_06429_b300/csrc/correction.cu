@@ -38,14 +38,7 @@
 
 namespace vsie {
 
-struct CellGrid {
-  double lo[3];
-  double inv;   // 1 / cell size
-  int nc[3];
-  int64_t ncell;
-  const int32_t* order = nullptr;   // element ids sorted by cell
-  const int64_t* start = nullptr;   // ncell + 1
-};
+
 
 __device__ __forceinline__ int cell_coord(double p, double lo, double inv, int nc) {
   int c = (int)floor((p - lo) * inv);
@@ -140,24 +133,7 @@ __device__ double2 dl_near(double x, double y, double z, const double4_32a* __re
   return acc;
 }
 
-struct CorrInputs {
-  const double4_32a* tgt;       // n
-  const double4_32a* tet_cen;   // n_tet
-  const double4_32a* tet_pts;   // 4 n_tet
-  const double* tet_s;
-  const double4_32a* tet_ga;
-  const double* tet_vol;
-  const double4_32a* tri_vtx;   // 3 n_tri
-  const double4_32a* tri_pts;   // 3 n_tri
-  const double4_32a* tri_cen;   // n_tri
-  const double4_32a* tri_nrm;   // (n, area)
-  const double* tri_omega;
-  int64_t n_tet, n_tri, n;
-  int far_points;
-  double R2v, R2t;          // squared radii (0 = inactive)
-  double k;
-  CellGrid gv, gt;
-};
+
 
 // Visit the correction entries of row i: vol near set (or self only), then tri near set.
 // fill == false: count only.
@@ -168,6 +144,7 @@ __global__ void corr_rows_kernel(CorrInputs in, const int64_t* __restrict__ row_
   if (i >= in.n) return;
   const double4_32a X = in.tgt[i];
   const double k = in.k;
+  const int64_t si = in.self ? i : -1;  // the row's own unknown, if any
   int64_t pos = fill ? row_ptr[i] : 0;
   int64_t cnt = 0;
   auto emit = [&](int32_t c, double2 a64, double2 a32) {
@@ -186,7 +163,7 @@ __global__ void corr_rows_kernel(CorrInputs in, const int64_t* __restrict__ row_
     double2 acc, f64 = make_double2(0, 0), f32 = make_double2(0, 0);
     const double s4 = s * vol * 0.25;
     const double4_32a g4 = make_double4_32a(ga.x * vol * 0.25, ga.y * vol * 0.25, ga.z * vol * 0.25, 0);
-    if (e == i) {
+    if (e == si) {
       // self: single layer over the equal-volume ball, adjoint double layer 0
       const double a = cbrt(3.0 * vol / kFourPi);
       double sn, cs;
@@ -216,7 +193,7 @@ __global__ void corr_rows_kernel(CorrInputs in, const int64_t* __restrict__ row_
     const double w = nr.w / 3.0;
     const double vx = -om * w * nr.x, vy = -om * w * nr.y, vz = -om * w * nr.z;
     double2 acc = make_double2(0, 0), f64 = make_double2(0, 0), f32 = make_double2(0, 0);
-    const bool self = (i == in.n_tet + t);
+    const bool self = (si == in.n_tet + t);
     if (!self) {
       const double2 d = dl_near(X.x, X.y, X.z, in.tri_vtx + 3 * t, Q, nr, k);
       acc = make_double2(om * d.x, om * d.y);
@@ -250,11 +227,11 @@ __global__ void corr_rows_kernel(CorrInputs in, const int64_t* __restrict__ row_
             const int32_t e = g.order[p];
             const double4_32a c = in.tet_cen[e];
             const double dx = X.x - c.x, dy = X.y - c.y, dz = X.z - c.z;
-            if (dx * dx + dy * dy + dz * dz < in.R2v || e == i) vol_entry(e);
+            if (dx * dx + dy * dy + dz * dz < in.R2v || e == si) vol_entry(e);
           }
         }
-  } else if (i < in.n_tet) {
-    vol_entry(i);
+  } else if (si >= 0 && si < in.n_tet) {
+    vol_entry(si);
   }
   // interface part
   if (in.R2t > 0.0) {
@@ -270,7 +247,7 @@ __global__ void corr_rows_kernel(CorrInputs in, const int64_t* __restrict__ row_
             const int32_t t = g.order[p];
             const double4_32a c = in.tri_cen[t];
             const double dx = X.x - c.x, dy = X.y - c.y, dz = X.z - c.z;
-            if (dx * dx + dy * dy + dz * dz < in.R2t || i == in.n_tet + t) tri_entry(t);
+            if (dx * dx + dy * dy + dz * dz < in.R2t || si == in.n_tet + t) tri_entry(t);
           }
         }
   }
@@ -544,10 +521,9 @@ static vsie_status make_grid(vsie_handle* h, const double4_32a* pts, int64_t np,
   int64_t* start;
   VSIE_CUDA(cudaMalloc(&key, sizeof(int64_t) * (np > 0 ? np : 1)));
   temps->push_back(key);
-  VSIE_CUDA(cudaMalloc(&order, sizeof(int32_t) * (np > 0 ? np : 1)));
-  temps->push_back(order);
-  VSIE_CUDA(cudaMalloc(&start, sizeof(int64_t) * (g->ncell + 1)));
-  temps->push_back(start);
+  // the sorted order and the cell starts stay with the handle (field evaluation reuses them)
+  VSIE_TRY(dalloc_t(h, &order, (size_t)(np > 0 ? np : 1)));
+  VSIE_TRY(dalloc_t(h, &start, (size_t)g->ncell + 1));
   if (np > 0) {
     cell_id_kernel<<<(unsigned)((np + 255) / 256), 256>>>(pts, np, *g, key, order);
     VSIE_CUDA(cudaGetLastError());
@@ -562,7 +538,6 @@ static vsie_status make_grid(vsie_handle* h, const double4_32a* pts, int64_t np,
   VSIE_CUDA(cudaGetLastError());
   g->order = order;
   g->start = start;
-  (void)h;
   return VSIE_OK;
 }
 
@@ -653,6 +628,87 @@ vsie_status build_correction(vsie_handle* h, const double4_32a* d_tet_cen, const
   h->C.val32 = reinterpret_cast<float4*>(v32);
   cleanup();
   if (e != cudaSuccess) return cuda_fail(e, "corr_rows_kernel(fill)", __FILE__, __LINE__);
+  h->geo = in;
+  return VSIE_OK;
+}
+
+// ----------------------------------------------------------------- field points
+
+// y_r = -(y_r + sum_k Delta_rk x_col(k)): one warp per field point, the entries in
+// double-float like corr_apply_kernel (no mass term: the points carry no unknown).
+__global__ void __launch_bounds__(256) field_corr_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                         const float4* __restrict__ val, const float4* __restrict__ xd,
+                                                         double2* __restrict__ y, int64_t m) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  float2 S = make_float2(0.0f, 0.0f), C = S;
+  const int64_t pe = rp[row + 1];
+  for (int64_t p = rp[row] + lane; p < pe; p += 32) df_cmac(S, C, val[p], xd[col[p]]);
+  df_renorm2(S, C);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) df_add2(S, C, shfl_down2(S, o), shfl_down2(C, o));
+  if (lane == 0) {
+    const double2 d = df_value(S, C);
+    const double2 o = y[row];
+    y[row] = make_double2(-(o.x + d.x), -(o.y + d.y));
+  }
+}
+
+vsie_status field_correction(vsie_handle* h, const double4_32a* d_pts, int64_t m, const double2* x,
+                             int nrhs, double2* y, int precision, cudaStream_t st) {
+  if (m <= 0 || nrhs <= 0) return VSIE_OK;
+  CorrInputs in = h->geo;
+  in.tgt = d_pts;
+  in.n = m;
+  in.self = 0;
+  int64_t* rp = nullptr;
+  int32_t* col = nullptr;
+  double2 *v64 = nullptr, *v32 = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(rp);
+    cudaFree(col);
+    cudaFree(v64);
+    cudaFree(v32);
+  };
+  auto fail = [&](cudaError_t e, const char* what) {
+    cleanup();
+    return cuda_fail(e, what, __FILE__, __LINE__);
+  };
+  cudaError_t e = cudaMalloc(&rp, sizeof(int64_t) * ((size_t)m + 1));
+  if (e != cudaSuccess) return fail(e, "cudaMalloc(field row_ptr)");
+  e = cudaMemsetAsync(rp, 0, sizeof(int64_t) * ((size_t)m + 1), st);
+  if (e != cudaSuccess) return fail(e, "cudaMemsetAsync(field row_ptr)");
+  const unsigned blocks = (unsigned)((m + 127) / 128);
+  corr_rows_kernel<<<blocks, 128, 0, st>>>(in, nullptr, rp, nullptr, nullptr, nullptr, 0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "corr_rows_kernel(field count)");
+  thrust::exclusive_scan(thrust::cuda::par.on(st), thrust::device_ptr<int64_t>(rp),
+                         thrust::device_ptr<int64_t>(rp + m + 1), thrust::device_ptr<int64_t>(rp));
+  int64_t nnz = 0;
+  if ((e = cudaMemcpyAsync(&nnz, rp + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return fail(e, "cudaMemcpyAsync(field nnz)");
+  const size_t cap = (size_t)(nnz > 0 ? nnz : 1);
+  if ((e = cudaMalloc(&col, sizeof(int32_t) * cap)) != cudaSuccess ||
+      (e = cudaMalloc(&v64, sizeof(double2) * cap)) != cudaSuccess ||
+      (e = cudaMalloc(&v32, sizeof(double2) * cap)) != cudaSuccess)
+    return fail(e, "cudaMalloc(field rows)");
+  corr_rows_kernel<<<blocks, 128, 0, st>>>(in, rp, nullptr, col, v64, v32, 1);
+  if (nnz > 0) {
+    to_df_inplace_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(v64, nnz);
+    to_df_inplace_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(v32, nnz);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "corr_rows_kernel(field fill)");
+  const float4* val = reinterpret_cast<const float4*>(precision == 32 ? v32 : v64);
+  const int64_t n = h->n;
+  for (int c = 0; c < nrhs; ++c) {
+    to_df_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x + (size_t)c * n, h->C.xd, n);
+    field_corr_kernel<<<(unsigned)((m * 32 + 255) / 256), 256, 0, st>>>(rp, col, val, h->C.xd,
+                                                                         y + (size_t)c * m, m);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return fail(e, "field_corr_kernel");
+  cleanup();
   return VSIE_OK;
 }
 

@@ -1190,6 +1190,51 @@ static vsie_status forward(vsie_handle* h, double2* y, int precision, double2* s
   return forward_sums<double>(h, y, P, slots, st, phase_mask, launches);
 }
 
+// The three class sums at m arbitrary points (the records written by far_prescale): the
+// policies of the collocation sums with their target arrays replaced.
+vsie_status far_sums_at(vsie_handle* h, const double2* x, const double4_32a* t64, const float4* t32,
+                        const float4* tdf, int64_t m, double2* y, int precision, cudaStream_t st) {
+  VSIE_TRY(far_prescale(h, x, precision, st, nullptr));
+  StreamK g, k, f;
+  if (precision == 48) {
+    g = plan_sk<double, PolGdf>(h, m, h->G.n);
+    k = plan_sk<double, PolKdf>(h, m, h->K.n);
+    f = plan_sk<double, PolFdf>(h, m, h->F.n);
+  } else if (precision == 32) {
+    g = plan_sk<float, PolG2>(h, m, h->G.n, 0);
+    k = plan_sk<float, PolK2>(h, m, h->K.n, 1);
+    f = plan_sk<float, PerTarget<float, PolF<float>>>(h, m, h->F.n, 2);
+  } else {
+    g = plan_sk<double, PerTarget<double, PolG<double>>>(h, m, h->G.n);
+    k = plan_sk<double, PerTarget<double, PolK<double>>>(h, m, h->K.n);
+    f = plan_sk<double, PerTarget<double, PolF<double>>>(h, m, h->F.n);
+  }
+  double2* slots = nullptr;
+  VSIE_TRY(handle_slots(h, std::max(slot_elems(g), std::max(slot_elems(k), slot_elems(f))), &slots));
+  VSIE_CUDA(cudaMemsetAsync(y, 0, sizeof(double2) * m, st));
+  const int mode = 1;  // every class adds into the zeroed y
+  if (precision == 48) {
+    if (h->G.n) VSIE_TRY((run_nbody<double, PolGdf>(PolGdf{{tdf, h->G.rdf}}, g, y, mode, slots, st, nullptr)));
+    if (h->K.n) VSIE_TRY((run_nbody<double, PolKdf>(PolKdf{{tdf, h->K.rdf}}, k, y, mode, slots, st, nullptr)));
+    if (h->F.n) VSIE_TRY((run_nbody<double, PolFdf>(PolFdf{{tdf, h->F.rdf}}, f, y, mode, slots, st, nullptr)));
+  } else if (precision == 32) {
+    PerTarget<float, PolF<float>> pf = make_f<float>(h);
+    pf.tgt = t32;
+    if (h->G.n) VSIE_TRY((run_nbody<float, PolG2>(PolG2{t32, h->G.r32a, h->G.r32b}, g, y, mode, slots, st, nullptr)));
+    if (h->K.n) VSIE_TRY((run_nbody<float, PolK2>(PolK2{t32, h->K.r32a}, k, y, mode, slots, st, nullptr)));
+    if (h->F.n) VSIE_TRY((run_nbody<float, PerTarget<float, PolF<float>>>(pf, f, y, mode, slots, st, nullptr)));
+  } else {
+    PerTarget<double, PolG<double>> pg = make_g<double>(h);
+    PerTarget<double, PolK<double>> pk = make_k<double>(h);
+    PerTarget<double, PolF<double>> pf = make_f<double>(h);
+    pg.tgt = pk.tgt = pf.tgt = t64;
+    if (h->G.n) VSIE_TRY((run_nbody<double, PerTarget<double, PolG<double>>>(pg, g, y, mode, slots, st, nullptr)));
+    if (h->K.n) VSIE_TRY((run_nbody<double, PerTarget<double, PolK<double>>>(pk, k, y, mode, slots, st, nullptr)));
+    if (h->F.n) VSIE_TRY((run_nbody<double, PerTarget<double, PolF<double>>>(pf, f, y, mode, slots, st, nullptr)));
+  }
+  return VSIE_OK;
+}
+
 // phase bits: 1 the volume (G) sum, 2 the interface (K) sum, 4 the heterogeneous-volume (F)
 // sum; each phase stores into y if it is the first class present, else adds.
 vsie_status far_sum_g(vsie_handle* h, double2* y, int precision, cudaStream_t st, int* launches) {

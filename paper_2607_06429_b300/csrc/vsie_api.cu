@@ -341,18 +341,9 @@ static vsie_status create_impl(const vsie_mesh* mesh, const vsie_material* mat, 
   }
   VSIE_TRY(build_correction(h, d_tet_cen, d_tet_pts, d_tet_s, d_tet_ga, d_tet_vol, d_tri_vtx,
                             d_tri_pts, d_tri_cen, d_tri_nrm, d_tri_omega, lo, hi));
+  // the geometry stays with the handle: field evaluation at arbitrary points builds its
+  // near-rule rows from it (about 200 bytes per tetrahedron)
   VSIE_CUDA(cudaDeviceSynchronize());
-  // create-time geometry is no longer needed
-  for (void* p : {(void*)d_tet_cen, (void*)d_tet_pts, (void*)d_tet_ga, (void*)d_tet_s,
-                  (void*)d_tet_vol, (void*)d_tri_vtx, (void*)d_tri_nrm, (void*)d_tri_omega,
-                  (void*)d_tri_pts, (void*)d_tri_cen}) {
-    for (size_t i = 0; i < h->allocs.size(); ++i)
-      if (h->allocs[i] == p) {
-        h->allocs.erase(h->allocs.begin() + i);
-        break;
-      }
-    cudaFree(p);
-  }
   return VSIE_OK;
 }
 

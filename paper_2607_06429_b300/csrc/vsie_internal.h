@@ -104,6 +104,41 @@ struct BatchBuffers {
   size_t xt_bytes = 0;
 };
 
+// Uniform cell grid over element centroids (cell >= the search radius); elements sorted
+// by cell.  Points outside the box clamp to its boundary cells, which still finds every
+// element within one cell of them.
+struct CellGrid {
+  double lo[3] = {0, 0, 0};
+  double inv = 0;   // 1 / cell size
+  int nc[3] = {0, 0, 0};
+  int64_t ncell = 0;
+  const int32_t* order = nullptr;   // element ids sorted by cell
+  const int64_t* start = nullptr;   // ncell + 1
+};
+
+// Geometry of the near-field rules (device arrays, kept for the life of the handle) and the
+// targets whose correction rows are built: the collocation points (self = 1: a target is
+// its own element's centroid) or arbitrary field points (self = 0).
+struct CorrInputs {
+  const double4_32a* tgt = nullptr;       // n targets
+  const double4_32a* tet_cen = nullptr;   // n_tet
+  const double4_32a* tet_pts = nullptr;   // 4 n_tet
+  const double* tet_s = nullptr;
+  const double4_32a* tet_ga = nullptr;
+  const double* tet_vol = nullptr;
+  const double4_32a* tri_vtx = nullptr;   // 3 n_tri
+  const double4_32a* tri_pts = nullptr;   // 3 n_tri
+  const double4_32a* tri_cen = nullptr;   // n_tri
+  const double4_32a* tri_nrm = nullptr;   // (n, area)
+  const double* tri_omega = nullptr;
+  int64_t n_tet = 0, n_tri = 0, n = 0;
+  int far_points = 1;
+  int self = 1;
+  double R2v = 0, R2t = 0;          // squared radii (0 = inactive)
+  double k = 0;
+  CellGrid gv, gt;
+};
+
 }  // namespace vsie
 
 struct vsie_handle {
@@ -123,6 +158,7 @@ struct vsie_handle {
 
   vsie::Sources G, K, F;
   vsie::Correction C;
+  vsie::CorrInputs geo;       // near-rule geometry and neighbour grids (field evaluation)
 
   // library-owned scratch
   double2* host_x = nullptr;  // device staging of vsie_apply_host
@@ -159,7 +195,18 @@ vsie_status build_correction(vsie_handle* h, const double4_32a* d_tet_cen,
                              const double4_32a* d_tri_pts /*3 per tri*/, const double4_32a* d_tri_cen,
                              const double4_32a* d_tri_nrm /*(n, area)*/, const double* d_tri_omega,
                              const double lo[3], const double hi[3]);
+// Field points (not collocation points): y_r = -(y_r + sum_k Delta(X_r, k) x_k) for each of
+// the nrhs columns (x: n x nrhs, y: m x nrhs), Delta = near-rule minus far-rule values at
+// the points X (the near sets of the create-time radii, no self terms).  Builds the rows
+// with the handle's geometry, applies them and frees them; blocking.
+vsie_status field_correction(vsie_handle* h, const double4_32a* d_pts, int64_t m, const double2* x,
+                             int nrhs, double2* y, int precision, cudaStream_t st);
 
+// Far-field sums at m arbitrary points: y_r = sum_j C(X_r, y_j) p_e(j) (t64: (x, y, z, 0),
+// t32: float(kappa X), tdf: double-float kappa X as (hi, lo) float4 pairs; the one of the
+// precision used is read).  x: n.  Asynchronous on st.
+vsie_status far_sums_at(vsie_handle* h, const double2* x, const double4_32a* t64, const float4* t32,
+                        const float4* tdf, int64_t m, double2* y, int precision, cudaStream_t st);
 // Far-field sums: y (+)= sum_j C(x_i, y_j) p_e(j) over the far-field source points.
 vsie_status far_apply(vsie_handle* h, const double2* x, double2* y, int precision,
                       cudaStream_t st);
