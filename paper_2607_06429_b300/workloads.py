@@ -366,3 +366,150 @@ CONFIGS = {
     "perturbed40_k6_lsq": lambda: nested_perturbed(40, 5, 6.0, lsq=True),
     "nested128_k25": lambda: nested_k25(128, 7, 25.0),
 }
+
+
+# ----------------------------------------------------------------------------- cuboid grids
+
+@dataclasses.dataclass
+class CuboidWorkload:
+    """A nonuniform cuboid grid (the paper's own mesh type) with per-cell material: cell
+    (i, j, k) spans [x_edges[i], x_edges[i+1]] x [y_edges[j], ...] x [z_edges[k], ...];
+    ``rho`` and ``c`` are (nx, ny, nz) arrays; the exterior (and everything outside the
+    grid) has rho0, c0."""
+    name: str
+    x_edges: np.ndarray
+    y_edges: np.ndarray
+    z_edges: np.ndarray
+    rho: np.ndarray
+    c: np.ndarray
+    k0: float
+    rho0: float = 1.0
+    c0: float = 1.0
+    layers: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def shape(self):
+        return self.rho.shape
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.rho.size)
+
+    def centres(self) -> np.ndarray:
+        """Cell centres (n_cells, 3) in the cell order (i, j, k), k fastest."""
+        cx = 0.5 * (self.x_edges[1:] + self.x_edges[:-1])
+        cy = 0.5 * (self.y_edges[1:] + self.y_edges[:-1])
+        cz = 0.5 * (self.z_edges[1:] + self.z_edges[:-1])
+        X, Y, Z = np.meshgrid(cx, cy, cz, indexing="ij")
+        return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+
+def sphere_in_cube(n_cells: int, R: float = 2.5, half: float = 3.0, c2: float = 5.0 / 6.0,
+                   lambda0: float = 2.0) -> CuboidWorkload:
+    """The sphere benchmark of Sec. 3 ("Verification with spherical harmonics"): a uniform
+    n^3 cuboid grid on the cube [-half, half]^3 (Omega_1, with the exterior material), the
+    sphere |x| < R (Omega_2) with speed of sound c2, density 1 everywhere, exterior
+    wavelength lambda0.  A cell takes c2 iff its centre lies inside the sphere (the
+    staircase interface)."""
+    e = np.linspace(-half, half, int(n_cells) + 1)
+    w = CuboidWorkload(name=f"sphere_cube{n_cells}", x_edges=e, y_edges=e.copy(), z_edges=e.copy(),
+                       rho=np.ones((n_cells,) * 3), c=np.ones((n_cells,) * 3),
+                       k0=2.0 * math.pi / lambda0,
+                       layers={"radii": [R], "rho": [1.0], "c": [c2]})
+    ctr = w.centres()
+    inside = (np.linalg.norm(ctr, axis=1) < R).reshape(w.shape)
+    w.c[inside] = c2
+    return w
+
+
+def _matched_edges(breaks, h):
+    """Edges of a nonuniform 1-D grid through every break point: each interval between
+    consecutive breaks is split into ceil(length / h) equal cells."""
+    out = [float(breaks[0])]
+    for a, b in zip(breaks[:-1], breaks[1:]):
+        m = max(1, int(math.ceil((b - a) / h - 1e-9)))
+        out.extend(list(np.linspace(a, b, m + 1)[1:]))
+    return np.asarray(out, dtype=np.float64)
+
+
+def nested_cubes(h: float, side1: float = 7.0, side2: float = 5.0, rho0: float = 1000.0,
+                 rho2: float = 500.0, c0: float = 1482.3, speed_ratio: float = 1.2,
+                 lambda0: float = 3.0) -> CuboidWorkload:
+    """The piecewise-constant density benchmark of Sec. 3: concentric cubes of sides side1
+    (Omega_1) and side2 (Omega_2) centred at the origin (lengths in mm), rho1 = rho0,
+    rho2, c1 = c2 = c0/speed_ratio, exterior wavelength lambda0.  A nonuniform grid whose
+    faces match both interfaces, cells at most h wide."""
+    a, b = 0.5 * side1, 0.5 * side2
+    e = _matched_edges([-a, -b, b, a], h)
+    n = e.shape[0] - 1
+    w = CuboidWorkload(name=f"nested_cubes_h{h:g}", x_edges=e, y_edges=e.copy(), z_edges=e.copy(),
+                       rho=np.full((n,) * 3, rho0), c=np.full((n,) * 3, c0 / speed_ratio),
+                       k0=2.0 * math.pi / lambda0, rho0=rho0, c0=c0)
+    ctr = w.centres()
+    inner = (np.max(np.abs(ctr), axis=1) < b).reshape(w.shape)
+    w.rho[inner] = rho2
+    return w
+
+
+def random_cuboids(shape, seed: int, k0: float = 3.0, jump_fraction: float = 0.5) -> CuboidWorkload:
+    """Seeded nonuniform grid on [-1, 1]^3 with random cell widths and per-cell material:
+    about ``jump_fraction`` of the cells take a random density in [0.5, 2] (the rest the
+    exterior density 1), every cell a random speed of sound in [0.7, 1.3]; many density
+    jumps between neighbouring cells, so every face orientation carries unknowns."""
+    rng = np.random.default_rng(seed)
+
+    def edges(n):
+        w = rng.uniform(0.5, 1.5, n)
+        return np.concatenate([[0.0], np.cumsum(w)]) / w.sum() * 2.0 - 1.0
+
+    nx, ny, nz = shape
+    rho = np.where(rng.random(shape) < jump_fraction, rng.uniform(0.5, 2.0, shape), 1.0)
+    return CuboidWorkload(name=f"random_cuboids{nx}x{ny}x{nz}_s{seed}", x_edges=edges(nx), y_edges=edges(ny),
+                          z_edges=edges(nz), rho=rho, c=rng.uniform(0.7, 1.3, shape), k0=float(k0))
+
+
+def cube_tets(n: int, half: float, rho1: float, c1: float, k0: float, rho0: float = 1.0, c0: float = 1.0,
+              tet_far_points: int = 4, tri_near_factor: float = 2.0) -> Workload:
+    """The cube [-half, half]^3 with constant material as a tetrahedral workload: the n^3
+    voxels Kuhn-split into six tetrahedra each, every boundary square split into two
+    outward-oriented triangles (Gamma_1)."""
+    h = 2.0 * half / n
+    M = n + 1
+
+    def node(i, j, k):
+        return (i * M + j) * M + k
+
+    I, J, K = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    base = np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1)
+    unit = np.eye(3, dtype=np.int64)
+    tets = np.empty((base.shape[0], 6, 4), dtype=np.int64)
+    for t, perm in enumerate(_KUHN_PERMS):
+        p1 = base + unit[perm[0]]
+        p2 = p1 + unit[perm[1]]
+        for q, pq in enumerate((base, p1, p2, base + 1)):
+            tets[:, t, q] = node(pq[:, 0], pq[:, 1], pq[:, 2])
+    g = np.arange(M)
+    GI, GJ, GK = np.meshgrid(g, g, g, indexing="ij")
+    vert = np.stack([GI.ravel(), GJ.ravel(), GK.ravel()], axis=1) * h - half
+    tris = []
+    for ax in range(3):
+        b1, b2 = (ax + 1) % 3, (ax + 2) % 3
+        for side, sgn in ((0, -1.0), (n, 1.0)):
+            for u in range(n):
+                for v in range(n):
+                    def p(du, dv):
+                        q = [0, 0, 0]
+                        q[ax], q[b1], q[b2] = side, u + du, v + dv
+                        return node(*q)
+                    a, b, c, d = p(0, 0), p(1, 0), p(1, 1), p(0, 1)
+                    # (b1, b2, ax) is right-handed: a->b->c is counter-clockwise about +ax
+                    quad = [(a, b, c), (a, c, d)] if sgn > 0 else [(a, c, b), (a, d, c)]
+                    tris.extend(quad)
+    tri = np.asarray(tris, dtype=np.int32)
+    nt = tets.shape[0] * 6
+    return Workload(name=f"cube_tets{n}", vert=vert.astype(np.float64), tet=tets.reshape(-1, 4).astype(np.int32),
+                    tri=tri, tri_iface=np.ones(tri.shape[0], dtype=np.int8), rho=np.full(nt, rho1),
+                    c=np.full(nt, c1), grad_alpha=None, tri_rho_in=np.full(tri.shape[0], rho1),
+                    tri_rho_out=np.full(tri.shape[0], rho0), k0=float(k0), rho0=rho0, c0=c0,
+                    tet_far_points=tet_far_points, tri_near_radius=tri_near_factor * h * math.sqrt(2.0), h=h,
+                    R1=half)
