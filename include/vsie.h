@@ -101,6 +101,32 @@ typedef struct {
 vsie_status vsie_create(const vsie_mesh* mesh, const vsie_material* mat, double k0,
                         const vsie_options* opt, vsie_handle** out);
 
+/* Nonuniform cuboid grid (Sec. 2.3.4, "Computational domain"): nx x ny x nz cells
+ * [x_i, x_{i+1}] x [y_j, y_{j+1}] x [z_k, z_{k+1}]; every cell face meets exactly one
+ * neighbouring face (no hanging nodes), so interfaces that follow cell faces are matched. */
+typedef struct {
+  int32_t nx, ny, nz;
+  const double* x_edges;    /* nx + 1 strictly increasing coordinates */
+  const double* y_edges;    /* ny + 1 */
+  const double* z_edges;    /* nz + 1 */
+} vsie_cuboid_grid;
+
+/* Build the operator of the paper's own discretisation (Sec. 2.3.4, "Discrete
+ * representation"): P0 unknowns on the cells and on the rectangular faces across which
+ * the density jumps, collocation at the centroids, every integral by the midpoint rule, the
+ * single-layer self term over the ball of equal volume (the double-layer self term of a
+ * flat face is 0).  rho, c: host nx*ny*nz per-cell density and sound speed, cell (i, j, k)
+ * at (i ny + j) nz + k; rho0, c0: the exterior material (also the material outside the
+ * grid); k0 = omega/c0.  Unknown order: the cells, then the jump faces normal to x (face a
+ * between cells a-1 and a, a = 0..nx, outside the grid the exterior density), ordered by
+ * (a, j, k), then those normal to y by (i, b, k), then those normal to z by (i, j, c);
+ * a face's normal is the +axis direction, its "in" side the cell below.  The handle
+ * serves every entry point of the tetrahedral one; the field-point near rules are off.
+ * Blocking.  Errors: VSIE_ERR_ARG (null/size), VSIE_ERR_MESH (edges not increasing,
+ * non-positive material), VSIE_ERR_OOM, VSIE_ERR_CUDA. */
+vsie_status vsie_create_cuboid(const vsie_cuboid_grid* grid, const double* rho, const double* c,
+                               double rho0, double c0, double k0, vsie_handle** out);
+
 void vsie_destroy(vsie_handle* h);
 
 /* Sizes of the discrete system. */

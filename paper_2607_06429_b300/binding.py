@@ -30,7 +30,7 @@ EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_appl
            "vsie_graph_create_batched", "vsie_graph_launch", "vsie_graph_nodes", "vsie_graph_destroy",
            "vsie_autotune", "vsie_gradient_channels", "vsie_source_points",
            "vsie_lsq_grad_alpha", "vsie_lsq_grad_alpha_adjoint", "vsie_scattered_field",
-           "vsie_last_error")
+           "vsie_create_cuboid", "vsie_last_error")
 
 
 class VsieError(RuntimeError):
@@ -50,6 +50,11 @@ class _Material(ctypes.Structure):
                 ("rho", ctypes.c_void_p), ("c", ctypes.c_void_p),
                 ("grad_alpha", ctypes.c_void_p), ("tri_rho_in", ctypes.c_void_p),
                 ("tri_rho_out", ctypes.c_void_p)]
+
+
+class _CuboidGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("x_edges", ctypes.c_void_p), ("y_edges", ctypes.c_void_p), ("z_edges", ctypes.c_void_p)]
 
 
 class _Options(ctypes.Structure):
@@ -116,6 +121,7 @@ def load_library(path: str = LIB_PATH):
     lib.vsie_far_field.argtypes = [P, P, I32, P, I32, P, P]
     lib.vsie_far_field_adjoint.argtypes = [P, P, I32, P, I32, P, P]
     lib.vsie_scattered_field.argtypes = [P, P, I32, P, I64, I32, P, P]
+    lib.vsie_create_cuboid.argtypes = [ctypes.POINTER(_CuboidGrid), P, P, D, D, D, ctypes.POINTER(P)]
     lib.vsie_solve.argtypes = [P, P, P, ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), P]
     lib.vsie_solve_batched.argtypes = [P, P, P, ctypes.c_int32, ctypes.POINTER(_SolveOpts),
                                        ctypes.POINTER(_SolveInfo), P]
@@ -210,6 +216,25 @@ class Operator:
         return cls(w.vert, w.tet, w.tri, w.rho, w.c, w.tri_rho_in, w.tri_rho_out, w.k0,
                    w.rho0, w.c0, ga, w.tet_far_points, w.near_radius,
                    w.tri_near_radius, **kw)
+
+    @classmethod
+    def from_cuboid(cls, w):
+        """The paper's cuboid discretisation of a CuboidWorkload (vsie_create_cuboid)."""
+        lib = load_library()
+        ex, ey, ez = (_f64(e) for e in (w.x_edges, w.y_edges, w.z_edges))
+        rho, c = _f64(np.asarray(w.rho).reshape(-1)), _f64(np.asarray(w.c).reshape(-1))
+        grid = _CuboidGrid(ex.shape[0] - 1, ey.shape[0] - 1, ez.shape[0] - 1, _ptr(ex), _ptr(ey), _ptr(ez))
+        h = ctypes.c_void_p()
+        _check(lib.vsie_create_cuboid(ctypes.byref(grid), _ptr(rho), _ptr(c), float(w.rho0), float(w.c0),
+                                      float(w.k0), ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self._h = h
+        self._keep = None
+        n, nf, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.vsie_sizes(h, ctypes.byref(n), ctypes.byref(nf), ctypes.byref(nnz)))
+        self.n, self.n_far_sources, self.nnz = n.value, nf.value, nnz.value
+        self.k0 = float(w.k0)
+        return self
 
     def close(self):
         if getattr(self, "_h", None):

@@ -110,15 +110,16 @@ extern "C" vsie_status vsie_sizes(const vsie_handle* h, int64_t* n, int64_t* n_f
   return VSIE_OK;
 }
 
-static vsie_status create_impl(const vsie_mesh* mesh, const vsie_material* mat, double k0,
-                               const vsie_options* opt, vsie_handle* h) {
-  const int64_t nv = mesh->n_vert, nt = mesh->n_tet, ns = mesh->n_tri;
-  h->n_tet = nt;
-  h->n_tri = ns;
-  h->n = nt + ns;
-  h->k0 = k0;
-  h->rho0 = mat->rho0;
-  h->c0 = mat->c0;
+// Per-element quantities of either mesh type, consumed by finish_create.
+struct ElementGeometry {
+  std::vector<double4_32a> tet_cen, tet_pts, tet_ga;   // volume elements ("tet" for either type)
+  std::vector<double> tet_vol, tet_s, mass;
+  std::vector<double4_32a> tri_vtx, tri_nrm, tri_cen, tri_pts;  // interface elements
+  std::vector<double> tri_omega;
+  int tri_npts = 3;  // far-rule points per interface element: 3 (triangles) or 1 (midpoint)
+};
+
+static vsie_status set_options(vsie_handle* h, const vsie_options* opt) {
   h->far_points = opt ? opt->tet_far_points : 1;
   h->near_radius = opt ? opt->near_radius : 0.0;
   h->tri_near_radius = opt ? opt->tri_near_radius : 0.0;
@@ -132,13 +133,36 @@ static vsie_status create_impl(const vsie_mesh* mesh, const vsie_material* mat, 
     set_error("vsie_create: negative near radius");
     return VSIE_ERR_ARG;
   }
+  return VSIE_OK;
+}
+
+static vsie_status tet_geometry(const vsie_mesh* mesh, const vsie_material* mat, double k0, vsie_handle* h,
+                                ElementGeometry& g) {
+  const int64_t nv = mesh->n_vert, nt = mesh->n_tet, ns = mesh->n_tri;
+  h->n_tet = nt;
+  h->n_tri = ns;
+  h->n = nt + ns;
   const double rho0 = mat->rho0, c0 = mat->c0;
   const double omega = k0 * c0;  // k0 = omega / c0
-  const int FP = h->far_points;
-
+  auto& tet_cen = g.tet_cen;
+  auto& tet_pts = g.tet_pts;
+  auto& tet_ga = g.tet_ga;
+  auto& tet_vol = g.tet_vol;
+  auto& tet_s = g.tet_s;
+  auto& mass = g.mass;
+  auto& tri_vtx = g.tri_vtx;
+  auto& tri_nrm = g.tri_nrm;
+  auto& tri_cen = g.tri_cen;
+  auto& tri_pts = g.tri_pts;
+  auto& tri_omega = g.tri_omega;
+  g.tri_npts = 3;
   // ---------------------------------------------------------------- volume elements
-  std::vector<double4_32a> tet_cen(nt), tet_pts(4 * nt), tet_ga(nt);
-  std::vector<double> tet_vol(nt), tet_s(nt), mass(h->n);
+  tet_cen.resize(nt);
+  tet_pts.resize(4 * nt);
+  tet_ga.resize(nt);
+  tet_vol.resize(nt);
+  tet_s.resize(nt);
+  mass.resize(h->n);
   for (int64_t e = 0; e < nt; ++e) {
     double P[12];
     for (int v = 0; v < 4; ++v) {
@@ -188,8 +212,11 @@ static vsie_status create_impl(const vsie_mesh* mesh, const vsie_material* mat, 
   }
 
   // ---------------------------------------------------------------- interface elements
-  std::vector<double4_32a> tri_vtx(3 * ns), tri_nrm(ns), tri_cen(ns), tri_pts(3 * ns);
-  std::vector<double> tri_omega(ns);
+  tri_vtx.resize(3 * ns);
+  tri_nrm.resize(ns);
+  tri_cen.resize(ns);
+  tri_pts.resize(3 * ns);
+  tri_omega.resize(ns);
   for (int64_t t = 0; t < ns; ++t) {
     double P[9];
     for (int v = 0; v < 3; ++v) {
@@ -228,6 +255,116 @@ static vsie_status create_impl(const vsie_mesh* mesh, const vsie_material* mat, 
     mass[nt + t] = 0.5 * (rho0 / rin + rho0 / rout);
   }
 
+  return VSIE_OK;
+}
+
+// Cuboid grid (Sec. 2.3.4, computational domain and discrete representation): P0 unknowns
+// on the cells and on the rectangular cell faces across which the density jumps; every
+// integral by the midpoint rule (one far-field point per element), the single-layer self
+// term over the ball of equal volume, the double-layer self term of a flat face 0, no near
+// rules.  Cells in the order (i ny + j) nz + k; then the jump faces normal to x (face a
+// between cells a-1 and a, the background outside the grid), ordered by (a, j, k), then
+// those normal to y by (i, b, k), then those normal to z by (i, j, c); a face's normal is
+// the +axis, "in" the cell below it and "out" the one above.
+static vsie_status cuboid_geometry(const vsie_cuboid_grid* grid, const double* rho, const double* c,
+                                   double k0, vsie_handle* h, ElementGeometry& g) {
+  const int64_t nx = grid->nx, ny = grid->ny, nz = grid->nz;
+  const double rho0 = h->rho0, c0 = h->c0;
+  const double omega = k0 * c0;
+  const double* E[3] = {grid->x_edges, grid->y_edges, grid->z_edges};
+  const int64_t N[3] = {nx, ny, nz};
+  for (int d = 0; d < 3; ++d)
+    for (int64_t a = 0; a < N[d]; ++a)
+      if (!(E[d][a + 1] > E[d][a]) || !std::isfinite(E[d][a]) || !std::isfinite(E[d][a + 1])) {
+        set_error("vsie_create_cuboid: edge coordinates must be finite and strictly increasing");
+        return VSIE_ERR_MESH;
+      }
+  const int64_t nc = nx * ny * nz;
+  auto cell = [&](int64_t i, int64_t j, int64_t k) { return (i * ny + j) * nz + k; };
+  g.tet_cen.resize(nc);
+  g.tet_pts.resize(4 * nc);
+  g.tet_ga.assign(nc, make_double4_32a(0.0, 0.0, 0.0, 0.0));
+  g.tet_vol.resize(nc);
+  g.tet_s.resize(nc);
+  g.mass.resize(nc);
+  for (int64_t i = 0; i < nx; ++i)
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t k = 0; k < nz; ++k) {
+        const int64_t e = cell(i, j, k);
+        if (!finite_pos(rho[e]) || !finite_pos(c[e])) {
+          set_error("vsie_create_cuboid: non-positive or non-finite material on cell " + std::to_string(e));
+          return VSIE_ERR_MESH;
+        }
+        const double alpha = rho0 / rho[e] - 1.0;                                        // Eq. (alpha)
+        const double beta = (rho0 / rho[e]) * (omega / c[e]) * (omega / c[e]) - (omega / c0) * (omega / c0);  // Eq. (beta)
+        const double4_32a ctr = make_double4_32a(0.5 * (E[0][i] + E[0][i + 1]), 0.5 * (E[1][j] + E[1][j + 1]),
+                                                 0.5 * (E[2][k] + E[2][k + 1]), 0.0);
+        g.tet_cen[e] = ctr;
+        for (int q = 0; q < 4; ++q) g.tet_pts[4 * e + q] = ctr;  // unused: no four-point rule
+        g.tet_vol[e] = (E[0][i + 1] - E[0][i]) * (E[1][j + 1] - E[1][j]) * (E[2][k + 1] - E[2][k]);
+        g.tet_s[e] = beta - k0 * k0 * alpha;
+        g.mass[e] = rho0 / rho[e];                                                         // Eq. (mass_function)
+      }
+  // jump faces, axis by axis
+  for (int ax = 0; ax < 3; ++ax) {
+    const int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;  // the face's in-plane axes
+    const int lo1 = std::min(b1, b2), lo2 = std::max(b1, b2);
+    for (int64_t u = 0; u < (ax == 0 ? N[0] + 1 : N[0]); ++u)
+      for (int64_t v = 0; v < (ax == 1 ? N[1] + 1 : N[1]); ++v)
+        for (int64_t w = 0; w < (ax == 2 ? N[2] + 1 : N[2]); ++w) {
+          int64_t I[3] = {u, v, w};
+          const int64_t a = I[ax];
+          int64_t below[3] = {I[0], I[1], I[2]}, above[3] = {I[0], I[1], I[2]};
+          below[ax] = a - 1;
+          const double rin = a > 0 ? rho[cell(below[0], below[1], below[2])] : rho0;
+          const double rout = a < N[ax] ? rho[cell(above[0], above[1], above[2])] : rho0;
+          if (rin == rout) continue;
+          double ctr[3], nrm[3] = {0.0, 0.0, 0.0};
+          ctr[ax] = E[ax][a];
+          ctr[lo1] = 0.5 * (E[lo1][I[lo1]] + E[lo1][I[lo1] + 1]);
+          ctr[lo2] = 0.5 * (E[lo2][I[lo2]] + E[lo2][I[lo2] + 1]);
+          nrm[ax] = 1.0;
+          const double area = (E[lo1][I[lo1] + 1] - E[lo1][I[lo1]]) * (E[lo2][I[lo2] + 1] - E[lo2][I[lo2]]);
+          const double4_32a cc = make_double4_32a(ctr[0], ctr[1], ctr[2], 0.0);
+          g.tri_cen.push_back(cc);
+          for (int q = 0; q < 3; ++q) {  // unused: midpoint rule, no near rule
+            g.tri_vtx.push_back(cc);
+            g.tri_pts.push_back(cc);
+          }
+          g.tri_nrm.push_back(make_double4_32a(nrm[0], nrm[1], nrm[2], area));
+          g.tri_omega.push_back(rho0 / rin - rho0 / rout);   // alpha_in - alpha_out
+          g.mass.push_back(0.5 * (rho0 / rin + rho0 / rout));  // Eq. (mass_function) on an interface
+        }
+  }
+  g.tri_npts = 1;
+  h->n_tet = nc;
+  h->n_tri = (int64_t)g.tri_cen.size();
+  h->n = h->n_tet + h->n_tri;
+  if (h->n > (int64_t)INT32_MAX / 4) {
+    set_error("vsie_create_cuboid: too many unknowns");
+    return VSIE_ERR_ARG;
+  }
+  return VSIE_OK;
+}
+
+// Everything after the element geometry, common to both mesh types: far-field source
+// classes, targets, records, and the self / near correction.
+static vsie_status finish_create(vsie_handle* h, ElementGeometry& g) {
+  const int64_t nt = h->n_tet, ns = h->n_tri;
+  const double k0 = h->k0;
+  const int FP = h->far_points;
+  const auto& tet_cen = g.tet_cen;
+  const auto& tet_pts = g.tet_pts;
+  const auto& tet_ga = g.tet_ga;
+  const auto& tet_vol = g.tet_vol;
+  const auto& tet_s = g.tet_s;
+  const auto& mass = g.mass;
+  const auto& tri_vtx = g.tri_vtx;
+  const auto& tri_nrm = g.tri_nrm;
+  const auto& tri_cen = g.tri_cen;
+  const auto& tri_pts = g.tri_pts;
+  const auto& tri_omega = g.tri_omega;
+  const int TP = g.tri_npts;
   // ---------------------------------------------------------------- far-field sources
   // G: volume points with grad(alpha) = 0; F: volume points with grad(alpha) != 0;
   // K: interface points (v = sigma n, sigma = -omega w since dG/dn_y = -grad_x G . n).
@@ -253,10 +390,10 @@ static vsie_status create_impl(const vsie_mesh* mesh, const vsie_material* mat, 
   for (int64_t t = 0; t < ns; ++t) {
     k_first.push_back((int32_t)k_ps.size());
     k_elem.push_back((int32_t)(nt + t));
-    const double w = tri_nrm[t].w / 3.0;
+    const double w = tri_nrm[t].w / TP;
     const double sigma = -tri_omega[t] * w;
-    for (int q = 0; q < 3; ++q) {
-      const double4_32a y = tri_pts[3 * t + q];
+    for (int q = 0; q < TP; ++q) {
+      const double4_32a y = TP == 1 ? tri_cen[t] : tri_pts[3 * t + q];
       k_ps.push_back(make_double4_32a(y.x, y.y, y.z, 0.0));
       k_v.push_back(make_double4_32a(sigma * tri_nrm[t].x, sigma * tri_nrm[t].y, sigma * tri_nrm[t].z, 0.0));
       k_aux.push_back(make_double4_32a(tri_nrm[t].x, tri_nrm[t].y, tri_nrm[t].z, sigma));
@@ -347,6 +484,17 @@ static vsie_status create_impl(const vsie_mesh* mesh, const vsie_material* mat, 
   return VSIE_OK;
 }
 
+static vsie_status create_impl(const vsie_mesh* mesh, const vsie_material* mat, double k0,
+                               const vsie_options* opt, vsie_handle* h) {
+  h->k0 = k0;
+  h->rho0 = mat->rho0;
+  h->c0 = mat->c0;
+  VSIE_TRY(set_options(h, opt));
+  ElementGeometry g;
+  VSIE_TRY(tet_geometry(mesh, mat, k0, h, g));
+  return finish_create(h, g);
+}
+
 extern "C" vsie_status vsie_create(const vsie_mesh* mesh, const vsie_material* mat, double k0,
                                    const vsie_options* opt, vsie_handle** out) {
   clear_error();
@@ -378,6 +526,53 @@ extern "C" vsie_status vsie_create(const vsie_mesh* mesh, const vsie_material* m
   }
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   vsie_status s = create_impl(mesh, mat, k0, opt, h);
+  if (s != VSIE_OK) {
+    std::string msg = vsie_last_error();
+    vsie_destroy(h);
+    set_error(msg);
+    return s;
+  }
+  *out = h;
+  return VSIE_OK;
+}
+
+extern "C" vsie_status vsie_create_cuboid(const vsie_cuboid_grid* grid, const double* rho, const double* c,
+                                          double rho0, double c0, double k0, vsie_handle** out) {
+  clear_error();
+  if (!out) {
+    set_error("vsie_create_cuboid: null output pointer");
+    return VSIE_ERR_ARG;
+  }
+  *out = nullptr;
+  if (!grid || !rho || !c || !grid->x_edges || !grid->y_edges || !grid->z_edges) {
+    set_error("vsie_create_cuboid: null grid or material array");
+    return VSIE_ERR_ARG;
+  }
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 ||
+      (int64_t)grid->nx * grid->ny * grid->nz > (int64_t)INT32_MAX / 8) {
+    set_error("vsie_create_cuboid: grid sizes out of range");
+    return VSIE_ERR_ARG;
+  }
+  if (!(k0 > 0.0) || !std::isfinite(k0) || !finite_pos(rho0) || !finite_pos(c0)) {
+    set_error("vsie_create_cuboid: k0, rho0 and c0 must be positive and finite");
+    return VSIE_ERR_ARG;
+  }
+  vsie_handle* h = new vsie_handle();
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "cudaGetDevice", __FILE__, __LINE__);
+  }
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  h->k0 = k0;
+  h->rho0 = rho0;
+  h->c0 = c0;
+  vsie_options opt{};
+  opt.tet_far_points = 1;  // midpoint rule, no near rules
+  ElementGeometry g;
+  vsie_status s = set_options(h, &opt);
+  if (s == VSIE_OK) s = cuboid_geometry(grid, rho, c, k0, h, g);
+  if (s == VSIE_OK) s = finish_create(h, g);
   if (s != VSIE_OK) {
     std::string msg = vsie_last_error();
     vsie_destroy(h);

@@ -1,0 +1,121 @@
+"""The paper's own cuboid discretisation (vsie_create_cuboid) through the C ABI: parity
+with the cuboid oracle, and the sphere benchmark of Sec. 3 reproduced on the GPU.
+
+Parity: full vectors on small grids (no faces; matched nested cubes; random per-cell
+material with jump faces of every orientation), relative L2 <= 1e-12 for the FP64 and
+double-float applies, <= 1e-5 for FP32, and the adjoint.  Benchmark: the sphere r = 2.5
+in the cube [-3, 3]^3 (c2 = 5/6, lambda0 = 2), solved with the mixed solver at 4, 8 and 16
+cells per interior wavelength; relative errors on the z = 0 slice of cell centres against
+the Mie series below 3% at 8 cells per wavelength in both norms, and about second-order
+convergence in the number of cells per dimension."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cuboid_oracle as CO
+from oracle import series as S
+from paper_2607_06429_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+TOL64 = 1e-12
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    return torch
+
+
+def _op(w):
+    from paper_2607_06429_b300 import binding as B
+    from paper_2607_06429_b300 import build as BUILD
+    BUILD.build()
+    return B.Operator.from_cuboid(w)
+
+
+def _cuda(v):
+    torch = _torch()
+    return torch.from_numpy(np.ascontiguousarray(v)).to("cuda")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+SMALL = {
+    "sphere_cube9": lambda: W.sphere_in_cube(9),
+    "nested_cubes_h1": lambda: W.nested_cubes(1.0),
+    "random_6x5x7": lambda: W.random_cuboids((6, 5, 7), seed=11),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SMALL))
+def test_cuboid_apply_matches_oracle(name):
+    _torch()
+    w = SMALL[name]()
+    op = _op(w)
+    D = CO.CuboidDiscretisation.from_workload(w)
+    assert op.n == D.n
+    A = D.assemble()
+    X = np.stack([W.random_vector(D.n, s) for s in (3, 4)])
+    ref = X @ A.T
+    Xd = _cuda(X)
+    for prec, tol in ((64, TOL64), (48, TOL64), (32, TOL32)):
+        got = op.apply(Xd, precision=prec).cpu().numpy()
+        assert rel(got, ref) <= tol, (name, prec, rel(got, ref))
+    lam = W.random_vector(D.n, 9)
+    xa = op.adjoint_apply(_cuda(lam), precision=64).cpu().numpy()
+    assert rel(xa, A.conj().T @ lam) <= TOL64
+
+
+def test_cuboid_face_count_and_exterior_field():
+    """Matched nested cubes: the unknowns are the cells plus the 6 x 25 faces of the inner
+    cube (rho1 = rho0, so the outer cube has none); the scattered field at exterior points
+    (midpoint rule, no near rows on a cuboid handle) against the oracle."""
+    _torch()
+    w = W.nested_cubes(1.0)
+    op = _op(w)
+    D = CO.CuboidDiscretisation.from_workload(w)
+    assert D.n_face == 150 and op.n == 343 + 150
+    x = W.random_vector(D.n, 21)
+    pts = 6.0 * W.fibonacci_dirs(20)
+    got = op.scattered_field(_cuda(x), pts, precision=64).cpu().numpy()
+    assert rel(got, D.scattered_field(x, pts)) <= TOL64
+
+
+def _slice_error(N):
+    from paper_2607_06429_b300 import binding as B  # noqa: F401
+    w = W.sphere_in_cube(N)
+    op = _op(w)
+    d = np.array([1.0, 0.0, 0.0])
+    b = op.plane_wave_rhs(d)[0]
+    x, info = op.solve(b, mode=32, tol=1e-8)
+    assert info.rel_residual <= 1e-8
+    p = x.cpu().numpy()
+    ctr = w.centres()
+    sl = np.abs(ctr[:, 2]) < 1e-12
+    ref = S.layered_sphere_field(ctr[sl], d, w.k0, [2.5], [1.0], [5.0 / 6.0])
+    e2 = np.linalg.norm(p[sl] - ref) / np.linalg.norm(ref)
+    einf = np.max(np.abs(p[sl] - ref)) / np.max(np.abs(ref))
+    per_lambda = (5.0 / 3.0) / (6.0 / N)
+    print(f"sphere benchmark N={N} ({per_lambda:.2f} cells per interior wavelength, n={op.n}): "
+          f"E2={e2:.4e} Einf={einf:.4e} iterations={info.iterations}")
+    return e2, einf
+
+
+def test_sphere_benchmark_reproduction():
+    """Sec. 3: below 3% at 8 cells per interior wavelength (N = 29), both norms; second-order
+    convergence over N = 15, 29, 57."""
+    _torch()
+    e15 = _slice_error(15)
+    e29 = _slice_error(29)
+    e57 = _slice_error(57)
+    assert e29[0] < 0.03 and e29[1] < 0.03, e29
+    assert e57[0] < e29[0] < e15[0]
+    order = math.log(e15[0] / e57[0]) / math.log(57.0 / 15.0)
+    print(f"sphere benchmark: observed order {order:.2f} over N = 15..57")
+    assert order > 1.5, order
