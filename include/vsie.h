@@ -127,6 +127,17 @@ typedef struct {
 vsie_status vsie_create_cuboid(const vsie_cuboid_grid* grid, const double* rho, const double* c,
                                double rho0, double c0, double k0, vsie_handle** out);
 
+/* Change the frequency of an existing operator: k0 = omega/c0 enters the volume weights
+ * through beta (Eq. beta) and every pair through G = exp(i k0 r)/(4 pi r) (Eq.
+ * greens_function), so the weights, source records and the near/self correction are
+ * rebuilt from the creation inputs (kept on the host by vsie_create / vsie_create_cuboid)
+ * exactly as a new create at k0 would build them; the geometry, material and the work
+ * shapes chosen by vsie_autotune stay.  Blocking (synchronises the device first).
+ * Every device buffer of the handle is reallocated, so CUDA-graph plans recorded on it
+ * (vsie_graph_create_batched) must be recreated.  On an error other than VSIE_ERR_ARG the
+ * handle holds no operator and may only be destroyed. */
+vsie_status vsie_set_frequency(vsie_handle* h, double k0);
+
 void vsie_destroy(vsie_handle* h);
 
 /* Sizes of the discrete system. */

@@ -30,7 +30,7 @@ EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_appl
            "vsie_graph_create_batched", "vsie_graph_launch", "vsie_graph_nodes", "vsie_graph_destroy",
            "vsie_autotune", "vsie_gradient_channels", "vsie_source_points",
            "vsie_lsq_grad_alpha", "vsie_lsq_grad_alpha_adjoint", "vsie_scattered_field",
-           "vsie_create_cuboid", "vsie_last_error")
+           "vsie_create_cuboid", "vsie_set_frequency", "vsie_last_error")
 
 
 class VsieError(RuntimeError):
@@ -122,6 +122,7 @@ def load_library(path: str = LIB_PATH):
     lib.vsie_far_field_adjoint.argtypes = [P, P, I32, P, I32, P, P]
     lib.vsie_scattered_field.argtypes = [P, P, I32, P, I64, I32, P, P]
     lib.vsie_create_cuboid.argtypes = [ctypes.POINTER(_CuboidGrid), P, P, D, D, D, ctypes.POINTER(P)]
+    lib.vsie_set_frequency.argtypes = [P, D]
     lib.vsie_solve.argtypes = [P, P, P, ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), P]
     lib.vsie_solve_batched.argtypes = [P, P, P, ctypes.c_int32, ctypes.POINTER(_SolveOpts),
                                        ctypes.POINTER(_SolveInfo), P]
@@ -235,6 +236,11 @@ class Operator:
         self.n, self.n_far_sources, self.nnz = n.value, nf.value, nnz.value
         self.k0 = float(w.k0)
         return self
+
+    def set_frequency(self, k0):
+        """Rebuild the operator for a new k0 (vsie_set_frequency)."""
+        _check(_lib.vsie_set_frequency(self._h, float(k0)))
+        self.k0 = float(k0)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -532,8 +532,72 @@ extern "C" vsie_status vsie_create(const vsie_mesh* mesh, const vsie_material* m
     set_error(msg);
     return s;
   }
+  auto& in = h->inputs;
+  in.kind = 0;
+  in.vert.assign(mesh->vert, mesh->vert + 3 * mesh->n_vert);
+  in.tet.assign(mesh->tet, mesh->tet + 4 * mesh->n_tet);
+  if (mesh->n_tri) {
+    in.tri.assign(mesh->tri, mesh->tri + 3 * mesh->n_tri);
+    in.tri_rho_in.assign(mat->tri_rho_in, mat->tri_rho_in + mesh->n_tri);
+    in.tri_rho_out.assign(mat->tri_rho_out, mat->tri_rho_out + mesh->n_tri);
+  }
+  if (mesh->n_tet) {
+    in.rho.assign(mat->rho, mat->rho + mesh->n_tet);
+    in.c.assign(mat->c, mat->c + mesh->n_tet);
+  }
+  in.has_grad_alpha = mat->grad_alpha != nullptr;
+  if (in.has_grad_alpha) in.grad_alpha.assign(mat->grad_alpha, mat->grad_alpha + 3 * mesh->n_tet);
+  in.has_opt = opt != nullptr;
+  if (opt) in.opt = *opt;
   *out = h;
   return VSIE_OK;
+}
+
+// Rebuild every frequency-dependent part of the handle (weights, records, correction) for
+// a new k0 from the saved creation inputs; the material, geometry and autotuned shapes stay.
+extern "C" vsie_status vsie_set_frequency(vsie_handle* h, double k0) {
+  clear_error();
+  if (!h || !(k0 > 0.0) || !std::isfinite(k0)) {
+    set_error("vsie_set_frequency: null handle or k0 not positive and finite");
+    return VSIE_ERR_ARG;
+  }
+  VSIE_CUDA(cudaDeviceSynchronize());
+  const int device = h->device, sms = h->num_sms;
+  const double rho0 = h->rho0, c0 = h->c0;
+  const auto tune = h->tune;
+  auto inputs = std::move(h->inputs);
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  *h = vsie_handle();
+  h->device = device;
+  h->num_sms = sms;
+  h->tune = tune;
+  h->inputs = std::move(inputs);
+  auto& in = h->inputs;
+  vsie_status s;
+  if (in.kind == 0) {
+    const vsie_mesh mesh{(int64_t)(in.vert.size() / 3), in.vert.data(), (int64_t)(in.tet.size() / 4),
+                         in.tet.data(), (int64_t)(in.tri.size() / 3), in.tri.empty() ? nullptr : in.tri.data()};
+    const vsie_material mat{rho0, c0, in.rho.data(), in.c.data(),
+                            in.has_grad_alpha ? in.grad_alpha.data() : nullptr,
+                            in.tri_rho_in.empty() ? nullptr : in.tri_rho_in.data(),
+                            in.tri_rho_out.empty() ? nullptr : in.tri_rho_out.data()};
+    s = create_impl(&mesh, &mat, k0, in.has_opt ? &in.opt : nullptr, h);
+  } else {
+    const vsie_cuboid_grid grid{(int32_t)in.x_edges.size() - 1, (int32_t)in.y_edges.size() - 1,
+                                (int32_t)in.z_edges.size() - 1, in.x_edges.data(), in.y_edges.data(),
+                                in.z_edges.data()};
+    h->k0 = k0;
+    h->rho0 = rho0;
+    h->c0 = c0;
+    vsie_options opt{};
+    opt.tet_far_points = 1;
+    ElementGeometry g;
+    s = set_options(h, &opt);
+    if (s == VSIE_OK) s = cuboid_geometry(&grid, in.rho.data(), in.c.data(), k0, h, g);
+    if (s == VSIE_OK) s = finish_create(h, g);
+  }
+  return s;
 }
 
 extern "C" vsie_status vsie_create_cuboid(const vsie_cuboid_grid* grid, const double* rho, const double* c,
@@ -579,6 +643,14 @@ extern "C" vsie_status vsie_create_cuboid(const vsie_cuboid_grid* grid, const do
     set_error(msg);
     return s;
   }
+  auto& in = h->inputs;
+  in.kind = 1;
+  in.x_edges.assign(grid->x_edges, grid->x_edges + grid->nx + 1);
+  in.y_edges.assign(grid->y_edges, grid->y_edges + grid->ny + 1);
+  in.z_edges.assign(grid->z_edges, grid->z_edges + grid->nz + 1);
+  const size_t ncell = (size_t)grid->nx * grid->ny * grid->nz;
+  in.rho.assign(rho, rho + ncell);
+  in.c.assign(c, c + ncell);
   *out = h;
   return VSIE_OK;
 }

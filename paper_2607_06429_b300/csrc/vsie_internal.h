@@ -176,6 +176,16 @@ struct vsie_handle {
   } tune;
 
   std::vector<void*> allocs;  // every device allocation, freed by vsie_destroy
+
+  // the creation inputs (host copies), from which vsie_set_frequency rebuilds the operator
+  struct {
+    int kind = 0;  // 0: tetrahedra and triangles (vsie_create); 1: cuboid grid (vsie_create_cuboid)
+    std::vector<double> vert, rho, c, grad_alpha, tri_rho_in, tri_rho_out;
+    std::vector<int32_t> tet, tri;
+    std::vector<double> x_edges, y_edges, z_edges;
+    bool has_opt = false, has_grad_alpha = false;
+    vsie_options opt{};
+  } inputs;
 };
 
 namespace vsie {
