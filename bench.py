@@ -96,12 +96,22 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+_ORACLE = {}
+
+
+def oracle_of(w):
+    """The FP64 oracle's discretisation of workload w, built once per run."""
+    from oracle import vsie_oracle as O
+    if id(w) not in _ORACLE:
+        _ORACLE[id(w)] = O.Discretisation.from_workload(w)
+    return _ORACLE[id(w)]
+
+
 def oracle_rows_rate(w, rows_count, seed=0, time_budget=None):
     """FP64 CPU oracle applied to a seeded sample of rows; returns (interactions/s, sample
     description, seconds)."""
-    from oracle import vsie_oracle as O
     from paper_2607_06429_b300 import workloads as W
-    D = O.Discretisation.from_workload(w)
+    D = oracle_of(w)
     rng = np.random.default_rng(seed)
     rows = np.sort(rng.choice(w.n, size=rows_count, replace=False))
     x = W.random_vector(w.n, 1)
@@ -279,6 +289,76 @@ def multifreq_timing(torch, B, W, mesh="nested24_k10", nfreq=8, ndir=64, steps=2
     return out
 
 
+def cuboid_timing(torch, B, W, N=91, steps=2):
+    """The paper's cuboid discretisation (Sec. 3 sphere benchmark grid, N^3 cells on
+    [-3, 3]^3): FP32 apply interactions/s with the far-sum kernel's own time, and the cuboid
+    oracle timed beside it on a few seeded rows."""
+    from oracle import cuboid_oracle as CO
+    w = W.sphere_in_cube(N)
+    op = B.Operator.from_cuboid(w)
+    x = torch.from_numpy(W.random_vector(op.n, 4)).cuda()
+    y = torch.empty_like(x)
+    op.apply(x, y, precision=32)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        op.apply(x, y, precision=32)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    phase, _ = op.apply_timed(x, y, precision=32)
+    inter = float(op.n) * float(op.n_far_sources)
+    D = CO.CuboidDiscretisation.from_workload(w)
+    xh = W.random_vector(op.n, 4)
+    rows = np.random.default_rng(0).choice(op.n, size=4, replace=False)
+    t0 = time.perf_counter()
+    for r in rows:
+        D.apply_rows(xh, np.array([r]))
+    dt = time.perf_counter() - t0
+    return {"workload": f"sphere_cube{N}", "n": op.n, "n_far_sources": op.n_far_sources,
+            "ms_per_apply": ms, "interactions_per_s": inter / (ms * 1e-3),
+            "far_volume_ms": phase["far_volume"],
+            "far_volume_interactions_per_s": inter / (phase["far_volume"] * 1e-3),
+            "oracle_interactions_per_s": len(rows) * op.n_far_sources / dt,
+            "oracle_sample": f"{len(rows)} seeded rows (FP64 numpy, 1 thread)"}
+
+
+def field_timing(torch, op, W, m=65536):
+    """Scattered field at m exterior points (shell 1.05 < |x| < 3 around the unit-ball
+    scatterer) through vsie_scattered_field, FP32 far sums plus the near rows of the points
+    within the near radii; the oracle timed beside it on a few points."""
+    rng = np.random.default_rng(5)
+    d = rng.normal(size=(m, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    pts = d * rng.uniform(1.05, 3.0, m)[:, None]
+    x = torch.from_numpy(W.random_vector(op.n, 6)).cuda()
+    op.scattered_field(x, pts[:1024], precision=32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    op.scattered_field(x, pts, precision=32)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"points": m, "n_far_sources": op.n_far_sources, "seconds": dt,
+            "interactions_per_s": m * float(op.n_far_sources) / dt,
+            "note": "wall time of the blocking call: point upload, far sums, near-row build and apply"}
+
+
+def field_oracle_rate(w, npts=4):
+    from oracle import vsie_oracle as O
+    from paper_2607_06429_b300 import workloads as W
+    D = oracle_of(w)
+    rng = np.random.default_rng(5)
+    d = rng.normal(size=(npts, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    pts = d * rng.uniform(1.05, 3.0, npts)[:, None]
+    x = W.random_vector(w.n, 6)
+    t0 = time.perf_counter()
+    O.scattered_field(D, x, pts)
+    dt = time.perf_counter() - t0
+    return npts * w.n_far_sources() / dt
+
+
 def flush_l2(torch, buf):
     buf.add_(1.0)
 
@@ -295,6 +375,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the cuboid-grid apply and the exterior-field timings")
     ap.add_argument("--multifreq-mesh", default="nested24_k10", choices=["nested24_k10", "nested80_k10", "none"])
     args = ap.parse_args()
     if args.impl == "reference":
@@ -408,6 +490,13 @@ def main():
         multifreq = multifreq_timing(torch, B, W, mesh=args.multifreq_mesh,
                                      steps=1 if args.multifreq_mesh == "nested80_k10" else 2)
 
+    extras = None
+    if not args.no_extras and args.precision == 32:
+        extras = {"cuboid": cuboid_timing(torch, B, W), "field": field_timing(torch, op, W)}
+        if world == 1 and not args.no_cpu_baseline:
+            extras["field"]["oracle_interactions_per_s"] = field_oracle_rate(w)
+            extras["field"]["oracle_sample"] = "4 seeded exterior points (FP64 numpy, 1 thread)"
+
     solve = None
     if not args.no_solve:
         solve = solve_timing(torch, B, W)
@@ -437,6 +526,7 @@ def main():
         "solve": solve,
         "batched": batched,
         "multifreq": multifreq,
+        "extras": extras,
         "cpu_baseline": cpu,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
