@@ -359,6 +359,26 @@ def field_oracle_rate(w, npts=4):
     return npts * w.n_far_sources() / dt
 
 
+def reduce_step_time(t_ms, world, dist, device="cuda"):
+    """The step time of the whole job: the maximum over ranks of each rank's mean."""
+    if world <= 1:
+        return float(t_ms)
+    import torch
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_value(interactions_per_step, world, t_ms):
+    """Interactions of all ranks (one replica apply each) per second of the slowest rank."""
+    return float(interactions_per_step) * world / (t_ms * 1e-3)
+
+
+def rank_seed(rank):
+    """Each replica applies the operator to its own seeded right-hand side."""
+    return 1 + int(rank)
+
+
 def flush_l2(torch, buf):
     buf.add_(1.0)
 
@@ -407,7 +427,7 @@ def main():
     n, nsrc = op.n, op.n_far_sources
     inter = float(n) * float(nsrc)
 
-    x = torch.from_numpy(W.random_vector(n, 1 + rank)).cuda()
+    x = torch.from_numpy(W.random_vector(n, rank_seed(rank))).cuda()
     y = torch.empty_like(x)
     l2buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     stream = torch.cuda.current_stream()
@@ -438,10 +458,8 @@ def main():
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_ms = float(np.mean(step_ms))
+    t_ms = reduce_step_time(t_ms, world, dist)
     if world > 1:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
         dist.barrier()
     clocks = clk.summary()
 
@@ -461,7 +479,7 @@ def main():
             dist.destroy_process_group()
         return
 
-    value = inter * world / (t_ms * 1e-3)
+    value = whole_job_value(inter, world, t_ms)
     # roofline of the dominant kernel: FP32 far-field sum over volume sources (G class)
     pk, pk_kind = peaks()
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
