@@ -171,6 +171,19 @@ class CuboidDiscretisation:
         d = np.asarray(direction, dtype=np.float64)
         return np.exp(1j * self.k0 * (self.targets @ d))
 
+    def far_field(self, p, dirs) -> np.ndarray:
+        """Far-field pattern p_inf(xhat) with p_s(R xhat) ~ e^{ikR}/R p_inf(xhat): the limit
+        of the representation formula, where G(x, y) -> e^{ikR}/(4 pi R) e^{-ik xhat.y} and
+        dG/dn_y -> e^{ikR}/(4 pi R) (-ik xhat.n) e^{-ik xhat.y}:
+            p_inf = (1/4pi) [sum_cells e^{-ik xhat.y} s V p + ik sum_faces e^{-ik xhat.y} (xhat.n) omega A p].
+        p: (n,) or (n, nrhs); dirs: (m, 3) unit vectors."""
+        k = self.k0
+        X = np.asarray(dirs, dtype=np.float64)
+        Ec = np.exp(-1j * k * (X @ self.cell_cen.T)) * (self.sdens * self.cell_vol)[None, :]
+        Ef = np.exp(-1j * k * (X @ self.face_cen.T)) * (1j * k) * (X @ self.face_nrm.T) * \
+            (self.face_omega * self.face_area)[None, :]
+        return np.concatenate([Ec, Ef], axis=1) @ p / FOUR_PI
+
     def scattered_field(self, p, points) -> np.ndarray:
         """Representation formula (Eq. vsie with m = 1) at exterior points: -(rows) p."""
         return -(self.integral_rows(points) @ p)

@@ -468,6 +468,67 @@ def random_cuboids(shape, seed: int, k0: float = 3.0, jump_fraction: float = 0.5
                           z_edges=edges(nz), rho=rho, c=rng.uniform(0.7, 1.3, shape), k0=float(k0))
 
 
+def nested_cube_tets(h: float, side1: float = 7.0, side2: float = 5.0, rho0: float = 1000.0,
+                     rho2: float = 500.0, c0: float = 1482.3, speed_ratio: float = 1.2,
+                     lambda0: float = 3.0, near_factor: float = 2.0,
+                     tri_near_factor: float = 2.0) -> Workload:
+    """The nested-cubes density benchmark of Sec. 3 as a tetrahedral workload (a second,
+    independent discretisation of the problem that ``nested_cubes`` grids with cuboids): a
+    uniform grid of spacing h (h must divide both half-sides) on the outer cube, every
+    voxel Kuhn-split into six tetrahedra, tetrahedra whose centroid lies in the inner cube
+    in Omega_2; the inner cube's boundary squares, two outward triangles each, form
+    Gamma_2 (rho_in = rho2, rho_out = rho1 = rho0, so Gamma_1 carries no jump and no
+    elements).  Centroid far rule, four-point rule within near_factor voxel widths,
+    singularity-subtracted triangles within tri_near_factor edge lengths."""
+    a, b = 0.5 * side1, 0.5 * side2
+    n = int(round(2 * a / h))
+    m_in = int(round((a - b) / h))
+    assert abs(n * h - 2 * a) < 1e-9 and abs(m_in * h - (a - b)) < 1e-9, "h must divide both half-sides"
+    M = n + 1
+
+    def node(i, j, k):
+        return (i * M + j) * M + k
+
+    I, J, K = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    base = np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1)
+    unit = np.eye(3, dtype=np.int64)
+    tets = np.empty((base.shape[0], 6, 4), dtype=np.int64)
+    for t, perm in enumerate(_KUHN_PERMS):
+        p1 = base + unit[perm[0]]
+        p2 = p1 + unit[perm[1]]
+        for q, pq in enumerate((base, p1, p2, base + 1)):
+            tets[:, t, q] = node(pq[:, 0], pq[:, 1], pq[:, 2])
+    tet = tets.reshape(-1, 4)
+    g = np.arange(M)
+    GI, GJ, GK = np.meshgrid(g, g, g, indexing="ij")
+    vert = np.stack([GI.ravel(), GJ.ravel(), GK.ravel()], axis=1) * h - a
+    cen = vert[tet].mean(axis=1)
+    inner = np.max(np.abs(cen), axis=1) < b
+    rho = np.where(inner, rho2, rho0)
+    c = np.full(tet.shape[0], c0 / speed_ratio)
+    lo, hi = m_in, n - m_in  # inner cube in node indices
+    tris = []
+    for ax in range(3):
+        b1, b2 = (ax + 1) % 3, (ax + 2) % 3
+        for side, sgn in ((lo, -1.0), (hi, 1.0)):
+            for u in range(lo, hi):
+                for v in range(lo, hi):
+                    def p(du, dv):
+                        q = [0, 0, 0]
+                        q[ax], q[b1], q[b2] = side, u + du, v + dv
+                        return node(*q)
+                    a0, a1, a2, a3 = p(0, 0), p(1, 0), p(1, 1), p(0, 1)
+                    tris.extend([(a0, a1, a2), (a0, a2, a3)] if sgn > 0 else [(a0, a2, a1), (a0, a3, a2)])
+    tri = np.asarray(tris, dtype=np.int32)
+    near = h * math.sqrt(near_factor ** 2 + 1.0 / 32.0)
+    dom = np.where(inner, 2, 1).astype(np.int8)
+    return Workload(name=f"nested_cube_tets_h{h:g}", vert=vert.astype(np.float64), tet=tet.astype(np.int32),
+                    tri=tri, tri_iface=np.full(tri.shape[0], 2, dtype=np.int8), rho=rho, c=c, grad_alpha=None,
+                    tri_rho_in=np.full(tri.shape[0], rho2), tri_rho_out=np.full(tri.shape[0], rho0),
+                    k0=2.0 * math.pi / lambda0, rho0=rho0, c0=c0, tet_far_points=1, near_radius=near,
+                    tri_near_radius=tri_near_factor * h * math.sqrt(2.0), h=h, R1=a, tet_domain=dom)
+
+
 def cube_tets(n: int, half: float, rho1: float, c1: float, k0: float, rho0: float = 1.0, c0: float = 1.0,
               tet_far_points: int = 4, tri_near_factor: float = 2.0) -> Workload:
     """The cube [-half, half]^3 with constant material as a tetrahedral workload: the n^3

@@ -119,3 +119,45 @@ def test_sphere_benchmark_reproduction():
     order = math.log(e15[0] / e57[0]) / math.log(57.0 / 15.0)
     print(f"sphere benchmark: observed order {order:.2f} over N = 15..57")
     assert order > 1.5, order
+
+
+def test_cuboid_far_field_matches_oracle():
+    _torch()
+    w = W.nested_cubes(1.0)
+    op = _op(w)
+    D = CO.CuboidDiscretisation.from_workload(w)
+    x = W.random_vector(D.n, 13)
+    dirs = W.fibonacci_dirs(32)
+    got = op.far_field(_cuda(x), dirs).cpu().numpy()
+    assert rel(got, D.far_field(x, dirs)) <= TOL64
+
+
+def _far_pattern(op, d, dirs):
+    b = op.plane_wave_rhs(d)[0]
+    x, info = op.solve(b, mode=32, tol=1e-8)
+    assert info.rel_residual <= 1e-8
+    return op.far_field(x, dirs).cpu().numpy(), info.iterations
+
+
+def test_nested_cubes_two_discretisations_converge():
+    """Sec. 3 density benchmark (cubes of 7 and 5 mm, rho2 = rho0/2, c1 = c2 = c0/1.2,
+    lambda0 = 3 mm), where the paper compares with a BEM: here the cuboid discretisation
+    against the tetrahedral one (Kuhn tetrahedra, near rules, triangle interfaces) on
+    matched grids of spacing h.  Their far-field patterns (64 directions) approach each
+    other as h shrinks."""
+    from paper_2607_06429_b300 import binding as B
+    _torch()
+    d = np.array([1.0, 0.0, 0.0])
+    dirs = W.fibonacci_dirs(64)
+    diffs = {}
+    for h in (1.0, 0.5, 0.25):
+        fc, itc = _far_pattern(_op(W.nested_cubes(h)), d, dirs)
+        ft, itt = _far_pattern(B.Operator.from_workload(W.nested_cube_tets(h)), d, dirs)
+        diffs[h] = rel(fc, ft)
+        print(f"nested cubes h={h} mm: cuboid vs tetrahedral far field {diffs[h]:.4e} "
+              f"(iterations {itc} / {itt})")
+    fc2, _ = _far_pattern(_op(W.nested_cubes(0.125)), d, dirs)
+    fc1, _ = _far_pattern(_op(W.nested_cubes(0.25)), d, dirs)
+    print(f"nested cubes: cuboid h=0.25 vs h=0.125 far field {rel(fc1, fc2):.4e}")
+    assert diffs[0.25] < diffs[0.5] < diffs[1.0]
+    assert diffs[0.25] < 0.08

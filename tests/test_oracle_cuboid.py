@@ -106,3 +106,23 @@ def test_density_jump_cube_against_the_tetrahedral_oracle():
             pf = np.linalg.solve(C.assemble(), C.plane_wave(d))
             assert np.linalg.norm(C.scattered_field(pf, pts) - ref) / np.linalg.norm(ref) > 1.0
     assert errs[1] < 0.06 and errs[1] < 0.7 * errs[0], errs
+
+
+def test_far_field_is_the_large_radius_limit_of_the_exterior_field():
+    """R e^{-ik0 R} p_s(R xhat) -> p_inf(xhat) with an O(k0 |y|^2 / R) error, for a grid with
+    interface faces of every orientation (both sums of the far-field formula)."""
+    w = W.random_cuboids((4, 5, 3), seed=4, k0=2.5)
+    D = CO.CuboidDiscretisation.from_workload(w)
+    assert D.n_face > 20
+    p = W.random_vector(D.n, 3)
+    xhat = W.fibonacci_dirs(16)
+    R = 1.0e5
+    lim = D.scattered_field(p, R * xhat) * R * np.exp(-1j * w.k0 * R)
+    pinf = D.far_field(p, xhat)
+    assert np.linalg.norm(lim - pinf) / np.linalg.norm(pinf) < 1e-4
+    # each part on its own (cells only, faces only)
+    for sl in (slice(0, D.n_cell), slice(D.n_cell, D.n)):
+        q = np.zeros_like(p)
+        q[sl] = p[sl]
+        lim = D.scattered_field(q, R * xhat) * R * np.exp(-1j * w.k0 * R)
+        assert np.linalg.norm(lim - D.far_field(q, xhat)) / np.linalg.norm(D.far_field(q, xhat)) < 1e-4
