@@ -70,6 +70,9 @@ def test_cuboid_apply_matches_oracle(name):
     lam = W.random_vector(D.n, 9)
     xa = op.adjoint_apply(_cuda(lam), precision=64).cpu().numpy()
     assert rel(xa, A.conj().T @ lam) <= TOL64
+    # the multi-right-hand-side applies (tensor cores; FP64-accurate CUDA cores)
+    assert rel(op.apply_batched(Xd, precision=32).cpu().numpy(), ref) <= TOL32
+    assert rel(op.apply_batched(Xd, precision=64).cpu().numpy(), ref) <= TOL64
 
 
 def test_cuboid_face_count_and_exterior_field():
