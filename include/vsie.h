@@ -135,7 +135,8 @@ vsie_status vsie_create_cuboid(const vsie_cuboid_grid* grid, const double* rho, 
  * shapes chosen by vsie_autotune stay.  Blocking (synchronises the device first).
  * Every device buffer of the handle is reallocated, so CUDA-graph plans recorded on it
  * (vsie_graph_create_batched) must be recreated.  On an error other than VSIE_ERR_ARG the
- * handle holds no operator and may only be destroyed. */
+ * handle is left empty (n = 0, no device buffers): it may be destroyed, or rebuilt by
+ * another vsie_set_frequency. */
 vsie_status vsie_set_frequency(vsie_handle* h, double k0);
 
 void vsie_destroy(vsie_handle* h);

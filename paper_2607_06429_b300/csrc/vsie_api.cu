@@ -597,6 +597,23 @@ extern "C" vsie_status vsie_set_frequency(vsie_handle* h, double k0) {
     if (s == VSIE_OK) s = cuboid_geometry(&grid, in.rho.data(), in.c.data(), k0, h, g);
     if (s == VSIE_OK) s = finish_create(h, g);
   }
+  if (s != VSIE_OK) {
+    // leave an empty operator (n = 0, no buffers): every call on it is a no-op or an
+    // argument error, and a later vsie_set_frequency may rebuild it
+    const std::string msg = vsie_last_error();
+    cudaDeviceSynchronize();
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    auto keep = std::move(h->inputs);
+    *h = vsie_handle();
+    h->device = device;
+    h->num_sms = sms;
+    h->tune = tune;
+    h->rho0 = rho0;
+    h->c0 = c0;
+    h->inputs = std::move(keep);
+    set_error(msg);
+  }
   return s;
 }
 
