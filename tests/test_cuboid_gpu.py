@@ -164,3 +164,21 @@ def test_nested_cubes_two_discretisations_converge():
     print(f"nested cubes: cuboid h=0.25 vs h=0.125 far field {rel(fc1, fc2):.4e}")
     assert diffs[0.25] < diffs[0.5] < diffs[1.0]
     assert diffs[0.25] < 0.08
+
+
+def test_cuboid_gradient_channels_match_oracle():
+    """The gradient channels at the cuboid handle's source points (cell centres, then face
+    centres) against the oracle's channel sums over the cuboid collocation points."""
+    from oracle import vsie_oracle as O
+    _torch()
+    w = W.random_cuboids((4, 5, 3), seed=5)
+    op = _op(w)
+    D = CO.CuboidDiscretisation.from_workload(w)
+    pts, owner, _ = op.source_points()
+    assert np.array_equal(np.sort(owner), np.arange(D.n))
+    lam = W.random_vector(D.n, 17)
+    for prec, tol in ((64, TOL64), (32, TOL32)):
+        phi, psi = op.gradient_channels(_cuda(lam), precision=prec)
+        rphi, rpsi = O.gradient_channels(D, lam, pts)
+        assert rel(phi.cpu().numpy(), rphi) <= tol
+        assert rel(psi.cpu().numpy(), rpsi) <= tol

@@ -126,3 +126,50 @@ def test_far_field_is_the_large_radius_limit_of_the_exterior_field():
         q[sl] = p[sl]
         lim = D.scattered_field(q, R * xhat) * R * np.exp(-1j * w.k0 * R)
         assert np.linalg.norm(lim - D.far_field(q, xhat)) / np.linalg.norm(D.far_field(q, xhat)) < 1e-4
+
+
+def test_reciprocity_exact_for_the_lippmann_schwinger_grid():
+    """Reciprocity p_inf(xhat; d) = p_inf(-d; -xhat).  With density 1 the cuboid system is
+    A = m - G S with G symmetric (midpoint rule, centroid collocation, symmetric self terms)
+    and S = diag(s V) also the far-field weights, so the discrete far field
+    u(-xhat)^T S A^{-1} u(d) / 4pi is reciprocal exactly (push-through identity), to
+    rounding (density jumps add the unsymmetric face terms: discretisation level only)."""
+    w = W.random_cuboids((5, 4, 6), seed=7, k0=2.0)
+    w.rho[:] = 1.0
+    D = CO.CuboidDiscretisation.from_workload(w)
+    A = D.assemble()
+    dirs = W.fibonacci_dirs(6)
+
+    def pinf(xhat, d):
+        p = np.linalg.solve(A, D.plane_wave(d))
+        return D.far_field(p, xhat[None])[0]
+
+    for a in range(3):
+        for b in range(3, 6):
+            f1, f2 = pinf(dirs[a], dirs[b]), pinf(-dirs[b], -dirs[a])
+            assert abs(f1 - f2) <= 1e-11 * abs(f1), (a, b, f1, f2)
+    # the sign of the far-field phase matters: with the exponent's sign flipped the
+    # identity fails
+    xh, d = dirs[0], dirs[4]
+    p = np.linalg.solve(A, D.plane_wave(d))
+    wrong = np.sum(np.exp(+1j * w.k0 * (D.cell_cen @ xh)) * D.sdens * D.cell_vol * p[:D.n_cell]) / (4 * math.pi)
+    assert abs(wrong - pinf(-d, -xh)) > 1e-3 * abs(pinf(-d, -xh))
+
+
+def test_reciprocity_of_the_tetrahedral_penetrable_ball():
+    """The tetrahedral discretisation (collocation at centroids, four-point sources) is not
+    symmetric, so reciprocity holds at discretisation level: within 1% for the 12^3 ball
+    over 9 direction pairs (0.26% measured)."""
+    w = W.single_ball(12, 3, 2.0)
+    D = O.Discretisation.from_workload(w)
+    A = D.assemble()
+    dirs = W.fibonacci_dirs(6)
+    lu = __import__("scipy.linalg", fromlist=["lu_factor"])
+    fac = lu.lu_factor(A)
+    worst = 0.0
+    for a in range(3):
+        for b in range(3, 6):
+            f1 = D.far_field(lu.lu_solve(fac, D.plane_wave(dirs[b])), dirs[a][None])[0]
+            f2 = D.far_field(lu.lu_solve(fac, D.plane_wave(-dirs[a])), -dirs[b][None])[0]
+            worst = max(worst, abs(f1 - f2) / abs(f1))
+    assert worst < 0.01, worst
