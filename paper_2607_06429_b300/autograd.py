@@ -128,3 +128,64 @@ def far_field_misfit(rho, c, workload, dirs, target, direction=(1.0, 0.0, 0.0), 
     kw.update(solve_kw)
     return FarFieldMisfit.apply(rho, c, workload, np.asarray(dirs, dtype=np.float64), target,
                                 tuple(direction), kw)
+
+
+class CuboidFarFieldMisfit(torch.autograd.Function):
+    """L(c) on a cuboid grid (the paper's discretisation) for per-cell sound speed c; the
+    density (and with it the interface faces, which exist where the density jumps) stays
+    fixed.  c enters only the cell weights s_e = (rho0/rho_e)((omega/c_e)^2 - k0^2) (Eqs.
+    alpha, beta), every entry of a cell's column (self term included) and of its far-field
+    column being linear in s_e.  dL/ds_e comes from an operator of the same grid with s = 1
+    on every cell (c_u = omega / sqrt(k0^2 + rho_e/rho0), same density, so the same faces and
+    mass): dL/ds_e = Re[conj(F_u^H r - (A_u^H lam - m lam))_e p_e], which also covers cells
+    without contrast (s_e = 0)."""
+
+    @staticmethod
+    def forward(ctx, c, workload, dirs, target, direction, solve_kw):
+        w = workload
+        cw = _with_c(w, c.detach().numpy())
+        op = B.Operator.from_cuboid(cw)
+        b = op.plane_wave_rhs([direction])[0].contiguous()
+        p, _ = op.solve(b, **solve_kw)
+        u = op.far_field(p, dirs)
+        t = torch.as_tensor(np.asarray(target), dtype=torch.complex128, device=u.device)
+        r = (u - t).contiguous()
+        loss = 0.5 * float((r.abs() ** 2).sum().item())
+        ctx.op, ctx.p, ctx.r, ctx.dirs, ctx.solve_kw, ctx.w = op, p, r, dirs, solve_kw, w
+        ctx.save_for_backward(c)
+        return torch.tensor(loss, dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        (c,) = ctx.saved_tensors
+        op, p, r, w = ctx.op, ctx.p, ctx.r, ctx.w
+        nc = w.n_cells
+        g_adj = op.far_field_adjoint(r, ctx.dirs)
+        lam, _ = op.solve(g_adj.contiguous(), adjoint=True, **ctx.solve_kw)
+        prec = 64 if ctx.solve_kw.get("mode", 32) == 64 else 32
+        rho = np.asarray(w.rho, dtype=np.float64).reshape(-1)
+        omega = w.k0 * w.c0
+        unit = B.Operator.from_cuboid(_with_c(w, (omega / np.sqrt(w.k0 ** 2 + rho / w.rho0)).reshape(w.shape)))
+        m = torch.as_tensor(w.rho0 / rho, dtype=torch.float64, device=p.device)
+        wu = unit.adjoint_apply(lam, precision=prec)[:nc] - m * lam[:nc]
+        gu = unit.far_field_adjoint(r, ctx.dirs)[:nc]
+        dLds = (torch.conj(gu - wu) * p[:nc]).real
+        cc = c.to(device=p.device, dtype=torch.float64)
+        ds_dc = -2.0 * m * omega ** 2 / cc ** 3
+        unit.close()
+        op.close()
+        return (dLds * ds_dc).cpu() * grad_loss, None, None, None, None, None
+
+
+def _with_c(w, c):
+    import dataclasses
+    return dataclasses.replace(w, c=np.asarray(c, dtype=np.float64).reshape(w.shape))
+
+
+def cuboid_far_field_misfit(c, workload, dirs, target, direction=(1.0, 0.0, 0.0), **solve_kw):
+    """Differentiable L(c) on a cuboid grid; c: CPU float64 tensor of the n_cells sound
+    speeds in cell order; solve_kw go to Operator.solve (default: mixed mode, 1e-10)."""
+    kw = dict(mode=32, tol=1e-10, max_iters=2000, inner_tol=1e-4, max_refinements=30)
+    kw.update(solve_kw)
+    return CuboidFarFieldMisfit.apply(c, workload, np.asarray(dirs, dtype=np.float64), target,
+                                      tuple(direction), kw)

@@ -182,3 +182,46 @@ def test_cuboid_gradient_channels_match_oracle():
         rphi, rpsi = O.gradient_channels(D, lam, pts)
         assert rel(phi.cpu().numpy(), rphi) <= tol
         assert rel(psi.cpu().numpy(), rpsi) <= tol
+
+
+def _oracle_misfit(w, c, dirs, target, d):
+    import dataclasses
+    D = CO.CuboidDiscretisation.from_workload(dataclasses.replace(w, c=c.reshape(w.shape)))
+    p = np.linalg.solve(D.assemble(), D.plane_wave(d))
+    return 0.5 * float(np.sum(np.abs(D.far_field(p, dirs) - target) ** 2))
+
+
+def test_cuboid_sound_speed_gradient_against_oracle_finite_differences():
+    """dL/dc of the far-field misfit on a cuboid grid (autograd through the library, FP64
+    solves) against central finite differences of the oracle's misfit, on cells with and
+    without contrast (s_e = 0 outside the inclusion)."""
+    import torch
+    from paper_2607_06429_b300 import autograd as AG
+    _torch()
+    w = W.sphere_in_cube(7, R=2.2)
+    w.rho[2:5, 2:5, 2:5] = 1.3           # an interior density block: faces take part
+    c0 = w.c.reshape(-1).copy()
+    dirs = W.fibonacci_dirs(12)
+    d = np.array([0.0, 0.6, 0.8])
+    rng = np.random.default_rng(3)
+    ct = c0 * (1.0 + 0.05 * rng.standard_normal(c0.shape))
+    import dataclasses
+    Dt = CO.CuboidDiscretisation.from_workload(dataclasses.replace(w, c=ct.reshape(w.shape)))
+    target = Dt.far_field(np.linalg.solve(Dt.assemble(), Dt.plane_wave(d)), dirs)
+    c = torch.tensor(c0, dtype=torch.float64, requires_grad=True)
+    L = AG.cuboid_far_field_misfit(c, w, dirs, target, direction=d, mode=64, tol=1e-12)
+    L.backward()
+    grad = c.grad.numpy()
+    L_or = _oracle_misfit(w, c0, dirs, target, d)
+    assert abs(float(L) - L_or) <= 1e-9 * L_or
+    inside = np.nonzero(c0 < 1.0)[0]
+    outside = np.nonzero(c0 == 1.0)[0]
+    cells = np.concatenate([inside[:4], outside[:4]])
+    assert outside.size and inside.size
+    for e in cells:
+        h = 1e-6 * c0[e]
+        cp, cm = c0.copy(), c0.copy()
+        cp[e] += h
+        cm[e] -= h
+        fd = (_oracle_misfit(w, cp, dirs, target, d) - _oracle_misfit(w, cm, dirs, target, d)) / (2 * h)
+        assert abs(grad[e] - fd) <= 1e-5 * np.max(np.abs(grad)) + 1e-6 * abs(fd), (e, grad[e], fd)
