@@ -213,7 +213,7 @@ def test_cuboid_sound_speed_gradient_against_oracle_finite_differences():
     L.backward()
     grad = c.grad.numpy()
     L_or = _oracle_misfit(w, c0, dirs, target, d)
-    assert abs(float(L) - L_or) <= 1e-9 * L_or
+    assert abs(L.item() - L_or) <= 1e-9 * L_or
     inside = np.nonzero(c0 < 1.0)[0]
     outside = np.nonzero(c0 == 1.0)[0]
     cells = np.concatenate([inside[:4], outside[:4]])
