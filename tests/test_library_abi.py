@@ -61,3 +61,28 @@ def test_calls_reject_null_handle(lib):
     assert lib.vsie_solve(None, None, None, None, None, None) == 1
     assert lib.vsie_plane_wave_rhs(None, None, 0, None, None) == 1
     assert lib.vsie_far_field(None, None, 1, None, 1, None, None) == 1
+
+
+def test_cuboid_create_rejects_bad_grids(lib):
+    h = ctypes.c_void_p()
+    e = np.array([0.0, 1.0, 2.0])
+    rho = np.ones(8)
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    assert lib.vsie_create_cuboid(None, P(rho), P(rho), 1.0, 1.0, 1.0, ctypes.byref(h)) == 1
+    grid = B._CuboidGrid(2, 2, 2, P(e), P(e), None)
+    assert lib.vsie_create_cuboid(ctypes.byref(grid), P(rho), P(rho), 1.0, 1.0, 1.0, ctypes.byref(h)) == 1
+    grid = B._CuboidGrid(0, 2, 2, P(e), P(e), P(e))
+    assert lib.vsie_create_cuboid(ctypes.byref(grid), P(rho), P(rho), 1.0, 1.0, 1.0, ctypes.byref(h)) == 1
+    assert b"sizes" in lib.vsie_last_error()
+    grid = B._CuboidGrid(2, 2, 2, P(e), P(e), P(e))
+    assert lib.vsie_create_cuboid(ctypes.byref(grid), P(rho), P(rho), 1.0, 1.0, 0.0, ctypes.byref(h)) == 1
+    assert b"k0" in lib.vsie_last_error()
+    assert lib.vsie_create_cuboid(ctypes.byref(grid), P(rho), P(rho), 1.0, 1.0, 1.0, None) == 1
+    assert not h.value
+
+
+def test_field_and_frequency_calls_reject_null_handle(lib):
+    pts = np.zeros(3)
+    assert lib.vsie_scattered_field(None, None, 1, pts.ctypes.data_as(ctypes.c_void_p), 1, 64, None, None) == 1
+    assert lib.vsie_set_frequency(None, 2.0) == 1
+    assert b"vsie_set_frequency" in lib.vsie_last_error()
