@@ -107,9 +107,21 @@ def oracle_of(w):
     return _ORACLE[id(w)]
 
 
+def one_thread():
+    """Limit the BLAS/OpenMP pools to one thread while the oracle is timed, so that the
+    reported core count (1) is the one used."""
+    from threadpoolctl import threadpool_limits
+    return threadpool_limits(limits=1)
+
+
 def oracle_rows_rate(w, rows_count, seed=0, time_budget=None):
     """FP64 CPU oracle applied to a seeded sample of rows; returns (interactions/s, sample
     description, seconds)."""
+    with one_thread():
+        return _oracle_rows_rate(w, rows_count, seed, time_budget)
+
+
+def _oracle_rows_rate(w, rows_count, seed=0, time_budget=None):
     from paper_2607_06429_b300 import workloads as W
     D = oracle_of(w)
     rng = np.random.default_rng(seed)
@@ -312,10 +324,11 @@ def cuboid_timing(torch, B, W, N=91, steps=2):
     D = CO.CuboidDiscretisation.from_workload(w)
     xh = W.random_vector(op.n, 4)
     rows = np.random.default_rng(0).choice(op.n, size=4, replace=False)
-    t0 = time.perf_counter()
-    for r in rows:
-        D.apply_rows(xh, np.array([r]))
-    dt = time.perf_counter() - t0
+    with one_thread():
+        t0 = time.perf_counter()
+        for r in rows:
+            D.apply_rows(xh, np.array([r]))
+        dt = time.perf_counter() - t0
     return {"workload": f"sphere_cube{N}", "n": op.n, "n_far_sources": op.n_far_sources,
             "ms_per_apply": ms, "interactions_per_s": inter / (ms * 1e-3),
             "far_volume_ms": phase["far_volume"],
@@ -353,9 +366,10 @@ def field_oracle_rate(w, npts=4):
     d /= np.linalg.norm(d, axis=1)[:, None]
     pts = d * rng.uniform(1.05, 3.0, npts)[:, None]
     x = W.random_vector(w.n, 6)
-    t0 = time.perf_counter()
-    O.scattered_field(D, x, pts)
-    dt = time.perf_counter() - t0
+    with one_thread():
+        t0 = time.perf_counter()
+        O.scattered_field(D, x, pts)
+        dt = time.perf_counter() - t0
     return npts * w.n_far_sources() / dt
 
 
