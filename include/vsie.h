@@ -271,6 +271,10 @@ typedef struct {
   double inner_tol;         /* mode 32: relative tolerance of each inner solve         */
   int32_t max_refinements;  /* mode 32: outer refinement steps                         */
   int32_t adjoint;          /* nonzero: solve A^H x = b (adjoint state of a gradient)   */
+  int32_t initial_guess;    /* vsie_solve: nonzero = x holds a starting iterate on entry
+                               (resume from a saved x_k: the first residual b - A x is
+                               formed with the FP64-accuracy apply); 0 = start from x = 0.
+                               Must be 0 for vsie_solve_batched                        */
 } vsie_solve_opts;
 
 typedef struct {

@@ -67,7 +67,7 @@ class _SolveOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("max_iters", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("inner_tol", ctypes.c_double), ("max_refinements", ctypes.c_int32),
-                ("adjoint", ctypes.c_int32)]
+                ("adjoint", ctypes.c_int32), ("initial_guess", ctypes.c_int32)]
 
 
 class _Tuning(ctypes.Structure):
@@ -422,14 +422,20 @@ class Operator:
                              i.fp32_applies) for i in infos]
 
     def solve(self, b, mode=32, tol=1e-8, max_iters=1000, restart=0, inner_tol=1e-4,
-              max_refinements=20, stream=None, raise_on_fail=True, adjoint=False):
-        """x with A x = b, or A^H x = b if adjoint (vsie_solve); returns (x, SolveInfo)."""
+              max_refinements=20, stream=None, raise_on_fail=True, adjoint=False, x0=None):
+        """x with A x = b, or A^H x = b if adjoint (vsie_solve); returns (x, SolveInfo).
+        x0: a starting iterate (resume from a saved solution), copied, not modified."""
         import torch
         if b.dim() != 1:
             raise ValueError("vsie_solve takes one right-hand side")
-        x = torch.empty_like(b)
+        if x0 is not None:
+            if tuple(x0.shape) != tuple(b.shape):
+                raise ValueError("x0 must have the shape of b")
+            x = x0.to(device=b.device, dtype=torch.complex128).clone()
+        else:
+            x = torch.empty_like(b)
         o = _SolveOpts(int(mode), float(tol), int(max_iters), int(restart), float(inner_tol),
-                       int(max_refinements), 1 if adjoint else 0)
+                       int(max_refinements), 1 if adjoint else 0, 0 if x0 is None else 1)
         info = _SolveInfo()
         st = _lib.vsie_solve(self._h, _dev(b, "b"), _dev(x, "x"), ctypes.byref(o),
                              ctypes.byref(info), _stream(stream))

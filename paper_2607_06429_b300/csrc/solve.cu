@@ -308,21 +308,40 @@ extern "C" vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
     cleanup();
     return s;
   }
+  // the apply that forms true residuals: the double-float sums (precision 48) in the
+  // refinement of a forward solve, plain FP64 otherwise
+  const int res_prec = (opts->mode == 32 && !adjoint) ? 48 : 64;
   auto run = [&]() -> vsie_status {
-    VSIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * n, st));
+    if (!opts->initial_guess) VSIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * n, st));
     double bnorm;
     VSIE_TRY(norm2(b, n, S, &bnorm, st));
     if (!std::isfinite(bnorm)) {
       set_error("vsie_solve: non-finite right-hand side");
       return VSIE_ERR_NAN;
     }
-    if (bnorm == 0.0) {
+    if (bnorm == 0.0) {  // the solution is 0 whatever the starting iterate
+      VSIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * n, st));
       inf.rel_residual = 0.0;
       return VSIE_OK;
     }
     const double target = opts->tol * bnorm;
-    VSIE_CUDA(cudaMemcpyAsync(S.r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
     double rnorm = bnorm;
+    if (opts->initial_guess) {
+      // resume: r = b - A x from the given iterate
+      VSIE_TRY(op_apply(h, adjoint, x, S.t, res_prec, st));
+      inf.fp64_applies += 1;
+      sub_kernel<<<nb256(n), 256, 0, st>>>(b, S.t, S.r, n);
+      VSIE_CUDA(cudaGetLastError());
+      VSIE_TRY(norm2(S.r, n, S, &rnorm, st));
+      if (!std::isfinite(rnorm)) {
+        set_error("vsie_solve: non-finite residual of the initial guess");
+        return VSIE_ERR_NAN;
+      }
+      inf.rel_residual = rnorm / bnorm;
+      if (rnorm <= target) return VSIE_OK;
+    } else {
+      VSIE_CUDA(cudaMemcpyAsync(S.r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+    }
     const int inner_prec = opts->mode;
     const int max_outer = opts->mode == 32 ? std::max(1, opts->max_refinements) : 1 << 30;
     int outer = 0;
@@ -339,9 +358,8 @@ extern "C" vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
         inf.fp32_applies += applies;
       else
         inf.fp64_applies += applies;
-      // true residual with an FP64-accuracy apply: the double-float sums (precision 48) in
-      // the refinement of a forward solve, plain FP64 otherwise
-      VSIE_TRY(op_apply(h, adjoint, x, S.t, (opts->mode == 32 && !adjoint) ? 48 : 64, st));
+      // true residual with the FP64-accuracy apply
+      VSIE_TRY(op_apply(h, adjoint, x, S.t, res_prec, st));
       inf.fp64_applies += 1;
       sub_kernel<<<nb256(n), 256, 0, st>>>(b, S.t, S.r, n);
       VSIE_CUDA(cudaGetLastError());

@@ -406,6 +406,10 @@ extern "C" vsie_status vsie_solve_batched(vsie_handle* h, const void* d_b, void*
     set_error("vsie_solve_batched: invalid options");
     return VSIE_ERR_ARG;
   }
+  if (opts->initial_guess) {
+    set_error("vsie_solve_batched: initial_guess is not supported (use vsie_solve)");
+    return VSIE_ERR_ARG;
+  }
   if (opts->adjoint) {
     set_error("vsie_solve_batched: adjoint solves are not batched; use vsie_solve");
     return VSIE_ERR_ARG;
