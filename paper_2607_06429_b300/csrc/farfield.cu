@@ -139,6 +139,7 @@ using namespace vsie;
 extern "C" vsie_status vsie_plane_wave_rhs(vsie_handle* h, const double* h_dirs, int32_t ndir, void* d_b,
                                            void* stream) {
   clear_error();
+  TraceRange trace("vsie_plane_wave_rhs");
   if (!h || !h_dirs || !d_b || ndir < 1 || ndir > 65535) {
     set_error("vsie_plane_wave_rhs: invalid argument");
     return VSIE_ERR_ARG;
@@ -158,6 +159,7 @@ extern "C" vsie_status vsie_plane_wave_rhs(vsie_handle* h, const double* h_dirs,
 extern "C" vsie_status vsie_far_field(vsie_handle* h, const void* d_p, int32_t nrhs, const double* h_dirs,
                                       int32_t ndir, void* d_out, void* stream) {
   clear_error();
+  TraceRange trace("vsie_far_field");
   if (!h || !d_p || !h_dirs || !d_out || ndir < 1 || nrhs < 1 || nrhs > 65535) {
     set_error("vsie_far_field: invalid argument");
     return VSIE_ERR_ARG;
@@ -181,6 +183,7 @@ extern "C" vsie_status vsie_far_field(vsie_handle* h, const void* d_p, int32_t n
 extern "C" vsie_status vsie_far_field_adjoint(vsie_handle* h, const void* d_r, int32_t nrhs, const double* h_dirs,
                                               int32_t ndir, void* d_x, void* stream) {
   clear_error();
+  TraceRange trace("vsie_far_field_adjoint");
   if (!h || !d_r || !h_dirs || !d_x || ndir < 1 || nrhs < 1) {
     set_error("vsie_far_field_adjoint: invalid argument");
     return VSIE_ERR_ARG;

@@ -17,6 +17,7 @@ using namespace vsie;
 extern "C" vsie_status vsie_scattered_field(vsie_handle* h, const void* d_p, int32_t nrhs, const double* h_points,
                                             int64_t m, int32_t precision, void* d_out, void* stream) {
   clear_error();
+  TraceRange trace("vsie_scattered_field");
   if (!h || !d_p || !h_points || !d_out || m < 1 || nrhs < 1 ||
       (precision != 32 && precision != 48 && precision != 64)) {
     set_error("vsie_scattered_field: invalid argument (handle, buffers, m >= 1, nrhs >= 1, precision 32/48/64)");

@@ -32,6 +32,7 @@ extern "C" void vsie_graph_destroy(vsie_graph* g) {
 extern "C" vsie_status vsie_graph_create_batched(vsie_handle* const* hs, int32_t nop, const void* const* d_x,
                                                  void* const* d_y, int32_t nrhs, vsie_graph** out) {
   clear_error();
+  TraceRange trace("vsie_graph_create_batched");
   if (!out) {
     set_error("vsie_graph_create_batched: null output");
     return VSIE_ERR_ARG;
@@ -69,6 +70,7 @@ extern "C" vsie_status vsie_graph_create_batched(vsie_handle* const* hs, int32_t
 
 extern "C" vsie_status vsie_graph_launch(vsie_graph* g, void* stream) {
   clear_error();
+  TraceRange trace("vsie_graph_launch");
   if (!g || !g->exec) {
     set_error("vsie_graph_launch: null plan");
     return VSIE_ERR_ARG;

@@ -265,6 +265,7 @@ using namespace vsie;
 extern "C" vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
                                   const vsie_solve_opts* opts, vsie_solve_info* info, void* stream) {
   clear_error();
+  TraceRange trace("vsie_solve");
   if (!h || !d_b || !d_x || !opts) {
     set_error("vsie_solve: null argument");
     return VSIE_ERR_ARG;

@@ -397,6 +397,7 @@ using namespace vsie;
 extern "C" vsie_status vsie_solve_batched(vsie_handle* h, const void* d_b, void* d_x, int32_t nrhs,
                                           const vsie_solve_opts* opts, vsie_solve_info* infos, void* stream) {
   clear_error();
+  TraceRange trace("vsie_solve_batched");
   if (!h || !d_b || !d_x || !opts || nrhs < 1 || nrhs > 65535) {
     set_error("vsie_solve_batched: null argument or nrhs outside [1, 65535]");
     return VSIE_ERR_ARG;

@@ -498,6 +498,7 @@ static vsie_status create_impl(const vsie_mesh* mesh, const vsie_material* mat, 
 extern "C" vsie_status vsie_create(const vsie_mesh* mesh, const vsie_material* mat, double k0,
                                    const vsie_options* opt, vsie_handle** out) {
   clear_error();
+  TraceRange trace("vsie_create");
   if (!out) {
     set_error("vsie_create: null output pointer");
     return VSIE_ERR_ARG;
@@ -557,6 +558,7 @@ extern "C" vsie_status vsie_create(const vsie_mesh* mesh, const vsie_material* m
 // a new k0 from the saved creation inputs; the material, geometry and autotuned shapes stay.
 extern "C" vsie_status vsie_set_frequency(vsie_handle* h, double k0) {
   clear_error();
+  TraceRange trace("vsie_set_frequency");
   if (!h || !(k0 > 0.0) || !std::isfinite(k0)) {
     set_error("vsie_set_frequency: null handle or k0 not positive and finite");
     return VSIE_ERR_ARG;
@@ -620,6 +622,7 @@ extern "C" vsie_status vsie_set_frequency(vsie_handle* h, double k0) {
 extern "C" vsie_status vsie_create_cuboid(const vsie_cuboid_grid* grid, const double* rho, const double* c,
                                           double rho0, double c0, double k0, vsie_handle** out) {
   clear_error();
+  TraceRange trace("vsie_create_cuboid");
   if (!out) {
     set_error("vsie_create_cuboid: null output pointer");
     return VSIE_ERR_ARG;
@@ -705,6 +708,7 @@ static vsie_status check_apply_args(vsie_handle* h, const void* x, const void* y
 extern "C" vsie_status vsie_apply(vsie_handle* h, const void* d_x, void* d_y, int32_t nrhs,
                                   int32_t precision, void* stream) {
   clear_error();
+  TraceRange trace("vsie_apply");
   VSIE_TRY(check_apply_args(h, d_x, d_y, nrhs, precision, "vsie_apply"));
   cudaStream_t st = (cudaStream_t)stream;
   const double2* x = (const double2*)d_x;
@@ -718,6 +722,7 @@ extern "C" vsie_status vsie_apply(vsie_handle* h, const void* d_x, void* d_y, in
 extern "C" vsie_status vsie_apply_host(vsie_handle* h, const double* h_x, double* h_y,
                                        int32_t nrhs, int32_t precision, void* stream) {
   clear_error();
+  TraceRange trace("vsie_apply_host");
   VSIE_TRY(check_apply_args(h, h_x, h_y, nrhs, precision, "vsie_apply_host"));
   cudaStream_t st = (cudaStream_t)stream;
   if (h->host_cols < nrhs) {
@@ -737,6 +742,7 @@ extern "C" vsie_status vsie_apply_host(vsie_handle* h, const double* h_x, double
 extern "C" vsie_status vsie_adjoint_apply(vsie_handle* h, const void* d_y, void* d_x,
                                           int32_t nrhs, int32_t precision, void* stream) {
   clear_error();
+  TraceRange trace("vsie_adjoint_apply");
   VSIE_TRY(check_apply_args(h, d_y, d_x, nrhs, precision, "vsie_adjoint_apply"));
   if (precision == 48) {
     set_error("vsie_adjoint_apply: precision must be 32 or 64");
@@ -797,6 +803,7 @@ extern "C" vsie_status vsie_apply_timed(vsie_handle* h, const void* d_x, void* d
 extern "C" vsie_status vsie_apply_batched(vsie_handle* h, const void* d_x, void* d_y, int32_t nrhs,
                                           int32_t precision, void* stream) {
   clear_error();
+  TraceRange trace("vsie_apply_batched");
   VSIE_TRY(check_apply_args(h, d_x, d_y, nrhs, precision, "vsie_apply_batched"));
   if (precision == 48) {
     set_error("vsie_apply_batched: precision must be 32 or 64");
@@ -866,6 +873,7 @@ vsie_status apply_batched_multi_launch(vsie_handle* const* hs, int nop, const do
 extern "C" vsie_status vsie_gradient_channels(vsie_handle* h, const void* d_lam, int32_t precision, void* d_phi,
                                               void* d_psi, void* stream) {
   clear_error();
+  TraceRange trace("vsie_gradient_channels");
   if (!h || !d_lam || !d_phi || !d_psi || (precision != 32 && precision != 64)) {
     set_error("vsie_gradient_channels: null argument or precision not 32 / 64");
     return VSIE_ERR_ARG;
@@ -922,6 +930,7 @@ __global__ void random_fill_kernel(double2* __restrict__ v, int64_t m, uint64_t 
 
 extern "C" vsie_status vsie_autotune(vsie_handle* h, int32_t flags, vsie_tuning* report, void* stream) {
   clear_error();
+  TraceRange trace("vsie_autotune");
   if (!h || (flags & ~3) || !flags) {
     set_error("vsie_autotune: null handle or flags outside {1, 2, 3}");
     return VSIE_ERR_ARG;
@@ -971,6 +980,7 @@ extern "C" vsie_status vsie_autotune(vsie_handle* h, int32_t flags, vsie_tuning*
 extern "C" vsie_status vsie_apply_batched_multi(vsie_handle* const* hs, int32_t nop, const void* const* d_x,
                                                 void* const* d_y, int32_t nrhs, void* stream) {
   clear_error();
+  TraceRange trace("vsie_apply_batched_multi");
   VSIE_TRY(check_multi_args(hs, nop, d_x, d_y, nrhs, "vsie_apply_batched_multi"));
   cudaStream_t st = (cudaStream_t)stream;
   VSIE_TRY(apply_batched_multi_launch(hs, nop, reinterpret_cast<const double2* const*>(d_x),

@@ -7,12 +7,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "vsie.h"
 
 namespace vsie {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kFourPi = 4.0 * kPi;
+
+// A named range on the host timeline for profilers (NVTX): it brackets one call of an
+// entry point or one phase of it; without an attached tool the push and pop do nothing.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Thread-local error text behind vsie_last_error().
 void set_error(const std::string& msg);
