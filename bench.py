@@ -357,6 +357,38 @@ def field_timing(torch, op, W, m=65536):
             "note": "wall time of the blocking call: point upload, far sums, near-row build and apply"}
 
 
+def adjoint_timing(torch, op, W, steps=2):
+    """The adjoint apply A^H lam (FP32 far sums with swapped roles, gather, correction
+    transpose), the gradient channels of lam, and the plane-wave right-hand side and
+    far-field pattern on 128 directions, on the benchmark operator; event-timed."""
+    lam = torch.from_numpy(W.random_vector(op.n, 8)).cuda()
+    x = torch.empty_like(lam)
+    dirs = W.fibonacci_dirs(128)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    inter = float(op.n) * float(op.n_far_sources)
+    adj_ms = timed(lambda: op.adjoint_apply(lam, x, precision=32), steps)
+    ch_ms = timed(lambda: op.gradient_channels(lam, precision=32), steps)
+    ff_ms = timed(lambda: op.far_field(lam, dirs), steps)
+    pw_ms = timed(lambda: op.plane_wave_rhs(dirs[:8]), steps)
+    return {"adjoint_ms": adj_ms, "adjoint_interactions_per_s": inter / (adj_ms * 1e-3),
+            "gradient_channels_ms": ch_ms,
+            "gradient_channels_interactions_per_s": inter / (ch_ms * 1e-3),
+            "far_field_128_dirs_ms": ff_ms,
+            "far_field_terms_per_s": 128.0 * op.n_far_sources / (ff_ms * 1e-3),
+            "plane_wave_8_dirs_ms": pw_ms}
+
+
 def field_oracle_rate(w, npts=4):
     from oracle import vsie_oracle as O
     from paper_2607_06429_b300 import workloads as W
@@ -524,7 +556,8 @@ def main():
 
     extras = None
     if not args.no_extras and args.precision == 32:
-        extras = {"cuboid": cuboid_timing(torch, B, W), "field": field_timing(torch, op, W)}
+        extras = {"cuboid": cuboid_timing(torch, B, W), "field": field_timing(torch, op, W),
+                  "adjoint": adjoint_timing(torch, op, W)}
         if world == 1 and not args.no_cpu_baseline:
             extras["field"]["oracle_interactions_per_s"] = field_oracle_rate(w)
             extras["field"]["oracle_sample"] = "4 seeded exterior points (FP64 numpy, 1 thread)"
