@@ -22,7 +22,12 @@ import sys
 import tempfile
 import time
 
-import numpy as np
+# the oracle timings report one core: hold numpy's BLAS/OpenMP pools to one thread (set
+# before numpy loads them; nothing on the GPU path uses them)
+for _var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_var, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -109,8 +114,13 @@ def oracle_of(w):
 
 def one_thread():
     """Limit the BLAS/OpenMP pools to one thread while the oracle is timed, so that the
-    reported core count (1) is the one used."""
-    from threadpoolctl import threadpool_limits
+    reported core count (1) is the one used (threadpoolctl where it is installed; the
+    environment variables set at start-up otherwise)."""
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:
+        import contextlib
+        return contextlib.nullcontext()
     return threadpool_limits(limits=1)
 
 
