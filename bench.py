@@ -388,7 +388,7 @@ def adjoint_timing(torch, op, W, steps=2):
 
     inter = float(op.n) * float(op.n_far_sources)
     adj_ms = timed(lambda: op.adjoint_apply(lam, x, precision=32), steps)
-    ch_ms = timed(lambda: op.gradient_channels(lam, precision=32), steps)
+    ch_ms = timed(lambda: op.gradient_channels(lam, precision=32), 1)  # ~20 s per call at nested80
     ff_ms = timed(lambda: op.far_field(lam, dirs), steps)
     pw_ms = timed(lambda: op.plane_wave_rhs(dirs[:8]), steps)
     return {"adjoint_ms": adj_ms, "adjoint_interactions_per_s": inter / (adj_ms * 1e-3),
