@@ -127,6 +127,19 @@ typedef struct {
 vsie_status vsie_create_cuboid(const vsie_cuboid_grid* grid, const double* rho, const double* c,
                                double rho0, double c0, double k0, vsie_handle** out);
 
+/* The interface unknowns of a cuboid grid, host-only (no device work): the faces across
+ * which the density jumps, in the unknown order of vsie_create_cuboid (they follow the
+ * nx*ny*nz cells).  n_faces receives their number; the arrays, each NULL or of at least
+ * `capacity` entries (centres 3 per face), receive per face its centre, normal axis
+ * (0, 1, 2: the normal is that +axis), area, omega = alpha_in - alpha_out = rho0/rho_in -
+ * rho0/rho_out (Eq. vsie) and mass function (rho0/rho_in + rho0/rho_out)/2 (Eq.
+ * mass_function).  Call with capacity 0 and NULL arrays to count.  VSIE_ERR_ARG on a
+ * null argument or a capacity below the count with arrays given; VSIE_ERR_MESH on edges
+ * that do not increase or a non-positive density. */
+vsie_status vsie_cuboid_faces(const vsie_cuboid_grid* grid, const double* rho, double rho0,
+                              int64_t capacity, int64_t* n_faces, double* centres, int32_t* axis,
+                              double* area, double* omega, double* mass);
+
 /* Change the frequency of an existing operator: k0 = omega/c0 enters the volume weights
  * through beta (Eq. beta) and every pair through G = exp(i k0 r)/(4 pi r) (Eq.
  * greens_function), so the weights, source records and the near/self correction are

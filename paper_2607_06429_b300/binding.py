@@ -30,7 +30,7 @@ EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_appl
            "vsie_graph_create_batched", "vsie_graph_launch", "vsie_graph_nodes", "vsie_graph_destroy",
            "vsie_autotune", "vsie_gradient_channels", "vsie_source_points",
            "vsie_lsq_grad_alpha", "vsie_lsq_grad_alpha_adjoint", "vsie_scattered_field",
-           "vsie_create_cuboid", "vsie_set_frequency", "vsie_last_error")
+           "vsie_create_cuboid", "vsie_set_frequency", "vsie_cuboid_faces", "vsie_last_error")
 
 
 class VsieError(RuntimeError):
@@ -123,6 +123,7 @@ def load_library(path: str = LIB_PATH):
     lib.vsie_scattered_field.argtypes = [P, P, I32, P, I64, I32, P, P]
     lib.vsie_create_cuboid.argtypes = [ctypes.POINTER(_CuboidGrid), P, P, D, D, D, ctypes.POINTER(P)]
     lib.vsie_set_frequency.argtypes = [P, D]
+    lib.vsie_cuboid_faces.argtypes = [ctypes.POINTER(_CuboidGrid), P, D, I64, ctypes.POINTER(I64), P, P, P, P, P]
     lib.vsie_solve.argtypes = [P, P, P, ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), P]
     lib.vsie_solve_batched.argtypes = [P, P, P, ctypes.c_int32, ctypes.POINTER(_SolveOpts),
                                        ctypes.POINTER(_SolveInfo), P]
@@ -506,6 +507,25 @@ def _tet_mesh(vert, tet):
     v = _f64(vert).reshape(-1)
     t = _i32(tet).reshape(-1)
     return _Mesh(v.shape[0] // 3, _ptr(v), t.shape[0] // 4, _ptr(t), 0, None), (v, t)
+
+
+def cuboid_faces(w):
+    """The interface unknowns of a CuboidWorkload in their unknown order (vsie_cuboid_faces):
+    dict of centres (m, 3), axis (m,), area, omega and mass (m,)."""
+    lib = load_library()
+    ex, ey, ez = (_f64(e) for e in (w.x_edges, w.y_edges, w.z_edges))
+    rho = _f64(np.asarray(w.rho).reshape(-1))
+    grid = _CuboidGrid(ex.shape[0] - 1, ey.shape[0] - 1, ez.shape[0] - 1, _ptr(ex), _ptr(ey), _ptr(ez))
+    cnt = ctypes.c_int64()
+    _check(lib.vsie_cuboid_faces(ctypes.byref(grid), _ptr(rho), float(w.rho0), 0, ctypes.byref(cnt),
+                                 None, None, None, None, None))
+    m = cnt.value
+    out = dict(centres=np.empty((m, 3)), axis=np.empty(m, dtype=np.int32), area=np.empty(m),
+               omega=np.empty(m), mass=np.empty(m))
+    _check(lib.vsie_cuboid_faces(ctypes.byref(grid), _ptr(rho), float(w.rho0), m, ctypes.byref(cnt),
+                                 _ptr(out["centres"]), _ptr(out["axis"]), _ptr(out["area"]),
+                                 _ptr(out["omega"]), _ptr(out["mass"])))
+    return out
 
 
 def lsq_grad_alpha(vert, tet, tet_domain, alpha):

@@ -258,6 +258,37 @@ static vsie_status tet_geometry(const vsie_mesh* mesh, const vsie_material* mat,
   return VSIE_OK;
 }
 
+// The faces of a cuboid grid across which the density jumps, in the unknown order: axis
+// by axis (x, y, z), each in lattice order (face index along the axis first); outside the
+// grid the exterior density rho0.  f(centre, axis, area, rho_in, rho_out) per face, "in"
+// the cell below the face along its axis.
+template <class F>
+static void for_each_jump_face(const vsie_cuboid_grid* grid, const double* rho, double rho0, F&& f) {
+  const int64_t N[3] = {grid->nx, grid->ny, grid->nz};
+  const double* E[3] = {grid->x_edges, grid->y_edges, grid->z_edges};
+  auto cell = [&](const int64_t* I) { return (I[0] * N[1] + I[1]) * N[2] + I[2]; };
+  for (int ax = 0; ax < 3; ++ax) {
+    const int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;  // the face's in-plane axes
+    for (int64_t u = 0; u < (ax == 0 ? N[0] + 1 : N[0]); ++u)
+      for (int64_t v = 0; v < (ax == 1 ? N[1] + 1 : N[1]); ++v)
+        for (int64_t w = 0; w < (ax == 2 ? N[2] + 1 : N[2]); ++w) {
+          const int64_t I[3] = {u, v, w};
+          const int64_t a = I[ax];
+          int64_t below[3] = {u, v, w};
+          below[ax] = a - 1;
+          const double rin = a > 0 ? rho[cell(below)] : rho0;
+          const double rout = a < N[ax] ? rho[cell(I)] : rho0;
+          if (rin == rout) continue;
+          double ctr[3];
+          ctr[ax] = E[ax][a];
+          ctr[b1] = 0.5 * (E[b1][I[b1]] + E[b1][I[b1] + 1]);
+          ctr[b2] = 0.5 * (E[b2][I[b2]] + E[b2][I[b2] + 1]);
+          const double area = (E[b1][I[b1] + 1] - E[b1][I[b1]]) * (E[b2][I[b2] + 1] - E[b2][I[b2]]);
+          f(ctr, ax, area, rin, rout);
+        }
+  }
+}
+
 // Cuboid grid (Sec. 2.3.4, computational domain and discrete representation): P0 unknowns
 // on the cells and on the rectangular cell faces across which the density jumps; every
 // integral by the midpoint rule (one far-field point per element), the single-layer self
@@ -306,36 +337,19 @@ static vsie_status cuboid_geometry(const vsie_cuboid_grid* grid, const double* r
         g.mass[e] = rho0 / rho[e];                                                         // Eq. (mass_function)
       }
   // jump faces, axis by axis
-  for (int ax = 0; ax < 3; ++ax) {
-    const int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;  // the face's in-plane axes
-    const int lo1 = std::min(b1, b2), lo2 = std::max(b1, b2);
-    for (int64_t u = 0; u < (ax == 0 ? N[0] + 1 : N[0]); ++u)
-      for (int64_t v = 0; v < (ax == 1 ? N[1] + 1 : N[1]); ++v)
-        for (int64_t w = 0; w < (ax == 2 ? N[2] + 1 : N[2]); ++w) {
-          int64_t I[3] = {u, v, w};
-          const int64_t a = I[ax];
-          int64_t below[3] = {I[0], I[1], I[2]}, above[3] = {I[0], I[1], I[2]};
-          below[ax] = a - 1;
-          const double rin = a > 0 ? rho[cell(below[0], below[1], below[2])] : rho0;
-          const double rout = a < N[ax] ? rho[cell(above[0], above[1], above[2])] : rho0;
-          if (rin == rout) continue;
-          double ctr[3], nrm[3] = {0.0, 0.0, 0.0};
-          ctr[ax] = E[ax][a];
-          ctr[lo1] = 0.5 * (E[lo1][I[lo1]] + E[lo1][I[lo1] + 1]);
-          ctr[lo2] = 0.5 * (E[lo2][I[lo2]] + E[lo2][I[lo2] + 1]);
-          nrm[ax] = 1.0;
-          const double area = (E[lo1][I[lo1] + 1] - E[lo1][I[lo1]]) * (E[lo2][I[lo2] + 1] - E[lo2][I[lo2]]);
-          const double4_32a cc = make_double4_32a(ctr[0], ctr[1], ctr[2], 0.0);
-          g.tri_cen.push_back(cc);
-          for (int q = 0; q < 3; ++q) {  // unused: midpoint rule, no near rule
-            g.tri_vtx.push_back(cc);
-            g.tri_pts.push_back(cc);
-          }
-          g.tri_nrm.push_back(make_double4_32a(nrm[0], nrm[1], nrm[2], area));
-          g.tri_omega.push_back(rho0 / rin - rho0 / rout);   // alpha_in - alpha_out
-          g.mass.push_back(0.5 * (rho0 / rin + rho0 / rout));  // Eq. (mass_function) on an interface
-        }
-  }
+  for_each_jump_face(grid, rho, rho0, [&](const double ctr[3], int ax, double area, double rin, double rout) {
+    double nrm[3] = {0.0, 0.0, 0.0};
+    nrm[ax] = 1.0;
+    const double4_32a cc = make_double4_32a(ctr[0], ctr[1], ctr[2], 0.0);
+    g.tri_cen.push_back(cc);
+    for (int q = 0; q < 3; ++q) {  // unused: midpoint rule, no near rule
+      g.tri_vtx.push_back(cc);
+      g.tri_pts.push_back(cc);
+    }
+    g.tri_nrm.push_back(make_double4_32a(nrm[0], nrm[1], nrm[2], area));
+    g.tri_omega.push_back(rho0 / rin - rho0 / rout);   // alpha_in - alpha_out
+    g.mass.push_back(0.5 * (rho0 / rin + rho0 / rout));  // Eq. (mass_function) on an interface
+  });
   g.tri_npts = 1;
   h->n_tet = nc;
   h->n_tri = (int64_t)g.tri_cen.size();
@@ -617,6 +631,50 @@ extern "C" vsie_status vsie_set_frequency(vsie_handle* h, double k0) {
     set_error(msg);
   }
   return s;
+}
+
+// Host-only description of the interface unknowns of a cuboid grid (the faces in their
+// unknown order), for callers that map solution vectors back to the grid.
+extern "C" vsie_status vsie_cuboid_faces(const vsie_cuboid_grid* grid, const double* rho, double rho0,
+                                         int64_t capacity, int64_t* n_faces, double* centres, int32_t* axis,
+                                         double* area, double* omega, double* mass) {
+  clear_error();
+  if (!grid || !rho || !n_faces || !grid->x_edges || !grid->y_edges || !grid->z_edges || grid->nx < 1 ||
+      grid->ny < 1 || grid->nz < 1 || capacity < 0 || !finite_pos(rho0)) {
+    set_error("vsie_cuboid_faces: invalid argument");
+    return VSIE_ERR_ARG;
+  }
+  const double* E[3] = {grid->x_edges, grid->y_edges, grid->z_edges};
+  const int64_t N[3] = {grid->nx, grid->ny, grid->nz};
+  for (int d = 0; d < 3; ++d)
+    for (int64_t a = 0; a < N[d]; ++a)
+      if (!(E[d][a + 1] > E[d][a]) || !std::isfinite(E[d][a]) || !std::isfinite(E[d][a + 1])) {
+        set_error("vsie_cuboid_faces: edge coordinates must be finite and strictly increasing");
+        return VSIE_ERR_MESH;
+      }
+  for (int64_t e = 0; e < N[0] * N[1] * N[2]; ++e)
+    if (!finite_pos(rho[e])) {
+      set_error("vsie_cuboid_faces: non-positive or non-finite density on cell " + std::to_string(e));
+      return VSIE_ERR_MESH;
+    }
+  int64_t count = 0;
+  for_each_jump_face(grid, rho, rho0, [&](const double ctr[3], int ax, double a, double rin, double rout) {
+    if (count < capacity) {
+      if (centres)
+        for (int d = 0; d < 3; ++d) centres[3 * count + d] = ctr[d];
+      if (axis) axis[count] = ax;
+      if (area) area[count] = a;
+      if (omega) omega[count] = rho0 / rin - rho0 / rout;
+      if (mass) mass[count] = 0.5 * (rho0 / rin + rho0 / rout);
+    }
+    ++count;
+  });
+  *n_faces = count;
+  if (count > capacity && (centres || axis || area || omega || mass)) {
+    set_error("vsie_cuboid_faces: capacity smaller than the number of faces");
+    return VSIE_ERR_ARG;
+  }
+  return VSIE_OK;
 }
 
 extern "C" vsie_status vsie_create_cuboid(const vsie_cuboid_grid* grid, const double* rho, const double* c,
