@@ -86,3 +86,28 @@ def test_field_and_frequency_calls_reject_null_handle(lib):
     assert lib.vsie_scattered_field(None, None, 1, pts.ctypes.data_as(ctypes.c_void_p), 1, 64, None, None) == 1
     assert lib.vsie_set_frequency(None, 2.0) == 1
     assert b"vsie_set_frequency" in lib.vsie_last_error()
+
+
+def test_header_is_plain_c_and_matches_the_binding_layouts(tmp_path):
+    """include/vsie.h compiles as pedantic C99, and the structs the binding mirrors have
+    the same sizes on both sides."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "vsie.h"\n'
+        "int main(void) {\n"
+        '  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(vsie_mesh), sizeof(vsie_material),\n'
+        "         sizeof(vsie_options), sizeof(vsie_solve_opts), sizeof(vsie_solve_info),\n"
+        "         sizeof(vsie_cuboid_grid));\n"
+        "  return 0;\n}\n")
+    exe = tmp_path / "abi"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                    os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    sizes = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                            text=True).stdout.split()]
+    assert sizes == [ctypes.sizeof(B._Mesh), ctypes.sizeof(B._Material), ctypes.sizeof(B._Options),
+                     ctypes.sizeof(B._SolveOpts), ctypes.sizeof(B._SolveInfo), ctypes.sizeof(B._CuboidGrid)]
