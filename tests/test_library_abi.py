@@ -111,3 +111,10 @@ def test_header_is_plain_c_and_matches_the_binding_layouts(tmp_path):
                                             text=True).stdout.split()]
     assert sizes == [ctypes.sizeof(B._Mesh), ctypes.sizeof(B._Material), ctypes.sizeof(B._Options),
                      ctypes.sizeof(B._SolveOpts), ctypes.sizeof(B._SolveInfo), ctypes.sizeof(B._CuboidGrid)]
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No CPU fallback: without libvsie.so the binding raises instead of computing."""
+    monkeypatch.setattr(B, "_lib", None)
+    with pytest.raises(ImportError):
+        B.load_library(str(tmp_path / "libvsie.so"))
