@@ -154,19 +154,28 @@ vsie_status vsie_set_frequency(vsie_handle* h, double k0);
 
 void vsie_destroy(vsie_handle* h);
 
-/* Sizes of the discrete system. */
+/* Sizes of the discrete system: n unknowns (volume elements, then interface elements),
+ * the number of far-field source points (quadrature points of the far rule), and the
+ * entries of the near/self correction.  Any output may be NULL.  VSIE_ERR_ARG on a null
+ * handle. */
 vsie_status vsie_sizes(const vsie_handle* h, int64_t* n, int64_t* n_far_sources,
                        int64_t* nnz_correction);
 
 /* y = A x for nrhs columns (Eq. vsie at every collocation point).  precision 32: far-field
- * sums in FP32 with per-tile FP64 accumulation, correction and mass in FP64;
- * precision 64: everything in FP64.  x, y: device complex128, n x nrhs column-major,
- * must not alias.  Errors: VSIE_ERR_ARG, VSIE_ERR_CUDA. */
+ * sums in FP32 with per-tile FP64 accumulation, correction and mass in double-float/FP64;
+ * precision 48: far-field sums in double-float arithmetic on the FP32 pipe (about 2^-47
+ * per operation, FP64-class results); precision 64: everything in FP64.  x, y: device
+ * complex128, n x nrhs column-major, must not alias.  Asynchronous.  Errors: VSIE_ERR_ARG
+ * (null pointer, nrhs < 1, precision not 32/48/64, aliasing), VSIE_ERR_OOM,
+ * VSIE_ERR_CUDA. */
 vsie_status vsie_apply(vsie_handle* h, const void* d_x, void* d_y, int32_t nrhs,
                        int32_t precision, void* stream);
 
 /* Same operator with host buffers: copies x to the device, applies, copies y back and
- * synchronises the stream before returning.  Uses library-owned device buffers. */
+ * synchronises the stream before returning.  h_x, h_y: host complex128 n x nrhs
+ * (interleaved doubles), caller-owned; pinned memory makes the copies asynchronous with
+ * respect to other streams.  Uses library-owned device buffers, grown on demand.  Errors
+ * as vsie_apply. */
 vsie_status vsie_apply_host(vsie_handle* h, const double* h_x, double* h_y, int32_t nrhs,
                             int32_t precision, void* stream);
 
@@ -258,19 +267,25 @@ vsie_status vsie_graph_launch(vsie_graph* g, void* stream);
 vsie_status vsie_graph_nodes(const vsie_graph* g, int64_t* nodes);
 void vsie_graph_destroy(vsie_graph* g);
 
-/* x = A^H y (conjugate transpose), same layouts and precisions as vsie_apply. */
+/* x = A^H y (conjugate transpose: the roles of targets and sources swapped in the far
+ * sums, the transposed correction, the real mass), same layouts as vsie_apply; precision
+ * 32 or 64 (VSIE_ERR_ARG for 48).  Asynchronous; the first call allocates the adjoint
+ * records. */
 vsie_status vsie_adjoint_apply(vsie_handle* h, const void* d_y, void* d_x, int32_t nrhs,
                                int32_t precision, void* stream);
 
 /* Right-hand side of Eq. (planewave): b_i = exp(i k0 x_i . d_j) for ndir unit directions
- * (host array 3*ndir, normalised by the library); b: device complex128 n x ndir. */
+ * (host array 3*ndir, normalised by the library); b: device complex128 n x ndir, column
+ * j for direction j.  FP64.  Blocking.  VSIE_ERR_ARG on a null pointer, ndir outside
+ * 1..65535 or a zero or non-finite direction. */
 vsie_status vsie_plane_wave_rhs(vsie_handle* h, const double* h_dirs, int32_t ndir,
                                 void* d_b, void* stream);
 
 /* Far-field pattern of the scattered field from Eq. (vsie) used as a representation
  * formula in Omega_0 (Sec. 2.3.1): p_inf(xhat) = (1/4pi) sum_j e^{-ik0 xhat.y_j}
  * (s_j - i k0 xhat.v_j) p_e(j) over the far-field source points.  p: device complex128
- * n x nrhs; dirs: host 3*ndir; out: device complex128 ndir x nrhs.  FP64. */
+ * n x nrhs; dirs: host 3*ndir; out: device complex128 ndir x nrhs.  FP64.  Blocking.
+ * VSIE_ERR_ARG on a null pointer, ndir < 1 or nrhs outside 1..65535. */
 vsie_status vsie_far_field(vsie_handle* h, const void* d_p, int32_t nrhs,
                            const double* h_dirs, int32_t ndir, void* d_out, void* stream);
 
