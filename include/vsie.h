@@ -313,9 +313,14 @@ typedef struct {
   int32_t fp32_applies;     /* number of FP32 operator applications                    */
 } vsie_solve_info;
 
-/* Solve A x = b for one right-hand side with x0 = 0 (GMRES, no preconditioner, as in
- * Sec. 3.1).  b, x: device complex128 (n).  Blocking (reads residual norms on the host).
- * Returns VSIE_ERR_NOT_CONVERGED (x still written, info filled) when the limits are hit. */
+/* Solve A x = b for one right-hand side from x0 = 0 (GMRES, no preconditioner, as in
+ * Sec. 3.1), or from the iterate held in x when opts->initial_guess is set.  b, x: device
+ * complex128 (n), caller-owned; the workspace ((basis + 4) x n complex128) is allocated
+ * and freed by the call.  Blocking (reads residual norms on the host).  Returns
+ * VSIE_ERR_NOT_CONVERGED (x still written, info filled) when the limits are hit,
+ * VSIE_ERR_NAN on a non-finite right-hand side or residual, VSIE_ERR_BREAKDOWN when GMRES
+ * stalls with a nonzero residual, VSIE_ERR_ARG on invalid options (a basis above 3000
+ * columns included). */
 vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
                        const vsie_solve_opts* opts, vsie_solve_info* info, void* stream);
 
