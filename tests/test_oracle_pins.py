@@ -557,3 +557,30 @@ def test_exterior_field_against_mie_and_far_field():
     far = O.scattered_field(D, p, R * xhat) * R * np.exp(-1j * D.k0 * R)
     pinf = D.far_field(p, xhat)
     assert np.linalg.norm(far - pinf) / np.linalg.norm(pinf) < 1e-3
+
+
+def test_lsq_grad_alpha_drops_nearly_coplanar_direction():
+    """The least-squares reading drops singular values below 1e-6 of the largest (minimum
+    norm in the span that is kept).  A tetrahedron whose three face neighbours' centroid
+    offsets are coplanar up to 1e-8 (relative) gets no gradient component along the
+    normal of that plane, although alpha is linear and has one; a 1e-10 cutoff would keep
+    it.  The neighbours are built by hand: neighbour f shares the face opposite vertex v of
+    e and has apex v + u_f, so its centroid offset is u_f / 4."""
+    A, B, C, D = np.eye(3)[0], np.eye(3)[1], np.eye(3)[2], np.zeros(3)
+    u1 = np.array([1.0, 0.2, -0.3])
+    u2 = np.array([-0.4, 1.0, 0.1])
+    nrm = np.cross(u1, u2)
+    nrm /= np.linalg.norm(nrm)
+    u3 = 0.7 * u1 - 0.5 * u2 + 1e-8 * nrm
+    vert = np.array([A, B, C, D, D + u1, C + u2, B + u3])
+    tet = np.array([[0, 1, 2, 3], [0, 1, 2, 4], [0, 1, 3, 5], [0, 2, 3, 6]])
+    dom = np.ones(4, dtype=np.int8)
+    g_true = np.array([0.3, -0.2, 0.5])
+    cen = vert[tet].mean(axis=1)
+    sv = np.linalg.svd(cen[1:] - cen[0], compute_uv=False)
+    assert 1e-10 < sv[-1] / sv[0] < 1e-6
+    g, _ = O.lsq_grad_alpha(vert, tet, dom, cen @ g_true)
+    assert abs(g[0] @ nrm) < 1e-6 * np.linalg.norm(g_true)       # direction dropped
+    assert abs(g_true @ nrm) > 0.1                                 # ... though alpha has one
+    inplane = g_true - (g_true @ nrm) * nrm
+    assert np.allclose(g[0], inplane, atol=1e-6)
