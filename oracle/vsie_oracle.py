@@ -341,6 +341,53 @@ class Discretisation:
             A[:, self.n_tet:] = acc
         return A
 
+    def matrix_columns(self, cols) -> np.ndarray:
+        """Columns ``cols`` of the collocation matrix A (n, len(cols)) from the same
+        element-by-element definition as ``matrix_rows``, read down a column: the integral
+        of element e at every collocation point (the far rule, or the near rule at points
+        within the near radius of e, the self term at e's own point), plus the mass on the
+        diagonal.  Serves entries of A^H lam = conj(A)^T lam at large sizes."""
+        cols = np.asarray(cols, dtype=np.int64)
+        X = self.targets
+        k = self.k0
+        out = np.zeros((self.n, cols.shape[0]), dtype=np.complex128)
+        for c, e in enumerate(cols):
+            if e < self.n_tet:
+                s = self.sdens[e] * self.tet_vol[e]
+                g = self.grad_alpha[e] * self.tet_vol[e]
+                if self.far_points == 4:
+                    for q in range(4):
+                        out[:, c] += pair_kernel(X - self.tet_pts[e, q], np.full(self.n, s / 4.0),
+                                                 np.tile(g / 4.0, (self.n, 1)), k)
+                else:
+                    d = X - self.tet_cen[e]
+                    out[:, c] = pair_kernel(d, np.full(self.n, s), np.tile(g, (self.n, 1)), k)
+                    if self.near_radius > 0.0:
+                        near = np.nonzero(np.einsum("ri,ri->r", d, d) < self.near_radius ** 2)[0]
+                        acc = np.zeros(near.shape[0], dtype=np.complex128)
+                        for q in range(4):
+                            acc += pair_kernel(X[near] - self.tet_pts[e, q], np.full(near.shape[0], s / 4.0),
+                                               np.tile(g / 4.0, (near.shape[0], 1)), k)
+                        out[near, c] = acc
+                out[e, c] = -self.sdens[e] * ball_green_integral(self.a_eq[e], k)
+            else:
+                t = e - self.n_tet
+                w3 = self.tri_area[t] / 3.0
+                vt = -(self.tri_omega[t] * w3) * self.tri_nrm[t]
+                for q in range(3):
+                    out[:, c] += pair_kernel(X - self.tri_pts[t, q], np.zeros(self.n),
+                                             np.tile(vt, (self.n, 1)), k)
+                if self.tri_near_radius > 0.0:
+                    d = X - self.tri_cen[t]
+                    near = np.nonzero(np.einsum("ri,ri->r", d, d) < self.tri_near_radius ** 2)[0]
+                    out[near, c] = self.tri_omega[t] * double_layer_near(
+                        X[near], np.broadcast_to(self.tri_P[t], (near.shape[0], 3, 3)),
+                        np.broadcast_to(self.tri_nrm[t], (near.shape[0], 3)),
+                        np.full(near.shape[0], self.tri_area[t]), k)
+                    out[e, c] = 0.0
+            out[e, c] += self.mass[e]
+        return out
+
     def _chunk(self) -> int:
         pts = self.n_tet * (4 if self.far_points == 4 else 1) + 3 * self.n_tri
         return max(1, int(3.0e6 // max(pts, 1)))

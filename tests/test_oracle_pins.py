@@ -584,3 +584,19 @@ def test_lsq_grad_alpha_drops_nearly_coplanar_direction():
     assert abs(g_true @ nrm) > 0.1                                 # ... though alpha has one
     inplane = g_true - (g_true @ nrm) * nrm
     assert np.allclose(g[0], inplane, atol=1e-6)
+
+
+@pytest.mark.parametrize("maker", [lambda: W.smooth_density_ball(6, 1, 1, 3.0),
+                                   lambda: W.single_ball(5, 1, 2.0),
+                                   lambda: W.layered_ball(6, 1, 1, 4.0)])
+def test_matrix_columns_equal_assembled_columns(maker):
+    """Columns read down the element-by-element definition equal the columns of the
+    assembled rows (every rule branch: far, near, self, interface near and self)."""
+    w = maker()
+    D = O.Discretisation.from_workload(w)
+    A = D.assemble()
+    rng = np.random.default_rng(4)
+    cols = np.concatenate([rng.choice(D.n_tet, 6, replace=False),
+                           D.n_tet + rng.choice(D.n_tri, 4, replace=False), [0, D.n - 1]])
+    C = D.matrix_columns(cols)
+    assert np.allclose(C, A[:, cols], rtol=1e-13, atol=1e-14 * np.abs(A).max())
