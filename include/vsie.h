@@ -179,6 +179,21 @@ vsie_status vsie_apply(vsie_handle* h, const void* d_x, void* d_y, int32_t nrhs,
 vsie_status vsie_apply_host(vsie_handle* h, const double* h_x, double* h_y, int32_t nrhs,
                             int32_t precision, void* stream);
 
+/* Rows row_begin .. row_end-1 of y = A x (Eq. vsie at those collocation points only):
+ * d_y[i - row_begin] = (A x)_i.  Every far-field source point contributes to every row,
+ * so x holds all n unknowns while y holds only the rows.  Rows are independent and equal in
+ * far-field work; a contiguous split of 0..n over several devices therefore
+ * partitions an apply, each device holding the whole operator and all of x (the row-sharded
+ * multi-GPU apply gathers the slices).  Each row equals the same row of vsie_apply to
+ * rounding; the summation order differs.  The same call also gives the error or the rate
+ * of an apply on a sample of rows.  x: device complex128 n; y: device complex128
+ * (row_end - row_begin); they must not alias.  precision 32, 48 or 64 as in vsie_apply.
+ * Asynchronous; may grow the handle's scratch on first use.  Errors: VSIE_ERR_ARG (null
+ * pointer, aliasing, precision, rows outside 0 <= row_begin <= row_end <= n),
+ * VSIE_ERR_OOM, VSIE_ERR_CUDA. */
+vsie_status vsie_apply_rows(vsie_handle* h, const void* d_x, void* d_y, int64_t row_begin,
+                            int64_t row_end, int32_t precision, void* stream);
+
 /* One vsie_apply (nrhs = 1) with CUDA events recorded on ``stream`` between its phases;
  * blocks until done.  kernel_ms[4] receives the device time of: the charge prescale, the
  * far-field sum over volume sources without a vector weight, the far-field sum over
@@ -196,13 +211,16 @@ vsie_status vsie_apply_timed(vsie_handle* h, const void* d_x, void* d_y, int32_t
  * 2,097,152 complex128 elements (32 MiB) compiled into the library, which every GPU that
  * loads the library holds until the process exits.  Calls allocate nothing and free
  * nothing.  The first call on a device looks up that array's device address (with the
- * handle's device made current for the lookup); make that first call before any stream
- * capture.  All calls share the one array and its contents persist between calls (every
+ * handle's device made current for the lookup) and keeps it for later calls; make that
+ * first call before any stream capture.  A device reset (cudaDeviceReset) reloads the
+ * library's device code and leaves the kept address stale: do not use this call on a
+ * device after resetting it.  All calls share the one array and its contents persist between calls (every
  * element a call reads it has written first), so calls that overlap on the GPU -- on
  * different streams or different handles -- race and must be serialised by the caller.
  * Same arguments, layouts and precisions as vsie_apply.  Errors: VSIE_ERR_ARG when the
- * operator's launch shape needs more scratch than the array holds (the message gives
- * both sizes; vsie_apply still works), and as vsie_apply otherwise. */
+ * operator's launch shape at the requested precision needs more scratch than the array
+ * holds (the message gives both sizes; y is not written; vsie_apply still works), and as
+ * vsie_apply otherwise. */
 vsie_status vsie_apply_noalloc(vsie_handle* h, const void* d_x, void* d_y, int32_t nrhs,
                                int32_t precision, void* stream);
 
@@ -394,6 +412,17 @@ vsie_status vsie_gradient_channels(vsie_handle* h, const void* d_lam, int32_t pr
  * NULL), h_owner n_far owning unknowns (may be NULL), h_class n_far class indices 0, 1, 2
  * (may be NULL).  Host arrays, caller-owned; blocking. */
 vsie_status vsie_source_points(const vsie_handle* h, double* h_xyz, int32_t* h_owner, int32_t* h_class);
+
+/* Measured issue rates of the SM pipes that bound the far-field sums (the paper reports
+ * no timings and has no counterpart; this is roofline evidence for the ALU-bound
+ * kernels).  On the current device, each of five probe kernels runs independent
+ * dependency chains of one instruction in one full wave of blocks.  per_clk_per_sm[5]
+ * receives the median over SMs of the operations completed per SM clock (clock64 spans)
+ * for: MUFU rsqrt, MUFU sin, scalar FP32 FMA, paired FP32x2 FMA (counted as two FMAs),
+ * FP64 FMA.  sm_mhz (may be NULL) receives the SM clock implied by the longest span and
+ * the launch's event time.  Allocates and frees a small device buffer; about 0.1 s;
+ * blocking.  Errors: VSIE_ERR_ARG (null output), VSIE_ERR_CUDA. */
+vsie_status vsie_pipe_probe(double* per_clk_per_sm, double* sm_mhz, void* stream);
 
 /* Thread-local description of the last error ("" if none). */
 const char* vsie_last_error(void);

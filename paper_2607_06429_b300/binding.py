@@ -30,7 +30,8 @@ EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_appl
            "vsie_graph_create_batched", "vsie_graph_launch", "vsie_graph_nodes", "vsie_graph_destroy",
            "vsie_autotune", "vsie_gradient_channels", "vsie_source_points",
            "vsie_lsq_grad_alpha", "vsie_lsq_grad_alpha_adjoint", "vsie_scattered_field",
-           "vsie_create_cuboid", "vsie_set_frequency", "vsie_cuboid_faces", "vsie_last_error")
+           "vsie_create_cuboid", "vsie_set_frequency", "vsie_cuboid_faces", "vsie_apply_rows",
+           "vsie_pipe_probe", "vsie_last_error")
 
 
 class VsieError(RuntimeError):
@@ -112,6 +113,8 @@ def load_library(path: str = LIB_PATH):
     lib.vsie_sizes.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
     lib.vsie_apply.argtypes = [P, P, P, I32, I32, P]
     lib.vsie_apply_host.argtypes = [P, P, P, I32, I32, P]
+    lib.vsie_apply_rows.argtypes = [P, P, P, I64, I64, I32, P]
+    lib.vsie_pipe_probe.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P]
     lib.vsie_apply_noalloc.argtypes = [P, P, P, I32, I32, P]
     lib.vsie_apply_batched.argtypes = [P, P, P, I32, I32, P]
     lib.vsie_adjoint_apply.argtypes = [P, P, P, I32, I32, P]
@@ -272,6 +275,23 @@ class Operator:
             y = torch.empty_like(x)
         _check(_lib.vsie_apply(self._h, _dev(x, "x"), _dev(y, "y"), nrhs, int(precision),
                                _stream(stream)))
+        return y
+
+    def apply_rows(self, x, row_begin, row_end, y=None, precision=32, stream=None):
+        """Rows row_begin .. row_end-1 of A x (vsie_apply_rows): x has all n unknowns, y the
+        (row_end - row_begin) rows."""
+        import torch
+        if x.dim() != 1 or x.shape[0] != self.n:
+            raise ValueError("x must have shape (n,)")
+        m = int(row_end) - int(row_begin)
+        if y is None:
+            y = torch.empty(max(m, 0), dtype=x.dtype, device=x.device)
+        elif y.dim() != 1 or y.shape[0] != m:
+            raise ValueError("y must have shape (row_end - row_begin,)")
+        if m == 0 and 0 <= int(row_begin) <= self.n:
+            return y  # nothing to compute (an empty tensor has no device address to pass)
+        _check(_lib.vsie_apply_rows(self._h, _dev(x, "x"), _dev(y, "y"), int(row_begin), int(row_end),
+                                    int(precision), _stream(stream)))
         return y
 
     def apply_batched(self, x, y=None, precision=32, stream=None):
@@ -444,6 +464,19 @@ class Operator:
             _check(st)
         return x, SolveInfo(st, info.iterations, info.refinements, info.rel_residual,
                             info.fp64_applies, info.fp32_applies)
+
+
+def pipe_probe(stream=None):
+    """Sustained issue rates per clock and per SM of the pipes the far-field sums use
+    (vsie_pipe_probe), measured on the current device, with the SM clock seen."""
+    load_library()
+    r = (ctypes.c_double * 5)()
+    mhz = ctypes.c_double()
+    _check(_lib.vsie_pipe_probe(r, ctypes.byref(mhz), _stream(stream)))
+    names = ("mufu_rsqrt", "mufu_sin", "ffma", "ffma2_fma_ops", "dfma")
+    out = {k: float(v) for k, v in zip(names, r)}
+    out["sm_mhz"] = float(mhz.value)
+    return out
 
 
 def _multi_arrays(ops, xs, ys):

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libvsie.so")
-SOURCES = ["vsie_api.cu", "nbody.cu", "correction.cu", "solve.cu", "farfield.cu", "noalloc.cu", "batch.cu", "batch64.cu", "solve_batched.cu", "graph.cu", "lsq_gradient.cu", "field.cu"]
+SOURCES = ["vsie_api.cu", "nbody.cu", "correction.cu", "solve.cu", "farfield.cu", "noalloc.cu", "batch.cu", "batch64.cu", "solve_batched.cu", "graph.cu", "lsq_gradient.cu", "field.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-ftz=true", "--expt-extended-lambda",
          "-Xcompiler", "-fPIC,-O2", "-shared", "-cudart", "static"]
@@ -27,12 +27,29 @@ def needs_build() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every source to an object file (in parallel, one nvcc per source), then link
+    the shared library."""
     if not force and not needs_build():
         return LIB
+    from concurrent.futures import ThreadPoolExecutor
     nvcc = os.environ.get("NVCC", "nvcc")
+    objdir = os.path.join(ROOT, "_build", "libvsie")
+    os.makedirs(objdir, exist_ok=True)
+    compile_flags = [f for f in FLAGS if f not in ("-shared",)]
+
+    def compile_one(src):
+        obj = os.path.join(objdir, os.path.splitext(src)[0] + ".o")
+        cmd = [nvcc, *ARCH, *compile_flags, "-I", INCLUDE, "-I", CSRC, "-c",
+               os.path.join(CSRC, src), "-o", obj]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        subprocess.run(cmd, check=True)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as pool:
+        objs = list(pool.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, *FLAGS, "-I", INCLUDE, "-I", CSRC,
-           *[os.path.join(CSRC, f) for f in SOURCES], "-o", tmp]
+    cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-Xcompiler", "-fPIC", *objs, "-o", tmp]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)

@@ -345,6 +345,22 @@ vsie_status correction_apply(vsie_handle* h, const double2* x, double2* y, int p
   return VSIE_OK;
 }
 
+// Rows [r0, r1) of the correction and mass: y_out[i - r0] += m_i x_i + (Delta x)_i.  The
+// row pointers hold absolute offsets into the column and value arrays, and the columns are
+// global unknowns, so the kernel of the full apply serves with its row arrays offset.
+vsie_status correction_apply_rows(vsie_handle* h, const double2* x, double2* y_out, int64_t r0, int64_t r1,
+                                  int precision, cudaStream_t st) {
+  const int64_t n = h->n, m = r1 - r0;
+  if (m <= 0) return VSIE_OK;
+  const float4* val = precision == 32 ? h->C.val32 : h->C.val64;
+  to_df_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, h->C.xd, n);
+  const unsigned blocks = (unsigned)((m * 32 + 255) / 256);
+  corr_apply_kernel<<<blocks, 256, 0, st>>>(h->C.row_ptr + r0, h->C.col, val, h->mass + r0, h->C.xd, x + r0,
+                                            y_out, m);
+  VSIE_CUDA(cudaGetLastError());
+  return VSIE_OK;
+}
+
 vsie_status correction_adjoint(vsie_handle* h, const double2* lam, double2* x, int precision,
                                cudaStream_t st) {
   const int64_t n = h->n;

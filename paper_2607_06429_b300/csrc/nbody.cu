@@ -1336,9 +1336,7 @@ vsie_status far_sum_f_only(vsie_handle* h, const double2* x, double2* y, int pre
   return forward(h, y, precision, nullptr, st, 4, nullptr);
 }
 
-size_t far_split_elems(const vsie_handle* h) {
-  return std::max(std::max(forward_plans(h, 32).slots, forward_plans(h, 64).slots), forward_plans(h, 48).slots);
-}
+size_t far_split_elems(const vsie_handle* h, int precision) { return forward_plans(h, precision).slots; }
 
 vsie_status far_sums_into(vsie_handle* h, double2* y, int precision, double2* scratch,
                           cudaStream_t st) {

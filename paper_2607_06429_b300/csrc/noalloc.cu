@@ -25,7 +25,10 @@ constexpr size_t kNoAllocScratchElems = (size_t)1 << 21;
 static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocScratchElems];
 
 // Device address of g_noalloc_scratch, looked up once per device (host code may not use
-// the symbol itself as a device pointer: on the host it names a shadow variable).
+// the symbol itself as a device pointer: on the host it names a shadow variable).  The
+// address belongs to the device's context as it was at the lookup: after a device reset
+// (cudaDeviceReset) the module is loaded again, possibly elsewhere, and the cached address
+// is stale, so the entry point must not be used across a reset.
 constexpr int kMaxDevices = 64;
 static std::mutex g_noalloc_mu;
 static double2* g_noalloc_ptr[kMaxDevices] = {};
@@ -57,6 +60,7 @@ using namespace vsie;
 extern "C" vsie_status vsie_apply_noalloc(vsie_handle* h, const void* d_x, void* d_y,
                                           int32_t nrhs, int32_t precision, void* stream) {
   clear_error();
+  TraceRange trace("vsie_apply_noalloc");
   if (!h || !d_x || !d_y) {
     set_error("vsie_apply_noalloc: null handle or vector");
     return VSIE_ERR_ARG;
@@ -65,7 +69,7 @@ extern "C" vsie_status vsie_apply_noalloc(vsie_handle* h, const void* d_x, void*
     set_error("vsie_apply_noalloc: nrhs must be >= 1, precision 32, 48 or 64, x and y distinct");
     return VSIE_ERR_ARG;
   }
-  const size_t need = far_split_elems(h);
+  const size_t need = far_split_elems(h, precision);
   if (need > kNoAllocScratchElems) {
     set_error("vsie_apply_noalloc: this operator's launch shape needs " + std::to_string(need) +
               " scratch elements; the fixed scratch holds " + std::to_string(kNoAllocScratchElems) +

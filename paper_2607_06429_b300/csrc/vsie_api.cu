@@ -777,6 +777,30 @@ extern "C" vsie_status vsie_apply(vsie_handle* h, const void* d_x, void* d_y, in
   return VSIE_OK;
 }
 
+extern "C" vsie_status vsie_apply_rows(vsie_handle* h, const void* d_x, void* d_y, int64_t row_begin,
+                                       int64_t row_end, int32_t precision, void* stream) {
+  clear_error();
+  TraceRange trace("vsie_apply_rows");
+  VSIE_TRY(check_apply_args(h, d_x, d_y, 1, precision, "vsie_apply_rows"));
+  if (row_begin < 0 || row_end < row_begin || row_end > h->n) {
+    set_error("vsie_apply_rows: rows must satisfy 0 <= row_begin <= row_end <= n (n = " +
+              std::to_string(h->n) + ")");
+    return VSIE_ERR_ARG;
+  }
+  const int64_t m = row_end - row_begin;
+  if (m == 0) return VSIE_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const double2* x = (const double2*)d_x;
+  double2* y = (double2*)d_y;
+  // the far sums of vsie_apply with the collocation records of the rows as targets (they
+  // zero y first), then the rows' correction and mass
+  VSIE_TRY(far_sums_at(h, x, h->tgt64 + row_begin, h->tgt32 + row_begin, h->tgtdf + 2 * row_begin, m, y,
+                       precision, st));
+  VSIE_TRY(correction_apply_rows(h, x, y, row_begin, row_end, precision, st));
+  VSIE_CUDA(cudaGetLastError());
+  return VSIE_OK;
+}
+
 extern "C" vsie_status vsie_apply_host(vsie_handle* h, const double* h_x, double* h_y,
                                        int32_t nrhs, int32_t precision, void* stream) {
   clear_error();

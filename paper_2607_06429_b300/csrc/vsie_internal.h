@@ -238,8 +238,8 @@ vsie_status far_prescale(vsie_handle* h, const double2* x, int precision, cudaSt
 vsie_status far_sum_g(vsie_handle* h, double2* y, int precision, cudaStream_t st, int* launches);
 vsie_status far_sum_f(vsie_handle* h, double2* y, int precision, cudaStream_t st, int* launches);
 // All far-field sums with the partial-tile slots in caller-provided scratch; the scratch
-// must hold far_split_elems(h) double2 values (nothing is allocated).
-size_t far_split_elems(const vsie_handle* h);
+// must hold far_split_elems(h, precision) double2 values (nothing is allocated).
+size_t far_split_elems(const vsie_handle* h, int precision);
 vsie_status far_sums_into(vsie_handle* h, double2* y, int precision, double2* scratch,
                           cudaStream_t st);
 // x_e = sum_{j in e} sum_i conj(C_ij) lam_i (overwrites x).
@@ -248,6 +248,9 @@ vsie_status far_adjoint(vsie_handle* h, const double2* lam, double2* x, int prec
 // y += m x + Delta x  (Delta for the given precision's far sum)
 vsie_status correction_apply(vsie_handle* h, const double2* x, double2* y, int precision,
                              cudaStream_t st);
+// rows [r0, r1) only: y_out[i - r0] += m_i x_i + (Delta x)_i  (x: all n unknowns)
+vsie_status correction_apply_rows(vsie_handle* h, const double2* x, double2* y_out, int64_t r0, int64_t r1,
+                                  int precision, cudaStream_t st);
 // y[:, r] += m x[:, r] + Delta x[:, r] for ncols columns (n x ncols column-major), 64 at a
 // time with one pass over the correction matrix per 64 columns
 vsie_status correction_apply_block(vsie_handle* h, const double2* x, double2* y, int ncols, int precision,

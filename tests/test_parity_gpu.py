@@ -232,3 +232,52 @@ def test_apply_sampled_rows_full_size(name, count):
     if name.startswith("perturbed40"):  # per-element contrast: the double-float sums at full size
         y48 = op.apply(xd, precision=48).cpu().numpy()
         assert rel(y48[rows], ref) <= TOL64, rel(y48[rows], ref)
+
+
+# ----------------------------------------------------------------- row ranges
+
+def test_apply_rows_small(small_case):
+    """vsie_apply_rows on ragged, empty, single-row and full ranges (volume rows, the
+    volume/interface boundary, interface rows) against the oracle's rows, all precisions."""
+    name, w, D, A = small_case
+    from paper_2607_06429_b300 import binding as B
+    op = _op(w)
+    x = W.random_vector(D.n, 31)
+    ref = A @ x
+    xd = _cuda(x)
+    nt = w.n_tet
+    ranges = [(0, D.n), (0, 1), (D.n - 1, D.n), (5, 5), (3, 700), (max(nt - 37, 0), min(nt + 41, D.n)),
+              (nt, D.n)]
+    for r0, r1 in ranges:
+        for prec, tol in ((64, TOL64), (48, TOL64), (32, TOL32)):
+            y = op.apply_rows(xd, r0, r1, precision=prec).cpu().numpy()
+            assert y.shape == (r1 - r0,)
+            if r1 > r0:
+                assert rel(y, ref[r0:r1]) <= tol, (name, r0, r1, prec, rel(y, ref[r0:r1]))
+    for r0, r1 in ((-1, 3), (4, 2), (0, D.n + 1)):
+        with pytest.raises(B.VsieError) as e:
+            op.apply_rows(xd, r0, r1, precision=32)
+        assert e.value.status == 1
+
+
+@pytest.mark.parametrize("name", ["nested80_k10", "nested128_k25"])
+def test_apply_rows_fp64_and_double_float_full_size(name):
+    """FP64 and double-float parity at full size on contiguous row blocks (volume rows deep
+    inside, the volume/interface boundary and the last interface rows), where a full
+    FP64 apply would take minutes: each row sums over every far-field source point."""
+    _torch()
+    w = W.CONFIGS[name]()
+    op = _op(w)
+    D = O.Discretisation.from_workload(w)
+    x = W.random_vector(w.n, 41)
+    xd = _cuda(x)
+    nt = w.n_tet
+    blocks = [(nt // 2, nt // 2 + 24), (nt - 12, nt + 12), (w.n - 16, w.n)]
+    for r0, r1 in blocks:
+        ref = D.apply_rows(x, np.arange(r0, r1))
+        y64 = op.apply_rows(xd, r0, r1, precision=64).cpu().numpy()
+        y48 = op.apply_rows(xd, r0, r1, precision=48).cpu().numpy()
+        y32 = op.apply_rows(xd, r0, r1, precision=32).cpu().numpy()
+        assert rel(y64, ref) <= TOL64, (name, r0, rel(y64, ref))
+        assert rel(y48, ref) <= TOL64, (name, r0, rel(y48, ref))
+        assert rel(y32, ref) <= TOL32, (name, r0, rel(y32, ref))
