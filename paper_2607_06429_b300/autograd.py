@@ -11,11 +11,14 @@ L = 1/2 sum_d |u_d - t_d|^2.  The backward pass is the adjoint method:
 A and F depend on (rho_e, c_e) through the single-layer weight
 s_e = beta_e - k0^2 alpha_e = k0^2 (rho0/rho_e)((c0/c_e)^2 - 1) of column e (Eqs. alpha, beta,
 vsie; every entry of that column is linear in s_e) and the mass m_e = rho0/rho_e
-(Eq. mass_function).  With g = F^H r and w = A^H lam - m * lam (the column sums of the
-single-layer part), the library's adjoint apply gives, per tetrahedron,
-    dL/ds_e = Re[conj(g_e - w_e) p_e] / s_e,    dL/dm_e = -Re[conj(lam_e) p_e],
-and the chain rule through s_e(rho_e, c_e) and m_e(rho_e) gives the gradients.  Elements
-with s_e = 0 (c_e = c0) are not supported (their single-layer column vanishes).
+(Eq. mass_function).  Column e is s_e times the single-layer column of unit weight, so
+dA/ds_e and dF/ds_e are the columns of an operator A_u (and its far-field map F_u) of the
+same mesh with s = 1 on every tetrahedron, no interface jump and rho = rho0 (unit mass):
+    dL/ds_e = Re[conj(F_u^H r - (A_u^H lam - lam))_e p_e],    dL/dm_e = -Re[conj(lam_e) p_e],
+from the library's adjoint apply and far-field adjoint on A_u (near and self corrections
+included), and the chain rule through s_e(rho_e, c_e) and m_e(rho_e) gives the gradients.
+No division by s_e occurs, so elements without contrast (c_e = c0, s_e = 0) and elements
+near it are covered.
 
 Without a density-gradient term (piecewise-constant density per element, grad(alpha) = 0)
 the column of element e scales as 1/rho_e as a whole, so p_e absorbs rho_e and the far field
@@ -77,9 +80,7 @@ class FarFieldMisfit(torch.autograd.Function):
         ds_dc = -2.0 * ctx.k0 ** 2 * (ctx.rho0 / rho_d) * ctx.c0 ** 2 / c_d ** 3
         dm_drho = -ctx.rho0 / rho_d ** 2
         if not ctx.lsq:
-            ahl = op.adjoint_apply(lam, precision=prec)
-            w = ahl[:nt] - m * lam[:nt]
-            dLds = (torch.conj(g[:nt] - w) * p[:nt]).real / s
+            dLds = _unit_channels(ctx.w, lam, r, p, ctx.dirs, prec, density_axes=False)[0]
             grad_rho = dLds * ds_drho + dLdm * dm_drho
         else:
             chans = _unit_channels(ctx.w, lam, r, p, ctx.dirs, prec)
@@ -94,19 +95,20 @@ class FarFieldMisfit(torch.autograd.Function):
         return grad_rho, grad_c, None, None, None, None, None
 
 
-def _unit_channels(w, lam, r, p, dirs, prec):
+def _unit_channels(w, lam, r, p, dirs, prec, density_axes=True):
     """Per-unit-weight derivative channels Re[conj(F_u^H r - (A_u^H lam - lam)) p] on the
-    tetrahedra for the unit single-layer weight (s = 1) and the unit density gradient along
-    x, y, z: A_u, F_u are the operator and far-field map of the same mesh with that unit
-    weight on every tetrahedron, no interface jump and unit mass (rho = rho0), so that every
-    column carries exactly d(column)/d(weight), near and self corrections included."""
+    tetrahedra for the unit single-layer weight (s = 1) and, with density_axes, the unit
+    density gradient along x, y, z: A_u, F_u are the operator and far-field map of the same
+    mesh with that unit weight on every tetrahedron, no interface jump and unit mass
+    (rho = rho0), so that every column carries exactly d(column)/d(weight), near and self
+    corrections included."""
     import torch
     nt = w.n_tet
     one = np.full(nt, w.rho0)
     tri_one = np.full(w.n_tri, w.rho0)
     c_s = np.full(nt, w.c0 / np.sqrt(1.0 + 1.0 / w.k0 ** 2))   # s = k0^2((c0/c)^2 - 1) = 1
     variants = [(c_s, None)]
-    for ax in range(3):
+    for ax in (range(3) if density_axes else ()):
         ga = np.zeros((nt, 3))
         ga[:, ax] = 1.0
         variants.append((np.full(nt, w.c0), ga))                 # s = 0, grad(alpha) = e_ax

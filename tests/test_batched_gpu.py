@@ -101,3 +101,24 @@ def test_expired_wait_reports_error_and_context_survives():
     Y = good.apply_batched(X)
     Yc = good.apply(X, precision=32)
     assert float(torch.linalg.norm(Y - Yc) / torch.linalg.norm(Yc)) <= TOL
+
+
+def test_batched_16_rhs_at_k25_full_size():
+    """The large workload at full size (128^3 grid, 6,594,816 tetrahedra, two ico-7 spheres,
+    k0 = 25, 7,250,176 unknowns, 8,560,896 far-field source points) with 16 right-hand
+    sides (plane waves) through the tensor-core multi-RHS apply: every column against the
+    oracle on seeded rows (volume rows, both interfaces)."""
+    torch, B = _setup()
+    w = W.nested_k25(128, 7, 25.0)
+    op = B.Operator.from_workload(w)
+    X = op.plane_wave_rhs(W.fibonacci_dirs(16)).contiguous()
+    Y = op.apply_batched(X)
+    D = O.Discretisation.from_workload(w)
+    rng = np.random.default_rng(128)
+    rows = np.sort(np.concatenate([rng.choice(w.n_tet, 3, replace=False),
+                                   w.n_tet + rng.choice(w.n_tri, 2, replace=False)]))
+    ref = D.apply_rows(X.cpu().numpy().T, rows)                  # (rows, 16)
+    got = Y.cpu().numpy()[:, rows].T
+    errs = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert errs.max() <= TOL, errs.max()
+    op.close()
