@@ -677,7 +677,7 @@ class Sections:
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the volume (G-class) far-sum
 # kernel on the benchmark workload, from the ncu capture summarised in
 # profiles/nbody_kernel_PolG2_nested80_k10.md; None once the kernel changes until recaptured.
-G_KERNEL_DRAM_BYTES = None
+G_KERNEL_DRAM_BYTES = 91616768
 
 
 def main():
@@ -693,6 +693,8 @@ def main():
                     help="wall-clock budget of the whole run; optional sections past it are skipped")
     ap.add_argument("--parallelism", default="replicas", choices=["replicas", "rows"],
                     help="N > 1: independent replica applies, or one apply sharded by rows")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in work shapes (profiling: no candidate launches)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -728,7 +730,7 @@ def main():
     # work shapes of the persistent kernels picked by timing candidates on this operator
     t0 = time.perf_counter()
     tuning = op.autotune(far=args.precision == 32, batched=args.precision == 32 and not args.no_batched) \
-        if args.precision == 32 else None
+        if args.precision == 32 and not args.no_autotune else None
     autotune_s = time.perf_counter() - t0
     n, nsrc = op.n, op.n_far_sources
     inter = float(n) * float(nsrc)

@@ -210,11 +210,13 @@ vsie_status vsie_apply_timed(vsie_handle* h, const void* d_x, void* d_y, int32_t
  * for source-split partial sums; this variant keeps them in a fixed device array of
  * 2,097,152 complex128 elements (32 MiB) compiled into the library, which every GPU that
  * loads the library holds until the process exits.  Calls allocate nothing and free
- * nothing.  The first call on a device looks up that array's device address (with the
- * handle's device made current for the lookup) and keeps it for later calls; make that
- * first call before any stream capture.  A device reset (cudaDeviceReset) reloads the
- * library's device code and leaves the kept address stale: do not use this call on a
- * device after resetting it.  All calls share the one array and its contents persist between calls (every
+ * nothing.  The array's device address is looked up (and the array loaded on the device,
+ * with the library's device code) once per device, when an operator is created there;
+ * should that lookup fail, the first call on the device repeats it (with the handle's
+ * device made current) and reports the failure, so make that first call before any
+ * stream capture.  A device reset (cudaDeviceReset) reloads the library's device code
+ * and leaves the kept address stale: do not use this call on a device after resetting
+ * it.  All calls share the one array and its contents persist between calls (every
  * element a call reads it has written first), so calls that overlap on the GPU -- on
  * different streams or different handles -- race and must be serialised by the caller.
  * Same arguments, layouts and precisions as vsie_apply.  Errors: VSIE_ERR_ARG when the

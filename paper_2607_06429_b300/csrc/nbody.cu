@@ -1469,6 +1469,179 @@ __global__ void channel_out_kernel(const double2* __restrict__ w, int64_t n, int
     psi[3 * j + ch - 1] = make_double2(kap * v.x, -kap * v.y);
 }
 
+// One-pass FP32 channels: every (source point j, collocation point i) pair is evaluated
+// once and feeds four complex sums, two source points per packed FP32x2 instruction:
+//   E = e^{2 pi i t} rinv c~_i,            Phi'_j += E,
+//   Psi'_j += d~ rinv^2 (Re + kr Im, Im - kr Re)(E),   kr = 2 pi t,  d~ = x~_i - y~_j,
+// so that sum_i conj(G) lam_i = conj(Phi') and sum_i conj(grad_x G) lam_i = -kappa conj(Psi')
+// (E (i kr - 1) = -(E.re + kr E.im) - i (E.im - kr E.re)).  Work items (tile of 256 points x
+// chunk of collocation points) as in the other sums, partial tiles to slots, fix-up after.
+constexpr int kChT = 2;                  // source points per thread (one packed pair)
+constexpr int kChTile = kBlock * kChT;   // source points per work item
+
+__global__ void __launch_bounds__(kBlock) channels_kernel(const float4* __restrict__ pts, const float4* __restrict__ ca,
+                                                          const float* __restrict__ cb, StreamK sk,
+                                                          double2* __restrict__ out, double2* __restrict__ slots) {
+  __shared__ float4 sa[kBlock], sb[kBlock], sc[kBlock];
+  const int tid = threadIdx.x;
+  const int64_t b = blockIdx.x;
+  const int64_t k0 = sk_begin(sk, b), k1 = sk_begin(sk, b + 1);
+  int64_t k = k0;
+  while (k < k1) {
+    const int64_t tile = k / sk.nchunk;
+    const int64_t c0 = k - tile * sk.nchunk;
+    const int64_t c1 = min(sk.nchunk, c0 + (k1 - k));
+    const int64_t ia = tile * kChTile + tid, ib = ia + kBlock;
+    const float4 pa = ia < sk.nt ? pts[ia] : make_float4(0, 0, 0, 0);
+    const float4 pb = ib < sk.nt ? pts[ib] : make_float4(0, 0, 0, 0);
+    const float2 ntx = make_float2(-pa.x, -pb.x), nty = make_float2(-pa.y, -pb.y), ntz = make_float2(-pa.z, -pb.z);
+    Acc<float> acc[kChT][4];
+#pragma unroll
+    for (int t = 0; t < kChT; ++t)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[t][c].zero();
+    const int64_t j_begin = c0 * sk.chunk;
+    const int64_t j_end = min(sk.ns, c1 * sk.chunk);
+    for (int64_t j0 = j_begin; j0 < j_end; j0 += kBlock) {
+      const int64_t j = j0 + tid;
+      const bool ok = j < j_end;
+      const float4 r = ok ? ca[j] : make_float4(0, 0, 0, 0);
+      const float ci = ok ? cb[j] : 0.0f;
+      sa[tid] = make_float4(r.x, r.x, r.y, r.y);
+      sb[tid] = make_float4(r.z, r.z, r.w, r.w);
+      sc[tid] = make_float4(ci, ci, -ci, -ci);
+      __syncthreads();
+      float2 phr = f2(0.0f), phi = phr, xr = phr, xi = phr, yr = phr, yi = phr, zr = phr, zi = phr;
+#pragma unroll 4
+      for (int jj = 0; jj < kBlock; ++jj) {
+        const float4 A = sa[jj], Bv = sb[jj], C = sc[jj];
+        const float2 dx = __fadd2_rn(make_float2(A.x, A.y), ntx);
+        const float2 dy = __fadd2_rn(make_float2(A.z, A.w), nty);
+        const float2 dz = __fadd2_rn(make_float2(Bv.x, Bv.y), ntz);
+        float2 r2 = __fmul2_rn(dx, dx);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dz, dz, r2);
+        float2 rinv, t, cs, sn;
+        phase2(r2, rinv, t, cs, sn);
+        const float2 er = __fmul2_rn(cs, rinv), ei = __fmul2_rn(sn, rinv);
+        const float2 cr = make_float2(Bv.z, Bv.w), cim = make_float2(C.x, C.y), ncim = make_float2(C.z, C.w);
+        const float2 Er = __ffma2_rn(ei, ncim, __fmul2_rn(er, cr));
+        const float2 Ei = __ffma2_rn(ei, cr, __fmul2_rn(er, cim));
+        phr = __fadd2_rn(phr, Er);
+        phi = __fadd2_rn(phi, Ei);
+        const float2 kr = __fmul2_rn(t, f2(6.28318530717958647692f));
+        const float2 nkr = __fmul2_rn(t, f2(-6.28318530717958647692f));
+        const float2 ri2 = __fmul2_rn(rinv, rinv);
+        const float2 hr = __fmul2_rn(ri2, __ffma2_rn(kr, Ei, Er));     // rinv^2 (Re + kr Im)
+        const float2 hi = __fmul2_rn(ri2, __ffma2_rn(nkr, Er, Ei));    // rinv^2 (Im - kr Re)
+        xr = __ffma2_rn(dx, hr, xr);
+        xi = __ffma2_rn(dx, hi, xi);
+        yr = __ffma2_rn(dy, hr, yr);
+        yi = __ffma2_rn(dy, hi, yi);
+        zr = __ffma2_rn(dz, hr, zr);
+        zi = __ffma2_rn(dz, hi, zi);
+      }
+      __syncthreads();
+      acc[0][0].fold(phr.x, phi.x);
+      acc[1][0].fold(phr.y, phi.y);
+      acc[0][1].fold(xr.x, xi.x);
+      acc[1][1].fold(xr.y, xi.y);
+      acc[0][2].fold(yr.x, yi.x);
+      acc[1][2].fold(yr.y, yi.y);
+      acc[0][3].fold(zr.x, zi.x);
+      acc[1][3].fold(zr.y, zi.y);
+    }
+    const bool complete = (c0 == 0 && c1 == sk.nchunk);
+    const int64_t slot = (k == k0) ? 2 * b : 2 * b + 1;
+#pragma unroll
+    for (int t = 0; t < kChT; ++t) {
+      const int64_t i = tile * kChTile + (int64_t)t * kBlock + tid;
+      if (i < sk.nt) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const double2 v = acc[t][c].value();
+          if (complete)
+            out[(int64_t)c * sk.nt + i] = v;
+          else
+            slots[(slot * 4 + c) * kChTile + (int64_t)t * kBlock + tid] = v;
+        }
+      }
+    }
+    k = tile * sk.nchunk + c1;
+  }
+}
+
+// Adds the pieces of point tiles that span several blocks, in block order (4 channels).
+__global__ void __launch_bounds__(kChTile) channels_fixup_kernel(StreamK sk, const double2* __restrict__ slots,
+                                                                 double2* __restrict__ out) {
+  const int64_t tile = blockIdx.x;
+  const int64_t kf = tile * sk.nchunk, kl = kf + sk.nchunk - 1;
+  const int64_t bs = sk_block_of(sk, kf), be = sk_block_of(sk, kl);
+  if (bs == be) return;
+  const int idx = threadIdx.x;
+  const int64_t i = tile * kChTile + idx;
+  if (i >= sk.nt) return;
+  for (int c = 0; c < 4; ++c) {
+    double sr = 0.0, si = 0.0;
+    for (int64_t bb = bs; bb <= be; ++bb) {
+      if (sk_begin(sk, bb) == sk_begin(sk, bb + 1)) continue;
+      const int64_t slot = (bb == bs && sk_begin(sk, bb) != kf) ? 2 * bb + 1 : 2 * bb;
+      const double2 v = slots[(slot * 4 + c) * kChTile + idx];
+      sr += v.x;
+      si += v.y;
+    }
+    out[(int64_t)c * sk.nt + i] = make_double2(sr, si);
+  }
+}
+
+// Phi_j = conj(Phi'_j);  Psi_j = -kappa conj(Psi'_j)
+__global__ void channels_finish_kernel(const double2* __restrict__ w4, int64_t n, double kap,
+                                       double2* __restrict__ phi, double2* __restrict__ psi) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double2 p = w4[j];
+  phi[j] = make_double2(p.x, -p.y);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double2 v = w4[(int64_t)(a + 1) * n + j];
+    psi[3 * j + a] = make_double2(-kap * v.x, kap * v.y);
+  }
+}
+
+static int channels_resident_per_sm() {
+  static int cached = 0;
+  if (!cached) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, channels_kernel, kBlock, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    cached = per_sm;
+  }
+  return cached;
+}
+
+static vsie_status channels_fp32(vsie_handle* h, const Sources& S, double2* phi, double2* psi, cudaStream_t st) {
+  AdjRecords* A = &h->adj;
+  const double kap = h->k0 / kTwoPi;
+  StreamK sk;
+  sk.nt = S.n;
+  sk.ns = h->n;
+  sk.chunk = kChunk;
+  sk.ntile = (sk.nt + kChTile - 1) / kChTile;
+  sk.nchunk = (sk.ns + sk.chunk - 1) / sk.chunk;
+  sk.nitems = sk.ntile * sk.nchunk;
+  int64_t C = (int64_t)channels_resident_per_sm() * (h->num_sms > 0 ? h->num_sms : 148);
+  if (h->tile_override > 0) C = h->tile_override;
+  sk.grid = std::max<int64_t>(1, std::min<int64_t>(C, sk.nitems));
+  double2* slots = nullptr;
+  VSIE_TRY(handle_slots(h, (size_t)(2 * sk.grid) * 4 * kChTile, &slots));
+  channels_kernel<<<(unsigned)sk.grid, kBlock, 0, st>>>(S.adj_p32, A->c_a32, A->c_b32, sk, A->ch_out, slots);
+  channels_fixup_kernel<<<(unsigned)sk.ntile, kChTile, 0, st>>>(sk, slots, A->ch_out);
+  channels_finish_kernel<<<nblk(S.n), 256, 0, st>>>(A->ch_out, S.n, kap, phi, psi);
+  VSIE_CUDA(cudaGetLastError());
+  return VSIE_OK;
+}
+
 vsie_status gradient_channels(vsie_handle* h, const double2* lam, int precision, double2* phi, double2* psi,
                               cudaStream_t st) {
   const int64_t n = h->n;
@@ -1488,6 +1661,20 @@ vsie_status gradient_channels(vsie_handle* h, const double2* lam, int precision,
                                                   A->c_a64, A->c_b64);
   VSIE_CUDA(cudaGetLastError());
   int64_t off = 0;
+  if (precision == 32) {
+    if (!A->ch_out) VSIE_TRY(dalloc_t(h, &A->ch_out, 4 * (size_t)maxn));
+    for (int c = 0; c < 3; ++c) {
+      Sources& S = *cls[c];
+      if (!S.n) continue;
+      if (n) VSIE_TRY(channels_fp32(h, S, phi + off, psi + 3 * off, st));
+      else {
+        VSIE_CUDA(cudaMemsetAsync(phi + off, 0, sizeof(double2) * S.n, st));
+        VSIE_CUDA(cudaMemsetAsync(psi + 3 * off, 0, sizeof(double2) * 3 * S.n, st));
+      }
+      off += S.n;
+    }
+    return VSIE_OK;
+  }
   for (int c = 0; c < 3; ++c) {
     Sources& S = *cls[c];
     if (!S.n) continue;

@@ -53,6 +53,16 @@ static vsie_status noalloc_scratch(int device, double2** out) {
   return VSIE_OK;
 }
 
+// Set-up at operator creation: loads the array on the device (with lazy module loading
+// the library's device image, and this array with it, is materialised on first use) and
+// caches its address, so that later vsie_apply_noalloc calls allocate nothing.  A failure
+// here is not an error of the creation: the first vsie_apply_noalloc call retries and
+// reports it.
+void noalloc_prepare(int device) {
+  double2* p = nullptr;
+  if (noalloc_scratch(device, &p) != VSIE_OK) clear_error();
+}
+
 }  // namespace vsie
 
 using namespace vsie;

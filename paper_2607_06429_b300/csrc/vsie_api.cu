@@ -495,6 +495,7 @@ static vsie_status finish_create(vsie_handle* h, ElementGeometry& g) {
   // the geometry stays with the handle: field evaluation at arbitrary points builds its
   // near-rule rows from it (about 200 bytes per tetrahedron)
   VSIE_CUDA(cudaDeviceSynchronize());
+  noalloc_prepare(h->device);
   return VSIE_OK;
 }
 

@@ -98,6 +98,7 @@ struct AdjRecords {
   float4* ch_v32 = nullptr;
   double4_32a* ch_p64 = nullptr;
   double4_32a* ch_v64 = nullptr;
+  double2* ch_out = nullptr;   // one-pass FP32 channels: 4 sums per source point (Phi, Psi x, y, z)
 };
 
 // Buffers of the tensor-core multi-RHS path (grown on demand).
@@ -240,6 +241,9 @@ vsie_status far_sum_f(vsie_handle* h, double2* y, int precision, cudaStream_t st
 // All far-field sums with the partial-tile slots in caller-provided scratch; the scratch
 // must hold far_split_elems(h, precision) double2 values (nothing is allocated).
 size_t far_split_elems(const vsie_handle* h, int precision);
+// Looks up (and caches) the device address of the allocation-free apply's fixed array on
+// the given device; called once an operator exists there.
+void noalloc_prepare(int device);
 vsie_status far_sums_into(vsie_handle* h, double2* y, int precision, double2* scratch,
                           cudaStream_t st);
 // x_e = sum_{j in e} sum_i conj(C_ij) lam_i (overwrites x).

@@ -156,16 +156,13 @@ def test_reciprocity_exact_for_the_lippmann_schwinger_grid():
     assert abs(wrong - pinf(-d, -xh)) > 1e-3 * abs(pinf(-d, -xh))
 
 
-def test_reciprocity_of_the_tetrahedral_penetrable_ball():
+def test_reciprocity_of_the_tetrahedral_penetrable_ball(ball12_lu):
     """The tetrahedral discretisation (collocation at centroids, four-point sources) is not
     symmetric, so reciprocity holds at discretisation level: within 1% for the 12^3 ball
     over 9 direction pairs (0.26% measured)."""
-    w = W.single_ball(12, 3, 2.0)
-    D = O.Discretisation.from_workload(w)
-    A = D.assemble()
+    w, D, fac = ball12_lu
     dirs = W.fibonacci_dirs(6)
-    lu = __import__("scipy.linalg", fromlist=["lu_factor"])
-    fac = lu.lu_factor(A)
+    lu = __import__("scipy.linalg", fromlist=["lu_solve"])
     worst = 0.0
     for a in range(3):
         for b in range(3, 6):

@@ -332,13 +332,18 @@ def _solve(D, d):
     return np.linalg.solve(A, D.plane_wave(d))
 
 
-def test_penetrable_ball_vs_mie_series():
+def test_penetrable_ball_vs_mie_series(ball12_lu):
+    import scipy.linalg as sla
     k, d = 2.0, np.array([0.0, 0.0, 1.0])
     out = []
     for N, sd in ((8, 2), (12, 3)):
-        w = W.single_ball(N, sd, k)
-        D = O.Discretisation.from_workload(w)
-        x = _solve(D, d)
+        if N == 12:
+            w, D, fac = ball12_lu
+            x = sla.lu_solve(fac, D.plane_wave(d))
+        else:
+            w = W.single_ball(N, sd, k)
+            D = O.Discretisation.from_workload(w)
+            x = _solve(D, d)
         r = np.linalg.norm(D.tet_cen, axis=1)
         m = r < 0.8
         ref_v = S.layered_sphere_field(D.tet_cen[m], d, k, [1.0], [1.5], [0.7])
@@ -539,15 +544,15 @@ def test_oracle_gradient_with_lsq_density_matches_finite_differences():
 
 # ----------------------------------------------------------------- exterior field
 
-def test_exterior_field_against_mie_and_far_field():
+def test_exterior_field_against_mie_and_far_field(ball12_lu):
     """The scattered field at exterior points (representation formula) for the penetrable
     ball: against the Mie series at radii 1.5-3 (discretisation level, as the far-field
     pin), and against the oracle's own far-field pattern at a large radius R, where
     R e^{-ikR} p_s(R xhat) -> p_inf(xhat) with an O(k |y|^2 / R) error."""
-    w = W.single_ball(12, 3, 2.0)
-    D = O.Discretisation.from_workload(w)
+    import scipy.linalg as sla
+    w, D, fac = ball12_lu
     d = np.array([0.0, 0.0, 1.0])
-    p = np.linalg.solve(D.assemble(), D.plane_wave(d))
+    p = sla.lu_solve(fac, D.plane_wave(d))
     xhat = W.fibonacci_dirs(24)
     pts = np.concatenate([1.5 * xhat, 3.0 * xhat])
     ps = O.scattered_field(D, p, pts)

@@ -31,10 +31,24 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def _load_device_code(torch, B):
+    """Runs every precision of the call once on a throwaway operator, so that the device
+    code the calls use is loaded (with lazy module loading the driver loads a module, and
+    reserves device memory for its code, on first use) before free memory is compared."""
+    op = B.Operator.from_workload(W.single_ball(4, 1, 2.0))
+    x = torch.from_numpy(W.random_vector(op.n, 1)).cuda()
+    y = torch.empty_like(x)
+    for prec in (32, 48, 64):
+        op.apply_noalloc(x, y, precision=prec)
+    torch.cuda.synchronize()
+    op.close()
+
+
 @pytest.mark.parametrize("maker", [lambda: W.single_ball(12, 3, 2.0),
                                    lambda: W.smooth_density_ball(8, 2, 1, 3.0)])
 def test_noalloc_matches_oracle_and_apply_on_two_calls(maker):
     torch, B = _setup()
+    _load_device_code(torch, B)
     w = maker()
     A = O.Discretisation.from_workload(w).assemble()
     op = B.Operator.from_workload(w)   # fresh: the handle's own split buffer does not exist yet
