@@ -303,7 +303,14 @@ def row_sample_apply_seconds(torch, op, x, precision, rows):
     return dt * op.n / rows, {"rows": rows, "seconds": dt}
 
 
-def solve_headline(torch, op, t32_s, tol=1e-5):
+def sampled_residual(D, b, x, rows):
+    """||b - A x|| / ||b|| over the given rows, with A from the oracle (rows independent)."""
+    rows = np.asarray(rows)
+    r = b[rows] - D.apply_rows(x, rows)
+    return float(np.linalg.norm(r) / np.linalg.norm(b[rows]))
+
+
+def solve_headline(torch, op, t32_s, tol=1e-5, D=None):
     """Time-to-solution on the benchmark mesh (Sec. 3.1 settings: x0 = 0, no restart, no
     preconditioner, plane wave along +x) at the paper's GMRES tolerance: the mixed solve
     measured (FP32-apply GMRES, its final residual formed with the double-float apply), the
@@ -316,6 +323,11 @@ def solve_headline(torch, op, t32_s, tol=1e-5):
                                                    max_refinements=4, raise_on_fail=False))
     mixed = _info(info, dt)
     mixed["status"] = info.status
+    if D is not None:
+        with one_thread():
+            rows = np.sort(np.random.default_rng(11).choice(op.n, size=32, replace=False))
+            mixed["rel_residual_oracle_rows"] = sampled_residual(D, b.cpu().numpy(), x.cpu().numpy(), rows)
+            mixed["oracle_rows"] = 32
     overhead = max(0.0, dt - info.fp32_applies * t32_s - info.fp64_applies * t48)
     fp64 = overhead + (info.iterations + 1) * t64
     return {"workload": "nested80_k10", "n": op.n, "tol": tol, "mixed": mixed,
@@ -366,10 +378,18 @@ def solve_timing(torch, B, W, name="nested24_k10", tol=1e-8, fp64_tol8=True):
                                                             inner_tol=1e-4, max_refinements=20))
     r = B64 - op.apply_batched(X, precision=64)
     worst = float((torch.linalg.norm(r, dim=1) / torch.linalg.norm(B64, dim=1)).max())
+    # the same residuals with the oracle's rows (4 columns x 64 seeded rows)
+    from oracle import vsie_oracle as O
+    D = O.Discretisation.from_workload(w)
+    rows = np.sort(np.random.default_rng(24).choice(op.n, size=64, replace=False))
+    Bh, Xh = B64.cpu().numpy(), X.cpu().numpy()
+    with one_thread():
+        worst_o = max(sampled_residual(D, Bh[c], Xh[c], rows) for c in (0, 21, 42, 63))
     its = [i.iterations for i in infos]
     out["batched_mixed"] = {
         "nrhs": nb, "seconds": dt, "seconds_per_rhs": dt / nb,
-        "max_rel_residual_fp64": worst, "iterations_mean": float(np.mean(its)), "iterations_max": max(its),
+        "max_rel_residual_fp64": worst, "max_rel_residual_oracle_rows": worst_o,
+        "iterations_mean": float(np.mean(its)), "iterations_max": max(its),
         "refinements_max": max(i.refinements for i in infos),
         "speedup_per_rhs_vs_mixed_single": out["mixed"]["seconds"] / (dt / nb)}
     if fp64_tol8:
@@ -526,6 +546,32 @@ def cuboid_timing(torch, B, W, N=91, steps=2):
             "rel_err_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
             "oracle_interactions_per_s": len(rows) * op.n_far_sources / dt,
             "oracle_sample": f"{len(rows)} seeded rows (FP64 numpy, 1 thread)"}
+
+
+def large_timing(torch, B, W, nrhs=16):
+    """The large workload (128^3 grid, k0 = 25, 7,250,176 unknowns, 8,560,896 far-field
+    source points) with 16 plane waves: one timed tensor-core multi-RHS apply, the FP32
+    single-column and double-float apply rates from row samples (rows carry equal work),
+    and the cost of a refined solve per GMRES iteration that follows from them."""
+    w = W.nested_k25(128, 7, 25.0)
+    t0 = time.perf_counter()
+    op = B.Operator.from_workload(w)
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    X = op.plane_wave_rhs(W.fibonacci_dirs(nrhs)).contiguous()
+    Y = torch.empty_like(X)
+    (_, dt) = _timed(torch, lambda: op.apply_batched(X, Y))
+    t32, s32 = row_sample_apply_seconds(torch, op, X[0].contiguous(), 32, 65536)
+    t48, s48 = row_sample_apply_seconds(torch, op, X[0].contiguous(), 48, 4096)
+    pairs = float(op.n) * float(op.n_far_sources)
+    out = {"workload": "nested128_k25", "n": op.n, "n_far_sources": op.n_far_sources, "nrhs": nrhs,
+           "create_s": create_s, "batched_seconds": dt, "batched_interactions_per_s": pairs * nrhs / dt,
+           "fp32_apply_seconds_from_rows": t32, "double_float_apply_seconds_from_rows": t48,
+           "row_samples": {"32": s32, "48": s48},
+           "per_iteration_seconds": {"batched_16_rhs": dt, "16_single_column_fp32": 16 * t32},
+           "refined_solve_seconds": "iterations x batched_seconds + refinements x 16 x double-float apply"}
+    op.close()
+    return out
 
 
 def field_points(m, seed=5):
@@ -701,6 +747,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the cuboid-grid apply, exterior-field and adjoint timings")
     ap.add_argument("--multifreq-mesh", default="auto", choices=["auto", "nested24_k10", "nested80_k10", "none"])
+    ap.add_argument("--large", action="store_true",
+                    help="also time the k0 = 25, 128^3 workload's 16-RHS apply (about 5 minutes)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -855,7 +903,8 @@ def main():
 
     solve80 = None
     if not args.no_solve and args.precision == 32 and args.workload == WORKLOAD:
-        solve80 = sec.run("solve_nested80", lambda: solve_headline(torch, op, t_ms * 1e-3), estimate_s=450)
+        D80 = oracle_of(w) if (world == 1 and not args.no_cpu_baseline) else None
+        solve80 = sec.run("solve_nested80", lambda: solve_headline(torch, op, t_ms * 1e-3, D=D80), estimate_s=450)
 
     batched = None
     if not args.no_batched and args.precision == 32:
@@ -887,6 +936,10 @@ def main():
         multifreq = sec.run("multifreq", lambda: multifreq_timing(
             torch, B, W, mesh=mesh, steps=1 if mesh == "nested80_k10" else 2), estimate_s=30)
 
+    large = None
+    if args.large and args.precision == 32:
+        large = sec.run("large", lambda: large_timing(torch, B, W), estimate_s=300)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True,
@@ -908,6 +961,7 @@ def main():
         "solve": {"nested80_k10": solve80, "nested24_k10": solve24},
         "batched": batched,
         "multifreq": multifreq,
+        "large": large,
         "extras": extras,
         "cpu_baseline": cpu,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},

@@ -17,9 +17,9 @@
 //     [Y_re | Y_im] += C_re [Q_re | Q_im] + C_im [-Q_im | Q_re],
 // the second with the instruction descriptor's negate-B bit applied to [Q_im | -Q_re].
 //
-// Layout.  One CTA (16 evaluating warps + 1 issuing warp, one CTA per SM) owns a tile of
-// 128 targets (the MMA M) and streams the sources in tiles of 32 (the MMA K is 8, four
-// k-steps per tile).
+// Layout.  One CTA (16 evaluating warps, an MMA warp and a copy warp; one CTA per SM) owns
+// a tile of 128 targets (the MMA M) and streams the sources in tiles of 32 (the MMA K is
+// 8, four k-steps per tile).
 //   * A operand (128 x 32 each): C_re and C_im, hi and lo, written straight into tensor
 //     memory by the evaluating warps (tcgen05.st) once the previous tile's MMAs retired;
 //   * B operands (64 x 32 per block, K-major, no swizzle, 8 x 16-byte core matrices):
@@ -33,7 +33,12 @@
 //     sum H: all 512 tensor-memory columns, allocated by warp 0.
 // Pipeline: four stages of charge images in shared memory (the copy engine runs up to
 // three tiles ahead of the tensor cores) while the CUDA cores evaluate the next tile.
-// Keeping A out of shared memory leaves its bandwidth to the B operand reads.  Work is
+// Keeping A out of shared memory leaves its bandwidth to the B operand reads (a variant
+// with a double-buffered A in shared memory ran 1.6x slower: the tensor cores' operand
+// reads doubled and only two image stages fitted).  Each tcgen05.mma of 128 x 128 x 8 TF32
+// occupies the issuing thread for about as long as the tensor pipe takes to execute it,
+// so the MMA thread has a warp of its own, and so have the bulk copies, whose issue can
+// also block.  Work is
 // split over the CTAs with the same balanced item ranges (target tile, 2048-source chunk)
 // and deterministic fix-up as the single-RHS sums.  Every wait on an mbarrier is bounded
 // (2 s of wall time); on expiry the kernel records an error code, stops issuing work,
@@ -116,6 +121,17 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  {
+    // fast path: a phase that has already completed is seen by a non-blocking test (the
+    // blocking try_wait costs about 150 cycles even then)
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
   uint64_t t0 = 0;
   for (uint32_t it = 0;; ++it) {
     uint32_t ok;
@@ -224,17 +240,18 @@ struct BatchArgs {
   int mode;                 // 0 store, 1 add
   double* slots;            // [2 grid][2][BT_R][BT_M] FP64 partial target tiles for the fix-up
   int* status;              // nonzero on a timed-out wait
-  int withhold_copies;      // failure-path test: the issuing warp never starts the copies
+  int withhold_copies;      // failure-path test: the copy warp never starts the copies
 };
 
 __device__ __forceinline__ int64_t bt_begin(const BatchArgs& a, int64_t b) { return (b * a.nitems) / a.grid; }
 
 // Warp roles: warps 0-15 (512 threads) evaluate the kernel tile and fold the tensor
-// accumulator; warp 16 issues the bulk copies and, from one lane, the MMAs.  They meet
-// only through mbarriers (a_full for the A operand; b_full, mma_done per image stage;
-// d_ready per accumulator buffer), so evaluation, copies and tensor-core work overlap.
+// accumulator; warp 16 issues the MMAs from one lane; warp 17 issues the bulk copies.
+// They meet only through mbarriers (a_full for the A operand; b_full, mma_done per image
+// stage; d_ready per accumulator buffer), so evaluation, copies and tensor-core work
+// overlap.
 constexpr int BT_EVAL_THREADS = 512;
-constexpr int BT_ALL_THREADS = BT_EVAL_THREADS + 32;
+constexpr int BT_ALL_THREADS = BT_EVAL_THREADS + 64;
 
 #define BT_LD8(addr, v)                                                                               \
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"                  \
@@ -281,47 +298,26 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
 
   // The CTA's items [k0, k1) form segments: runs of consecutive chunks of one target tile.
   // Both roles walk the same sequence of source tiles; g counts them over the whole range.
-  if (warp == BT_EVAL_THREADS / 32) {
-    // ------------------------------------------------------------ issuing warp
+  if (warp == BT_EVAL_THREADS / 32 + 1) {
+    // ------------------------------------------------------------ copy warp
+    // Streams the tiles' charge images into the stages, NB - 1 tiles ahead of the MMAs at
+    // most: stage gp % NB is refilled once the MMAs of tile gp - NB, its last reader, have
+    // retired.  A bulk copy can block its issuing thread while the copy engine is busy, so
+    // it has a warp of its own rather than sharing the MMA thread.
     if (lane == 0) {
-      // copy cursor (runs up to NB - 1 tiles ahead of the MMA cursor)
-      int64_t pk = k0, ps = 0, pend = 0;
-      bool pstarted = false, pdone = false;
-      const unsigned char* pimg = nullptr;  // images of the current item's operator
-      auto pitem = [&]() {
-        ps = (pk % a.nchunk) * a.chunk_tiles;
-        pend = min(a.ntiles_src, ps + a.chunk_tiles);
-        pimg = a.img[(pk / a.nchunk) / a.ntile_t];
-      };
-      auto pnext = [&]() -> int64_t {
-        if (!pstarted) {
-          pstarted = true;
-          if (pk >= k1) return -1;
-          pitem();
-          return ps;
-        }
-        if (pk >= k1) return -1;
-        if (++ps < pend) return ps;
-        if (++pk >= k1) return -1;
-        pitem();
-        return ps;
-      };
-      uint32_t gp = 0;  // copies issued
-      auto refill = [&](uint32_t g_limit) {
-        // issue copies for tiles gp < g_limit; image stage gp % NB was last read by tile gp - NB
-        while (!pdone && gp < g_limit && !err) {
-          const int64_t s_next = pnext();
-          if (s_next < 0) {
-            pdone = true;
-            break;
-          }
+      uint32_t gp = 0;
+      for (int64_t k = k0; k < k1 && !err;) {
+        const int64_t tile = k / a.nchunk;
+        const int64_t c0 = k - tile * a.nchunk;
+        const int64_t c1 = min(a.nchunk, c0 + (k1 - k));
+        const int64_t s_begin = c0 * a.chunk_tiles, s_end = min(a.ntiles_src, c1 * a.chunk_tiles);
+        const unsigned char* pimg = a.img[tile / a.ntile_t];
+        for (int64_t s = s_begin; s < s_end && !err; ++s, ++gp) {
           const int st2 = gp % BT_NB;
           if (gp >= BT_NB) err = !mbar_wait(mma_done + st2, ((gp - BT_NB) / BT_NB) & 1);
-          if (err) break;
+          if (err || a.withhold_copies) continue;
           unsigned char* bimg = smem + BT_B_OFF + st2 * BT_SIMG;
-          const unsigned char* gimg = pimg + s_next * (int64_t)BT_IMG;
-          ++gp;
-          if (a.withhold_copies) continue;
+          const unsigned char* gimg = pimg + s * (int64_t)BT_IMG;
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b_full + st2)),
                        "r"(BT_IMG)
                        : "memory");
@@ -337,8 +333,19 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
               "l"(gimg + BT_HDR + 2 * BT_B_MAT), "r"(2 * BT_B_MAT), "r"(su32(b_full + st2))
               : "memory");
         }
-      };
-      refill(BT_NB - 1);
+        k = tile * a.nchunk + c1;
+      }
+      // before the CTA exits (and its shared memory goes away) every issued copy must have
+      // landed; the last NB tiles' copies are the ones possibly in flight
+      const bool err_wait = err;
+      if (!a.withhold_copies)
+        for (uint32_t t = gp > BT_NB ? gp - BT_NB : 0; t < gp; ++t)
+          if (!mbar_wait(b_full + t % BT_NB, (t / BT_NB) & 1)) err = true;
+      if (err || err_wait) atomicExch(a.status, 1);
+    }
+  } else if (warp == BT_EVAL_THREADS / 32) {
+    // ------------------------------------------------------------ MMA warp
+    if (lane == 0) {
       uint32_t g = 0;
       for (int64_t k = k0; k < k1 && !err;) {
         const int64_t tile = k / a.nchunk;
@@ -379,16 +386,12 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            su32(mma_done + sb))
                        : "memory");
-          refill(g + BT_NB);
         }
         k = tile * a.nchunk + c1;
       }
-      // before the CTA exits (and its shared and tensor memory go away): copies still in
-      // flight and the last MMAs must have landed (only the error path leaves any)
+      // before the CTA exits (and its tensor memory goes away) the last MMAs must have
+      // retired
       const bool err_wait = err;
-      if (!a.withhold_copies)
-        for (uint32_t t = g; t < gp; ++t)
-          if (!mbar_wait(b_full + t % BT_NB, (t / BT_NB) & 1)) err = true;
       if (g > 0 && !mbar_wait(mma_done + (g - 1) % BT_NB, ((g - 1) / BT_NB) & 1)) err = true;
       if (err || err_wait) atomicExch(a.status, 1);
     }
