@@ -198,7 +198,9 @@ vsie_status vsie_apply_rows(vsie_handle* h, const void* d_x, void* d_y, int64_t 
  * blocks until done.  kernel_ms[4] receives the device time of: the charge prescale, the
  * far-field sum over volume sources without a vector weight, the far-field sum over
  * sources with a vector weight (interfaces, heterogeneous density), and the correction
- * + mass kernel.  *launches (optional) receives the number of kernels launched. */
+ * + mass kernel.  The phases run one after the other here even where vsie_apply runs the
+ * G and K sums concurrently (vsie_set_tuning, vsie_autotune).  *launches (optional)
+ * receives the number of kernels one vsie_apply launches with the work shapes in use. */
 vsie_status vsie_apply_timed(vsie_handle* h, const void* d_x, void* d_y, int32_t precision,
                              void* stream, double* kernel_ms, int32_t* launches);
 
@@ -244,7 +246,10 @@ vsie_status vsie_apply_batched(vsie_handle* h, const void* d_x, void* d_y, int32
 /* Autotuning of the work shapes (the target-tile x source-chunk items of the persistent
  * kernels) on this operator.  flags bit 0: the FP32 far-field sums of vsie_apply (sources
  * per work item in {512, 1024, 2048, 4096} x resident blocks per SM in {max, 3/4 max,
- * max/2}, per source class); bit 1: the tensor-core sums of vsie_apply_batched (32-source
+ * max/2}, per source class; then whether the volume (G) and interface (K) sums run one
+ * after the other or concurrently on two streams, each with part of every SM's resident
+ * blocks, so that the MUFU-bound G sum and the FMA-bound K sum share the SMs' pipes);
+ * bit 1: the tensor-core sums of vsie_apply_batched (32-source
  * tiles per work item in {16, 32, 64, 128}).  Each candidate is timed (CUDA events, best
  * of two runs after a warm-up) on a sample of the targets sized to a few tens of
  * milliseconds, with pseudo-random charges; the fastest is kept in the handle and used
@@ -260,8 +265,28 @@ typedef struct {
   double batch_ms;               /* chosen, ms for G + K on the tuning sample (64 columns) */
   double batch_default_ms;       /* built-in default (64 tiles) */
   int32_t candidates;            /* configurations timed */
+  int32_t gk_blocks_per_sm[2];   /* G and K sums run concurrently with these blocks per SM
+                                    each; 0, 0: one after the other (bit 0) */
+  double gk_ms;                  /* chosen, ms for G + K on the tuning sample */
+  double gk_sequential_ms;       /* G then K with their tuned shapes, same sample */
 } vsie_tuning;
 vsie_status vsie_autotune(vsie_handle* h, int32_t flags, vsie_tuning* report, void* stream);
+
+/* The work shapes in use (times zero): the fields vsie_set_tuning reads, 0 where the
+ * built-in default applies.  Errors: VSIE_ERR_ARG for a null argument. */
+vsie_status vsie_get_tuning(const vsie_handle* h, vsie_tuning* tuning);
+
+/* Sets the work shapes without timing them, e.g. those an earlier vsie_autotune chose for the
+ * same mesh (read back with vsie_get_tuning): far_chunk (0 or a multiple of 128, at most
+ * 2^20) and far_blocks_per_sm (0..64, clamped to the kernel's occupancy) per class,
+ * batch_chunk_tiles (0..65536) and gk_blocks_per_sm (both 0: the G and K sums one after
+ * the other; both >= 1: concurrently with that many blocks per SM each); 0 selects the
+ * built-in default; the time fields are ignored.  Allocates the concurrent sums' buffers (a
+ * second stream, two events, n complex128 values and split slots) the first time they are
+ * chosen; blocking only for those allocations.  Results change only by the summation order.
+ * Errors: VSIE_ERR_ARG for a null argument or a value out of range (the handle unchanged);
+ * VSIE_ERR_CUDA if an allocation fails. */
+vsie_status vsie_set_tuning(vsie_handle* h, const vsie_tuning* tuning);
 
 /* The precision-32 vsie_apply_batched of nop operators at once, operator p applied to its
  * own block d_x[p] -> d_y[p] (each n x nrhs): the persistent tensor-core launch of each

@@ -28,7 +28,7 @@ EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_appl
            "vsie_adjoint_apply", "vsie_plane_wave_rhs", "vsie_far_field", "vsie_solve",
            "vsie_far_field_adjoint", "vsie_solve_batched", "vsie_apply_batched_multi",
            "vsie_graph_create_batched", "vsie_graph_launch", "vsie_graph_nodes", "vsie_graph_destroy",
-           "vsie_autotune", "vsie_gradient_channels", "vsie_source_points",
+           "vsie_autotune", "vsie_get_tuning", "vsie_set_tuning", "vsie_gradient_channels", "vsie_source_points",
            "vsie_lsq_grad_alpha", "vsie_lsq_grad_alpha_adjoint", "vsie_scattered_field",
            "vsie_create_cuboid", "vsie_set_frequency", "vsie_cuboid_faces", "vsie_apply_rows",
            "vsie_pipe_probe", "vsie_last_error")
@@ -75,7 +75,9 @@ class _Tuning(ctypes.Structure):
     _fields_ = [("far_chunk", ctypes.c_int32 * 3), ("far_blocks_per_sm", ctypes.c_int32 * 3),
                 ("far_ms", ctypes.c_double * 3), ("far_default_ms", ctypes.c_double * 3),
                 ("batch_chunk_tiles", ctypes.c_int32), ("batch_ms", ctypes.c_double),
-                ("batch_default_ms", ctypes.c_double), ("candidates", ctypes.c_int32)]
+                ("batch_default_ms", ctypes.c_double), ("candidates", ctypes.c_int32),
+                ("gk_blocks_per_sm", ctypes.c_int32 * 2), ("gk_ms", ctypes.c_double),
+                ("gk_sequential_ms", ctypes.c_double)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -136,6 +138,8 @@ def load_library(path: str = LIB_PATH):
                                               I32, ctypes.POINTER(P)]
     lib.vsie_graph_launch.argtypes = [P, P]
     lib.vsie_autotune.argtypes = [P, I32, ctypes.POINTER(_Tuning), P]
+    lib.vsie_get_tuning.argtypes = [P, ctypes.POINTER(_Tuning)]
+    lib.vsie_set_tuning.argtypes = [P, ctypes.POINTER(_Tuning)]
     lib.vsie_gradient_channels.argtypes = [P, P, I32, P, P, P]
     lib.vsie_source_points.argtypes = [P, P, P, P]
     lib.vsie_lsq_grad_alpha.argtypes = [ctypes.POINTER(_Mesh), P, P, P]
@@ -325,6 +329,25 @@ class Operator:
                                            _dev(psi, "psi"), _stream(stream)))
         return phi, psi
 
+    def get_tuning(self):
+        """The work shapes in use (vsie_get_tuning), 0 where the built-in default applies."""
+        t = _Tuning()
+        _check(_lib.vsie_get_tuning(self._h, ctypes.byref(t)))
+        return {"far_chunk": list(t.far_chunk), "far_blocks_per_sm": list(t.far_blocks_per_sm),
+                "batch_chunk_tiles": t.batch_chunk_tiles, "gk_blocks_per_sm": list(t.gk_blocks_per_sm)}
+
+    def set_tuning(self, far_chunk=(0, 0, 0), far_blocks_per_sm=(0, 0, 0), batch_chunk_tiles=0,
+                   gk_blocks_per_sm=(0, 0)):
+        """Set the work shapes without timing them (vsie_set_tuning); takes get_tuning()'s
+        keys."""
+        t = _Tuning()
+        for i in range(3):
+            t.far_chunk[i] = int(far_chunk[i])
+            t.far_blocks_per_sm[i] = int(far_blocks_per_sm[i])
+        t.batch_chunk_tiles = int(batch_chunk_tiles)
+        t.gk_blocks_per_sm[0], t.gk_blocks_per_sm[1] = (int(v) for v in gk_blocks_per_sm)
+        _check(_lib.vsie_set_tuning(self._h, ctypes.byref(t)))
+
     def autotune(self, far=True, batched=True, stream=None):
         """Time candidate work shapes on this operator and keep the fastest (vsie_autotune);
         returns the report as a dict."""
@@ -335,6 +358,8 @@ class Operator:
         return {"far": {c: {"chunk": t.far_chunk[i], "blocks_per_sm": t.far_blocks_per_sm[i],
                             "ms": t.far_ms[i], "default_ms": t.far_default_ms[i]}
                         for i, c in enumerate(cls) if t.far_chunk[i]} if far else None,
+                "concurrent_gk": {"blocks_per_sm": list(t.gk_blocks_per_sm), "ms": t.gk_ms,
+                                  "sequential_ms": t.gk_sequential_ms} if far else None,
                 "batched": {"chunk_tiles": t.batch_chunk_tiles, "ms": t.batch_ms,
                             "default_ms": t.batch_default_ms} if batched else None,
                 "candidates": t.candidates}

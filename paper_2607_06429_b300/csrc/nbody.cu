@@ -1180,8 +1180,64 @@ static vsie_status forward_sums_df(vsie_handle* h, double2* y, const ForwardPlan
   return VSIE_OK;
 }
 
+// y[i] += z[i], i < n (the concurrent K sum's output joined into y).
+__global__ void add_into_kernel(double2* __restrict__ y, const double2* __restrict__ z, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double2 a = y[i], b = z[i];
+    y[i] = make_double2(a.x + b.x, a.y + b.y);
+  }
+}
+
+// The FP32 volume (G) and interface (K) sums over the first nt targets at the same time,
+// with gbps and kbps resident blocks per SM: G stores into y on st while K stores into
+// h->gk_y on the handle's second stream, forked from st and joined back into it with events
+// (so the pair is captured into a CUDA graph like any other launch sequence); the
+// heterogeneous-volume sum (F, with_f) follows G on st, and y += gk_y after the join.  The G tiles
+// are bound by the MUFU pipe and the K tiles by the FMA pipe, so blocks of both on one SM
+// keep both pipes busy.  slots: G's and F's split slots; K's are h->gk_split.
+static vsie_status gk_concurrent(vsie_handle* h, const PolG2& pg, const PolK2& pk, int64_t nt, int gbps, int kbps,
+                                 bool with_f, double2* y, double2* slots, cudaStream_t st, int* launches) {
+  const StreamK g = plan_sk<float, PolG2>(h, nt, h->G.n, 0, 0, gbps);
+  const StreamK k = plan_sk<float, PolK2>(h, nt, h->K.n, 1, 0, kbps);
+  VSIE_CUDA(cudaEventRecord(h->gk_fork, st));
+  VSIE_CUDA(cudaStreamWaitEvent(h->gk_stream, h->gk_fork, 0));
+  VSIE_TRY((run_nbody<float, PolG2>(pg, g, y, 0, slots, st, launches)));
+  VSIE_TRY((run_nbody<float, PolK2>(pk, k, h->gk_y, 0, h->gk_split, h->gk_stream, launches)));
+  VSIE_CUDA(cudaEventRecord(h->gk_join, h->gk_stream));
+  if (with_f && h->F.n) {
+    const StreamK f = plan_sk<float, PerTarget<float, PolF<float>>>(h, nt, h->F.n, 2);
+    VSIE_TRY((run_nbody<float, PerTarget<float, PolF<float>>>(make_f<float>(h), f, y, 1, slots, st, launches)));
+  }
+  VSIE_CUDA(cudaStreamWaitEvent(st, h->gk_join, 0));
+  add_into_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(y, h->gk_y, nt);
+  VSIE_CUDA(cudaGetLastError());
+  if (launches) *launches += 1;
+  return VSIE_OK;
+}
+
+// Slots the concurrent sums need on the main stream (G's with gbps blocks per SM, F's).
+static size_t gk_main_slots(const vsie_handle* h, int64_t nt, int gbps) {
+  size_t e = slot_elems(plan_sk<float, PolG2>(h, nt, h->G.n, 0, 0, gbps));
+  if (h->F.n) e = std::max(e, slot_elems(plan_sk<float, PerTarget<float, PolF<float>>>(h, nt, h->F.n, 2)));
+  return e;
+}
+
+// True when the autotuner chose the concurrent sums and their buffers are in place.
+static bool gk_ready(const vsie_handle* h) {
+  return h->tune.gk_bps[0] > 0 && h->tune.gk_bps[1] > 0 && h->G.n && h->K.n && h->gk_stream && h->gk_y &&
+         h->gk_y_n >= h->n &&
+         h->gk_split_elems >= slot_elems(plan_sk<float, PolK2>(h, h->n, h->K.n, 1, 0, h->tune.gk_bps[1]));
+}
+
 static vsie_status forward(vsie_handle* h, double2* y, int precision, double2* slots_given,
                            cudaStream_t st, int phase_mask, int* launches) {
+  if (precision == 32 && phase_mask == 7 && !slots_given && gk_ready(h)) {
+    double2* slots = nullptr;
+    VSIE_TRY(handle_slots(h, gk_main_slots(h, h->n, h->tune.gk_bps[0]), &slots));
+    return gk_concurrent(h, make_g<float>(h), make_k<float>(h), h->n, h->tune.gk_bps[0], h->tune.gk_bps[1], true,
+                         y, slots, st, launches);
+  }
   const ForwardPlans P = forward_plans(h, precision);
   double2* slots = slots_given;
   if (!slots) VSIE_TRY(handle_slots(h, P.slots, &slots));
@@ -1326,6 +1382,115 @@ vsie_status far_autotune(vsie_handle* h, const double2* x, double2* scratch, cud
     cand_out[cls][1] = best_bps;
     ms_out[cls][0] = best;
     ms_out[cls][1] = dflt;
+  }
+  return VSIE_OK;
+}
+
+// The second stream, the fork/join events, K's output (n values) and K's split slots of the
+// concurrent G and K sums, sized for any split, and G's slots: created once per handle, here
+// only, so that an apply never allocates for them.
+static vsie_status gk_resources(vsie_handle* h) {
+  const int maxg = resident_per_sm<float, PolG2>(), maxk = resident_per_sm<float, PolK2>();
+  if (!h->gk_stream) VSIE_CUDA(cudaStreamCreateWithFlags(&h->gk_stream, cudaStreamNonBlocking));
+  if (!h->gk_fork) VSIE_CUDA(cudaEventCreateWithFlags(&h->gk_fork, cudaEventDisableTiming));
+  if (!h->gk_join) VSIE_CUDA(cudaEventCreateWithFlags(&h->gk_join, cudaEventDisableTiming));
+  if (h->gk_y_n < h->n) {
+    VSIE_TRY(dalloc_t(h, &h->gk_y, (size_t)h->n));
+    h->gk_y_n = h->n;
+  }
+  const size_t kslots = slot_elems(plan_sk<float, PolK2>(h, h->n, h->K.n, 1, 0, maxk));
+  if (h->gk_split_elems < kslots) {
+    VSIE_TRY(dalloc_t(h, &h->gk_split, kslots));
+    h->gk_split_elems = kslots;
+  }
+  double2* slots = nullptr;
+  return handle_slots(h, std::max(gk_main_slots(h, h->n, maxg), forward_plans(h, 32).slots), &slots);
+}
+
+int far_gk_extra_launches(const vsie_handle* h, int precision) {
+  return precision == 32 && gk_ready(h) ? 1 : 0;
+}
+
+vsie_status far_set_gk(vsie_handle* h, int gbps, int kbps) {
+  h->tune.gk_bps[0] = h->tune.gk_bps[1] = 0;
+  if (gbps <= 0 || kbps <= 0 || !h->G.n || !h->K.n) return VSIE_OK;
+  VSIE_TRY(gk_resources(h));
+  h->tune.gk_bps[0] = std::min(gbps, resident_per_sm<float, PolG2>());
+  h->tune.gk_bps[1] = std::min(kbps, resident_per_sm<float, PolK2>());
+  return VSIE_OK;
+}
+
+// Times the FP32 G and K sums (records prescaled by far_autotune) one after the other with
+// their tuned shapes, and concurrently for every split of the resident blocks per SM
+// between them; keeps the concurrent split if it is at least 2% faster.  The second stream,
+// the events, K's output (n values) and K's slots are created here, the only place they
+// are allocated, so that an apply never allocates for them.
+vsie_status far_autotune_gk(vsie_handle* h, const double2* x, double2* scratch, cudaStream_t st, int out_bps[2],
+                            double out_ms[2], int* candidates) {
+  out_bps[0] = out_bps[1] = 0;
+  out_ms[0] = out_ms[1] = 0.0;
+  h->tune.gk_bps[0] = h->tune.gk_bps[1] = 0;
+  if (!h->G.n || !h->K.n || !h->n) return VSIE_OK;
+  VSIE_TRY(far_prescale(h, x, 32, st, nullptr));
+  const int maxg = resident_per_sm<float, PolG2>(), maxk = resident_per_sm<float, PolK2>();
+  if (maxg < 2 || maxk < 2) return VSIE_OK;
+  VSIE_TRY(gk_resources(h));
+  const int64_t want = std::max<int64_t>((int64_t)kTile * 2 * std::max(h->num_sms, 1),
+                                         (int64_t)(4e10 / (double)(h->G.n + h->K.n)));
+  const int64_t nt = std::min<int64_t>(h->n, want);
+  double2* slots = h->split;
+  const PolG2 pg = make_g<float>(h);
+  const PolK2 pk = make_k<float>(h);
+  cudaEvent_t e0, e1;
+  VSIE_CUDA(cudaEventCreate(&e0));
+  VSIE_CUDA(cudaEventCreate(&e1));
+  // gbps == 0: sequential (G then K, tuned shapes)
+  auto time_one = [&](int gbps, int kbps, float* best_ms) -> vsie_status {
+    float best = 1e30f;
+    for (int r = 0; r <= 2; ++r) {
+      VSIE_CUDA(cudaEventRecord(e0, st));
+      if (gbps == 0) {
+        VSIE_TRY((run_nbody<float, PolG2>(pg, plan_sk<float, PolG2>(h, nt, h->G.n, 0), scratch, 0, slots, st,
+                                          nullptr)));
+        VSIE_TRY((run_nbody<float, PolK2>(pk, plan_sk<float, PolK2>(h, nt, h->K.n, 1), scratch, 1, slots, st,
+                                          nullptr)));
+      } else {
+        VSIE_TRY(gk_concurrent(h, pg, pk, nt, gbps, kbps, false, scratch, slots, st, nullptr));
+      }
+      VSIE_CUDA(cudaEventRecord(e1, st));
+      VSIE_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      VSIE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (r > 0) best = std::min(best, ms);
+    }
+    *best_ms = best;
+    return VSIE_OK;
+  };
+  float seq = 0.0f, best = 1e30f;
+  int bg = 0, bk = 0;
+  vsie_status s = time_one(0, 0, &seq);
+  ++*candidates;
+  for (int gb = 1; gb < maxg && s == VSIE_OK; ++gb) {
+    const int kb = std::max(1, (maxk * (maxg - gb)) / maxg);
+    float ms = 0.0f;
+    s = time_one(gb, kb, &ms);
+    ++*candidates;
+    if (s == VSIE_OK && ms < best) {
+      best = ms;
+      bg = gb;
+      bk = kb;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  VSIE_TRY(s);
+  out_ms[1] = seq;
+  if (bg > 0 && best < 0.98f * seq) {
+    h->tune.gk_bps[0] = out_bps[0] = bg;
+    h->tune.gk_bps[1] = out_bps[1] = bk;
+    out_ms[0] = best;
+  } else {
+    out_ms[0] = seq;
   }
   return VSIE_OK;
 }

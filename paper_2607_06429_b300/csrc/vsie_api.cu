@@ -94,6 +94,9 @@ extern "C" void vsie_destroy(vsie_handle* h) {
   cudaGetDevice(&prev);
   cudaSetDevice(h->device);
   for (void* p : h->allocs) cudaFree(p);
+  if (h->gk_stream) cudaStreamDestroy(h->gk_stream);
+  if (h->gk_fork) cudaEventDestroy(h->gk_fork);
+  if (h->gk_join) cudaEventDestroy(h->gk_join);
   cudaSetDevice(prev);
   delete h;
 }
@@ -868,6 +871,7 @@ extern "C" vsie_status vsie_apply_timed(vsie_handle* h, const void* d_x, void* d
     VSIE_CUDA(cudaEventRecord(ev[3], st));
     VSIE_TRY(correction_apply(h, x, y, precision, st));
     n_launch += (h->n > 0) ? 2 : 0;  // x to double-float, then the CSR correction + mass
+    n_launch += far_gk_extra_launches(h, precision);
     VSIE_CUDA(cudaEventRecord(ev[4], st));
     VSIE_CUDA(cudaEventSynchronize(ev[4]));
     for (int i = 0; i < 4; ++i) {
@@ -1043,6 +1047,13 @@ extern "C" vsie_status vsie_autotune(vsie_handle* h, int32_t flags, vsie_tuning*
         rep.far_ms[c] = ms[c][0];
         rep.far_default_ms[c] = ms[c][1];
       }
+      int gk_bps[2];
+      double gk_ms[2];
+      VSIE_TRY(far_autotune_gk(h, x, y, st, gk_bps, gk_ms, &rep.candidates));
+      rep.gk_blocks_per_sm[0] = gk_bps[0];
+      rep.gk_blocks_per_sm[1] = gk_bps[1];
+      rep.gk_ms = gk_ms[0];
+      rep.gk_sequential_ms = gk_ms[1];
     }
     if (flags & 2) {
       double ms[2];
@@ -1058,6 +1069,52 @@ extern "C" vsie_status vsie_autotune(vsie_handle* h, int32_t flags, vsie_tuning*
   cudaFree(y);
   if (report) *report = rep;
   return s;
+}
+
+extern "C" vsie_status vsie_set_tuning(vsie_handle* h, const vsie_tuning* t) {
+  clear_error();
+  if (!h || !t) {
+    set_error("vsie_set_tuning: null handle or tuning");
+    return VSIE_ERR_ARG;
+  }
+  for (int c = 0; c < 3; ++c)
+    if (t->far_chunk[c] < 0 || t->far_chunk[c] > (1 << 20) || t->far_chunk[c] % 128 != 0 ||
+        t->far_blocks_per_sm[c] < 0 || t->far_blocks_per_sm[c] > 64) {
+      set_error("vsie_set_tuning: far_chunk must be 0 or a multiple of 128 up to 2^20 and "
+                "far_blocks_per_sm in [0, 64]");
+      return VSIE_ERR_ARG;
+    }
+  if (t->batch_chunk_tiles < 0 || t->batch_chunk_tiles > 65536 || t->gk_blocks_per_sm[0] < 0 ||
+      t->gk_blocks_per_sm[1] < 0 || t->gk_blocks_per_sm[0] > 64 || t->gk_blocks_per_sm[1] > 64 ||
+      (t->gk_blocks_per_sm[0] > 0) != (t->gk_blocks_per_sm[1] > 0)) {
+    set_error("vsie_set_tuning: batch_chunk_tiles must be in [0, 65536] and gk_blocks_per_sm both 0 or "
+              "both in [1, 64]");
+    return VSIE_ERR_ARG;
+  }
+  for (int c = 0; c < 3; ++c) {
+    h->tune.chunk[c] = t->far_chunk[c];
+    h->tune.bps[c] = t->far_blocks_per_sm[c];
+  }
+  h->tune.bt_chunk_tiles = t->batch_chunk_tiles;
+  return far_set_gk(h, t->gk_blocks_per_sm[0], t->gk_blocks_per_sm[1]);
+}
+
+extern "C" vsie_status vsie_get_tuning(const vsie_handle* h, vsie_tuning* t) {
+  clear_error();
+  if (!h || !t) {
+    set_error("vsie_get_tuning: null handle or tuning");
+    return VSIE_ERR_ARG;
+  }
+  vsie_tuning r{};
+  for (int c = 0; c < 3; ++c) {
+    r.far_chunk[c] = h->tune.chunk[c];
+    r.far_blocks_per_sm[c] = h->tune.bps[c];
+  }
+  r.batch_chunk_tiles = h->tune.bt_chunk_tiles;
+  r.gk_blocks_per_sm[0] = h->tune.gk_bps[0];
+  r.gk_blocks_per_sm[1] = h->tune.gk_bps[1];
+  *t = r;
+  return VSIE_OK;
 }
 
 extern "C" vsie_status vsie_apply_batched_multi(vsie_handle* const* hs, int32_t nop, const void* const* d_x,

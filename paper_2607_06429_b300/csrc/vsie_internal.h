@@ -185,7 +185,16 @@ struct vsie_handle {
     int chunk[3] = {0, 0, 0};  // FP32 far sums (G, K, F): sources per work item
     int bps[3] = {0, 0, 0};    // FP32 far sums: resident blocks per SM
     int bt_chunk_tiles = 0;    // tensor-core batched sums: 32-source tiles per work item
+    int gk_bps[2] = {0, 0};    // FP32 G and K sums run concurrently with these blocks per SM
+                               // each (0: one after the other)
   } tune;
+  // concurrent G and K sums: the K sum's stream, fork/join events, output and slots
+  cudaStream_t gk_stream = nullptr;
+  cudaEvent_t gk_fork = nullptr, gk_join = nullptr;
+  double2* gk_y = nullptr;
+  int64_t gk_y_n = 0;
+  double2* gk_split = nullptr;
+  size_t gk_split_elems = 0;
 
   std::vector<void*> allocs;  // every device allocation, freed by vsie_destroy
 
@@ -293,6 +302,17 @@ vsie_status far_batched64_gk(vsie_handle* h, const double2* x, double2* y, int n
 // scratch holds n values): chosen (chunk, blocks per SM) and (chosen, default) times per class.
 vsie_status far_autotune(vsie_handle* h, const double2* x, double2* scratch, cudaStream_t st, int cand_out[3][2],
                          double ms_out[3][2], int* candidates);
+// Then the choice between the G and K sums one after the other and concurrently (resident
+// blocks per SM split between them), timed on a target sample: sets h->tune.gk_bps;
+// (chosen, sequential) times.
+vsie_status far_autotune_gk(vsie_handle* h, const double2* x, double2* scratch, cudaStream_t st, int out_bps[2],
+                            double out_ms[2], int* candidates);
+// Sets the concurrent G and K sums with gbps and kbps resident blocks per SM (clamped to the
+// kernels' occupancy), allocating their buffers; 0, 0: the sums one after the other.
+vsie_status far_set_gk(vsie_handle* h, int gbps, int kbps);
+// Kernels vsie_apply launches beyond the sequential sums' count (1 with the concurrent sums:
+// the join's addition).
+int far_gk_extra_launches(const vsie_handle* h, int precision);
 // The same for the tensor-core batched sums' source tiles per work item (x: a block of 64
 // random columns, y: n x 64 scratch).
 vsie_status batch_autotune(vsie_handle* h, const double2* x, double2* y, cudaStream_t st, int* chunk_tiles,

@@ -55,3 +55,73 @@ def test_autotune_choices_and_parity_after_tuning():
     assert _rel(y1[rows], M @ X[0]) <= 1e-5
     # the tuned shapes stay deterministic
     assert np.array_equal(op.apply(Xd[0], precision=32).cpu().numpy(), y1)
+
+
+@pytest.mark.parametrize("split", [(1, 7), (4, 4), (6, 2)])
+def test_concurrent_g_and_k_sums_match_sequential_and_oracle(split):
+    """The G and K sums on two streams at once (vsie_set_tuning's gk_blocks_per_sm) give the
+    sequential result up to the summation order, and the oracle's rows, for any split of the
+    resident blocks; a mixed-precision solve through them converges to the same solution."""
+    torch, B = _setup()
+    w = W.nested_k10(24, 4, 10.0)
+    op = B.Operator.from_workload(w)
+    D = O.Discretisation.from_workload(w)
+    x = W.random_vector(w.n, 41)
+    xd = torch.from_numpy(x).cuda()
+    y_seq = op.apply(xd, precision=32).cpu().numpy()
+    op.set_tuning(gk_blocks_per_sm=split)
+    t = op.get_tuning()
+    assert t["gk_blocks_per_sm"] == list(split)
+    y_con = op.apply(xd, precision=32).cpu().numpy()
+    assert _rel(y_con, y_seq) <= 1e-6
+    rows = np.sort(np.random.default_rng(5).choice(w.n, 16, replace=False))
+    assert _rel(y_con[rows], D.matrix_rows(rows) @ x) <= 1e-5
+    assert np.array_equal(op.apply(xd, precision=32).cpu().numpy(), y_con)   # deterministic
+    # other precisions do not take the concurrent path
+    y64 = op.apply(xd, precision=64).cpu().numpy()
+    assert _rel(y64[rows], D.matrix_rows(rows) @ x) <= 1e-11
+    b = op.plane_wave_rhs([1.0, 0.0, 0.0])[0].contiguous()
+    p_con, info = op.solve(b, mode=32, tol=1e-8)
+    op.set_tuning()
+    assert op.get_tuning()["gk_blocks_per_sm"] == [0, 0]
+    p_seq, _ = op.solve(b, mode=32, tol=1e-8)
+    assert _rel(p_con.cpu().numpy(), p_seq.cpu().numpy()) <= 1e-7
+
+
+def test_concurrent_sums_with_heterogeneous_volume_sources():
+    """With the least-squares density gradient the F class follows G on the main stream
+    while K runs concurrently; rows against the oracle."""
+    torch, B = _setup()
+    w = W.nested_perturbed(10, 2, 6.0, lsq=True)
+    op = B.Operator.from_workload(w)
+    assert op.n_far_sources > 0
+    D = O.Discretisation.from_workload(w)
+    x = W.random_vector(w.n, 43)
+    xd = torch.from_numpy(x).cuda()
+    y_seq = op.apply(xd, precision=32).cpu().numpy()
+    op.set_tuning(gk_blocks_per_sm=(3, 5))
+    y_con = op.apply(xd, precision=32).cpu().numpy()
+    assert _rel(y_con, y_seq) <= 1e-6
+    rows = np.sort(np.random.default_rng(6).choice(w.n, 24, replace=False))
+    assert _rel(y_con[rows], D.matrix_rows(rows) @ x) <= 1e-5
+
+
+def test_set_tuning_rejects_out_of_range_values_and_keeps_the_shapes():
+    torch, B = _setup()
+    w = W.nested_k10(16, 3, 10.0)
+    op = B.Operator.from_workload(w)
+    op.set_tuning(far_chunk=(2048, 1024, 0), far_blocks_per_sm=(6, 4, 0), batch_chunk_tiles=32,
+                  gk_blocks_per_sm=(5, 3))
+    before = op.get_tuning()
+    assert before == {"far_chunk": [2048, 1024, 0], "far_blocks_per_sm": [6, 4, 0],
+                      "batch_chunk_tiles": 32, "gk_blocks_per_sm": [5, 3]}
+    for bad in (dict(far_chunk=(100, 0, 0)), dict(far_blocks_per_sm=(0, 65, 0)),
+                dict(batch_chunk_tiles=-1), dict(gk_blocks_per_sm=(4, 0))):
+        with pytest.raises(B.VsieError):
+            op.set_tuning(**bad)
+        assert op.get_tuning() == before
+    x = torch.from_numpy(W.random_vector(w.n, 7)).cuda()
+    D = O.Discretisation.from_workload(w)
+    rows = np.arange(0, w.n, max(1, w.n // 20))
+    y = op.apply(x, precision=32).cpu().numpy()
+    assert _rel(y[rows], D.matrix_rows(rows) @ x.cpu().numpy()) <= 1e-5
