@@ -878,6 +878,14 @@ def main():
               "traffic": G_KERNEL_DRAM_BYTES, "kernel_ms": g_ms,
               "algorithmic_bytes_per_launch": 20.0 * n_g + 16.0 * n + 16.0 * n,
               "measured_pipes_per_clk_per_sm": probe}
+        # the timed apply's far sums as a whole (G and K concurrently when the autotuner chose
+        # it): every class takes 3 MUFU operations per pair, so the same MUFU bound applies
+        other_ms = float(np.mean([p["prescale"] + p["correction"] for p in phase_ms]))
+        far_ms = max(t_ms - other_ms, 1e-9)
+        rf["apply_far_sums"] = {"achieved": inter / (far_ms * 1e-3) / 1e9, "peak": xu / 1e9,
+                                "unit": "Ginteractions/s", "frac": inter / (far_ms * 1e-3) / xu,
+                                "far_ms": far_ms,
+                                "concurrent_gk": (tuning or {}).get("concurrent_gk")}
 
     # error of the timed result against the oracle on seeded rows, and the oracle's rate on
     # all host cores (rows are independent): the CPU baseline
