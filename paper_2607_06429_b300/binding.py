@@ -31,7 +31,8 @@ EXPORTS = ("vsie_create", "vsie_destroy", "vsie_sizes", "vsie_apply", "vsie_appl
            "vsie_autotune", "vsie_get_tuning", "vsie_set_tuning", "vsie_gradient_channels", "vsie_source_points",
            "vsie_lsq_grad_alpha", "vsie_lsq_grad_alpha_adjoint", "vsie_scattered_field",
            "vsie_create_cuboid", "vsie_set_frequency", "vsie_cuboid_faces", "vsie_apply_rows",
-           "vsie_pipe_probe", "vsie_last_error")
+           "vsie_pipe_probe", "vsie_last_error", "vsie_bem_create", "vsie_bem_destroy", "vsie_bem_sizes",
+           "vsie_bem_apply", "vsie_bem_rhs", "vsie_bem_solve", "vsie_bem_far_field")
 
 
 class VsieError(RuntimeError):
@@ -78,6 +79,14 @@ class _Tuning(ctypes.Structure):
                 ("batch_default_ms", ctypes.c_double), ("candidates", ctypes.c_int32),
                 ("gk_blocks_per_sm", ctypes.c_int32 * 2), ("gk_ms", ctypes.c_double),
                 ("gk_sequential_ms", ctypes.c_double)]
+
+
+class _BemDesc(ctypes.Structure):
+    _fields_ = [("n_interfaces", ctypes.c_int32), ("h_vert", ctypes.c_void_p * 2), ("h_tri", ctypes.c_void_p * 2),
+                ("n_vert", ctypes.c_int64 * 2), ("n_tri", ctypes.c_int64 * 2), ("k0", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("c0", ctypes.c_double), ("rho", ctypes.c_double * 2),
+                ("c", ctypes.c_double * 2), ("far_order", ctypes.c_int32), ("near_order", ctypes.c_int32),
+                ("near_factor", ctypes.c_double)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -147,10 +156,18 @@ def load_library(path: str = LIB_PATH):
     lib.vsie_graph_nodes.argtypes = [P, ctypes.POINTER(I64)]
     lib.vsie_graph_destroy.argtypes = [P]
     lib.vsie_graph_destroy.restype = None
+    lib.vsie_bem_create.argtypes = [ctypes.POINTER(_BemDesc), ctypes.POINTER(P)]
+    lib.vsie_bem_destroy.argtypes = [P]
+    lib.vsie_bem_destroy.restype = None
+    lib.vsie_bem_sizes.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    lib.vsie_bem_apply.argtypes = [P, P, P, I32, P]
+    lib.vsie_bem_rhs.argtypes = [P, P, P, P]
+    lib.vsie_bem_solve.argtypes = [P, P, P, ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), P]
+    lib.vsie_bem_far_field.argtypes = [P, P, P, I32, P, P]
     lib.vsie_last_error.argtypes = []
     lib.vsie_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("vsie_destroy", "vsie_last_error", "vsie_graph_destroy"):
+        if name not in ("vsie_destroy", "vsie_last_error", "vsie_graph_destroy", "vsie_bem_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -489,6 +506,95 @@ class Operator:
             _check(st)
         return x, SolveInfo(st, info.iterations, info.refinements, info.rel_residual,
                             info.fp64_applies, info.fp32_applies)
+
+
+class BemOperator:
+    """The nested PMCHWT boundary element operator (vsie_bem_*): P1 Galerkin on one or two
+    nested closed triangulated interfaces (outermost first), unknowns [u_1, v_1, u_2, v_2]
+    at the vertices, rows scaled by the lumped mass."""
+
+    def __init__(self, surfaces, k0, rho, c, rho0=1.0, c0=1.0, far_order=3, near_order=4, near_factor=2.0):
+        load_library()
+        if len(surfaces) not in (1, 2) or len(rho) != len(surfaces) or len(c) != len(surfaces):
+            raise ValueError("one or two interfaces, with one (rho, c) per layer")
+        self._keep = []
+        d = _BemDesc()
+        d.n_interfaces = len(surfaces)
+        for m, (v, t) in enumerate(surfaces):
+            v, t = _f64(v), _i32(t)
+            self._keep += [v, t]
+            d.h_vert[m] = v.ctypes.data
+            d.h_tri[m] = t.ctypes.data
+            d.n_vert[m] = v.shape[0]
+            d.n_tri[m] = t.shape[0]
+            d.rho[m] = float(rho[m])
+            d.c[m] = float(c[m])
+        d.k0, d.rho0, d.c0 = float(k0), float(rho0), float(c0)
+        d.far_order, d.near_order, d.near_factor = int(far_order), int(near_order), float(near_factor)
+        self._h = ctypes.c_void_p()
+        _check(_lib.vsie_bem_create(ctypes.byref(d), ctypes.byref(self._h)))
+        self._keep = None
+        n, q, nn = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.vsie_bem_sizes(self._h, ctypes.byref(n), ctypes.byref(q), ctypes.byref(nn)))
+        self.n, self.n_points, self.n_near_pairs = n.value, q.value, nn.value
+
+    @classmethod
+    def nested_spheres(cls, subdiv, radii, k0, rho, c, rho0=1.0, c0=1.0, **kw):
+        """Concentric icosphere interfaces (workloads.icosphere)."""
+        from .workloads import icosphere
+        subdiv = [subdiv] * len(radii) if np.isscalar(subdiv) else list(subdiv)
+        return cls([icosphere(sd, R) for sd, R in zip(subdiv, radii)], k0, rho, c, rho0, c0, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.vsie_bem_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, x, y=None, precision=32, stream=None):
+        """y = P A x (vsie_bem_apply); x: CUDA complex128 (n,)."""
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        _check(_lib.vsie_bem_apply(self._h, _dev(x, "x"), _dev(y, "y"), int(precision), _stream(stream)))
+        return y
+
+    def rhs(self, direction, device="cuda", stream=None):
+        """P (int phi p_inc, int phi (1/rho0) dp_inc/dn) for the plane wave along direction."""
+        import torch
+        b = torch.empty(self.n, dtype=torch.complex128, device=device)
+        d = _f64(direction)
+        _check(_lib.vsie_bem_rhs(self._h, _ptr(d), _dev(b, "b"), _stream(stream)))
+        return b
+
+    def solve(self, b, mode=32, tol=1e-8, max_iters=1000, restart=0, inner_tol=1e-4, max_refinements=20,
+              stream=None, raise_on_fail=True):
+        """x with P A x = P b (vsie_bem_solve); returns (x, SolveInfo)."""
+        import torch
+        x = torch.empty_like(b)
+        o = _SolveOpts(int(mode), float(tol), int(max_iters), int(restart), float(inner_tol),
+                       int(max_refinements), 0, 0)
+        info = _SolveInfo()
+        st = _lib.vsie_bem_solve(self._h, _dev(b, "b"), _dev(x, "x"), ctypes.byref(o), ctypes.byref(info),
+                                 _stream(stream))
+        if raise_on_fail:
+            _check(st)
+        return x, SolveInfo(st, info.iterations, info.refinements, info.rel_residual, info.fp64_applies,
+                            info.fp32_applies)
+
+    def far_field(self, x, dirs, stream=None):
+        """Far-field pattern on the unit directions dirs (m, 3) (vsie_bem_far_field)."""
+        import torch
+        dirs = _f64(dirs).reshape(-1, 3)
+        out = torch.empty(dirs.shape[0], dtype=torch.complex128, device=x.device)
+        _check(_lib.vsie_bem_far_field(self._h, _dev(x, "x"), _ptr(dirs), dirs.shape[0], _dev(out, "out"),
+                                       _stream(stream)))
+        return out
 
 
 def pipe_probe(stream=None):

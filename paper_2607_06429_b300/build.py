@@ -10,14 +10,14 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libvsie.so")
-SOURCES = ["vsie_api.cu", "nbody.cu", "correction.cu", "solve.cu", "farfield.cu", "noalloc.cu", "batch.cu", "batch64.cu", "solve_batched.cu", "graph.cu", "lsq_gradient.cu", "field.cu", "probe.cu"]
+SOURCES = ["vsie_api.cu", "nbody.cu", "correction.cu", "solve.cu", "farfield.cu", "noalloc.cu", "batch.cu", "batch64.cu", "solve_batched.cu", "graph.cu", "lsq_gradient.cu", "field.cu", "probe.cu", "bem.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-ftz=true", "--expt-extended-lambda",
          "-Xcompiler", "-fPIC,-O2", "-shared", "-cudart", "static"]
 
 
 def _stamp() -> float:
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "vsie.h"),
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)] + [
                                                                    os.path.abspath(__file__)]
     return max(os.path.getmtime(f) for f in files)
 

@@ -160,8 +160,6 @@ static vsie_status norm2(const double2* w, int64_t n, SolveWork& S, double* out,
   return VSIE_OK;
 }
 
-// One GMRES cycle for A d = r0 from d = 0 (d is ADDED to x).  Stops when the Arnoldi
-// residual estimate drops below target_abs or after max_it iterations.
 // y = A x (adjoint == false) or y = A^H x (adjoint == true)
 static vsie_status op_apply(vsie_handle* h, bool adjoint, const double2* x, double2* y, int precision,
                             cudaStream_t st) {
@@ -170,11 +168,12 @@ static vsie_status op_apply(vsie_handle* h, bool adjoint, const double2* x, doub
   return correction_adjoint(h, x, y, precision, st);
 }
 
-static vsie_status gmres_cycle(vsie_handle* h, bool adjoint, int precision, const double2* r0,
+// One GMRES cycle for A d = r0 from d = 0 (d is ADDED to x).  Stops when the Arnoldi
+// residual estimate drops below target_abs or after max_it iterations.
+static vsie_status gmres_cycle(int64_t n, const ApplyFn& apply, int precision, const double2* r0,
                                double r0norm, double2* x, double target_abs, int max_it, SolveWork& S,
                                cudaStream_t st, int* iters, double* est, int* applies,
-                               bool* breakdown) {
-  const int64_t n = h->n;
+                               bool* breakdown, const char* who) {
   const int m = std::min(max_it, S.m);
   std::vector<cplx> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
   g[0] = r0norm;
@@ -186,7 +185,7 @@ static vsie_status gmres_cycle(vsie_handle* h, bool adjoint, int precision, cons
   std::vector<cplx> h1, h2;
   for (j = 0; j < m; ++j) {
     double2* vj = S.V + (size_t)j * n;
-    VSIE_TRY(op_apply(h, adjoint, vj, S.w, precision, st));
+    VSIE_TRY(apply(vj, S.w, precision));
     ++*applies;
     // CGS2
     // (multidot leaves the coefficients in S.hdev for the update kernel)
@@ -199,7 +198,7 @@ static vsie_status gmres_cycle(vsie_handle* h, bool adjoint, int precision, cons
     double beta;
     VSIE_TRY(norm2(S.w, n, S, &beta, st));
     if (!std::isfinite(beta)) {
-      set_error("vsie_solve: non-finite value in the Arnoldi process");
+      set_error(std::string(who) + ": non-finite value in the Arnoldi process");
       return VSIE_ERR_NAN;
     }
     for (int i = 0; i <= j; ++i) H[(size_t)j * (m + 1) + i] = h1[i] + h2[i];
@@ -258,35 +257,18 @@ static vsie_status gmres_cycle(vsie_handle* h, bool adjoint, int precision, cons
   return VSIE_OK;
 }
 
-}  // namespace vsie
-
-using namespace vsie;
-
-extern "C" vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
-                                  const vsie_solve_opts* opts, vsie_solve_info* info, void* stream) {
-  clear_error();
-  TraceRange trace("vsie_solve");
-  if (!h || !d_b || !d_x || !opts) {
-    set_error("vsie_solve: null argument");
-    return VSIE_ERR_ARG;
-  }
-  if ((opts->mode != 32 && opts->mode != 64) || !(opts->tol > 0.0) || opts->max_iters < 1 ||
-      opts->restart < 0 || (opts->mode == 32 && !(opts->inner_tol > 0.0))) {
-    set_error("vsie_solve: invalid options");
-    return VSIE_ERR_ARG;
-  }
-  cudaStream_t st = (cudaStream_t)stream;
-  const int64_t n = h->n;
-  const double2* b = (const double2*)d_b;
-  double2* x = (double2*)d_x;
-  const bool adjoint = opts->adjoint != 0;
+// GMRES (x0 = 0 or the given iterate) with, in mode 32, FP64 iterative refinement: inner
+// cycles with the inner_prec apply to inner_tol, true residuals with the res_prec apply.
+vsie_status gmres_solve(int64_t n, const ApplyFn& apply, const double2* b, double2* x,
+                        const vsie_solve_opts* opts, vsie_solve_info* info, cudaStream_t st, int inner_prec,
+                        int res_prec, const char* who) {
   vsie_solve_info local{};
   vsie_solve_info& inf = info ? *info : local;
   inf = vsie_solve_info{};
 
   const int m = (opts->restart > 0 && opts->restart < opts->max_iters) ? opts->restart : opts->max_iters;
   if (m > 3000) {
-    set_error("vsie_solve: Krylov basis larger than 3000 columns; set restart <= 3000");
+    set_error(std::string(who) + ": Krylov basis larger than 3000 columns; set restart <= 3000");
     return VSIE_ERR_ARG;
   }
   std::vector<void*> temps;
@@ -309,15 +291,12 @@ extern "C" vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
     cleanup();
     return s;
   }
-  // the apply that forms true residuals: the double-float sums (precision 48) in the
-  // refinement of a forward solve, plain FP64 otherwise
-  const int res_prec = (opts->mode == 32 && !adjoint) ? 48 : 64;
   auto run = [&]() -> vsie_status {
     if (!opts->initial_guess) VSIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * n, st));
     double bnorm;
     VSIE_TRY(norm2(b, n, S, &bnorm, st));
     if (!std::isfinite(bnorm)) {
-      set_error("vsie_solve: non-finite right-hand side");
+      set_error(std::string(who) + ": non-finite right-hand side");
       return VSIE_ERR_NAN;
     }
     if (bnorm == 0.0) {  // the solution is 0 whatever the starting iterate
@@ -329,13 +308,13 @@ extern "C" vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
     double rnorm = bnorm;
     if (opts->initial_guess) {
       // resume: r = b - A x from the given iterate
-      VSIE_TRY(op_apply(h, adjoint, x, S.t, res_prec, st));
+      VSIE_TRY(apply(x, S.t, res_prec));
       inf.fp64_applies += 1;
       sub_kernel<<<nb256(n), 256, 0, st>>>(b, S.t, S.r, n);
       VSIE_CUDA(cudaGetLastError());
       VSIE_TRY(norm2(S.r, n, S, &rnorm, st));
       if (!std::isfinite(rnorm)) {
-        set_error("vsie_solve: non-finite residual of the initial guess");
+        set_error(std::string(who) + ": non-finite residual of the initial guess");
         return VSIE_ERR_NAN;
       }
       inf.rel_residual = rnorm / bnorm;
@@ -343,7 +322,6 @@ extern "C" vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
     } else {
       VSIE_CUDA(cudaMemcpyAsync(S.r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
     }
-    const int inner_prec = opts->mode;
     const int max_outer = opts->mode == 32 ? std::max(1, opts->max_refinements) : 1 << 30;
     int outer = 0;
     while (true) {
@@ -352,21 +330,21 @@ extern "C" vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
       int it = 0, applies = 0;
       double est;
       bool brk;
-      VSIE_TRY(gmres_cycle(h, adjoint, inner_prec, S.r, rnorm, x, cycle_target,
-                           opts->max_iters - inf.iterations, S, st, &it, &est, &applies, &brk));
+      VSIE_TRY(gmres_cycle(n, apply, inner_prec, S.r, rnorm, x, cycle_target, opts->max_iters - inf.iterations,
+                           S, st, &it, &est, &applies, &brk, who));
       inf.iterations += it;
       if (inner_prec == 32)
         inf.fp32_applies += applies;
       else
         inf.fp64_applies += applies;
       // true residual with the FP64-accuracy apply
-      VSIE_TRY(op_apply(h, adjoint, x, S.t, res_prec, st));
+      VSIE_TRY(apply(x, S.t, res_prec));
       inf.fp64_applies += 1;
       sub_kernel<<<nb256(n), 256, 0, st>>>(b, S.t, S.r, n);
       VSIE_CUDA(cudaGetLastError());
       VSIE_TRY(norm2(S.r, n, S, &rnorm, st));
       if (!std::isfinite(rnorm)) {
-        set_error("vsie_solve: non-finite residual");
+        set_error(std::string(who) + ": non-finite residual");
         return VSIE_ERR_NAN;
       }
       ++outer;
@@ -374,11 +352,11 @@ extern "C" vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
       inf.rel_residual = rnorm / bnorm;
       if (rnorm <= target) return VSIE_OK;
       if (brk && it == 0) {
-        set_error("vsie_solve: GMRES breakdown");
+        set_error(std::string(who) + ": GMRES breakdown");
         return VSIE_ERR_BREAKDOWN;
       }
       if (inf.iterations >= opts->max_iters || outer >= max_outer) {
-        set_error("vsie_solve: tolerance not reached within the iteration limits");
+        set_error(std::string(who) + ": tolerance not reached within the iteration limits");
         return VSIE_ERR_NOT_CONVERGED;
       }
     }
@@ -387,4 +365,33 @@ extern "C" vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
   cudaStreamSynchronize(st);
   cleanup();
   return s;
+}
+
+}  // namespace vsie
+
+using namespace vsie;
+
+extern "C" vsie_status vsie_solve(vsie_handle* h, const void* d_b, void* d_x,
+                                  const vsie_solve_opts* opts, vsie_solve_info* info, void* stream) {
+  clear_error();
+  TraceRange trace("vsie_solve");
+  if (!h || !d_b || !d_x || !opts) {
+    set_error("vsie_solve: null argument");
+    return VSIE_ERR_ARG;
+  }
+  if ((opts->mode != 32 && opts->mode != 64) || !(opts->tol > 0.0) || opts->max_iters < 1 ||
+      opts->restart < 0 || (opts->mode == 32 && !(opts->inner_tol > 0.0))) {
+    set_error("vsie_solve: invalid options");
+    return VSIE_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool adjoint = opts->adjoint != 0;
+  // the apply that forms true residuals: the double-float sums (precision 48) in the
+  // refinement of a forward solve, plain FP64 otherwise
+  const int res_prec = (opts->mode == 32 && !adjoint) ? 48 : 64;
+  const ApplyFn apply = [&](const double2* xx, double2* yy, int prec) {
+    return op_apply(h, adjoint, xx, yy, prec, st);
+  };
+  return gmres_solve(h->n, apply, (const double2*)d_b, (double2*)d_x, opts, info, st, opts->mode, res_prec,
+                     "vsie_solve");
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -276,6 +277,14 @@ vsie_status gradient_channels(vsie_handle* h, const double2* lam, int precision,
 vsie_status correction_adjoint(vsie_handle* h, const double2* lam, double2* x,
                                int precision, cudaStream_t st);
 
+// y = A x at the given precision (an operator for the generic GMRES driver)
+using ApplyFn = std::function<vsie_status(const double2* x, double2* y, int precision)>;
+// GMRES (x0 = 0, or the iterate in x with opts->initial_guess) with, in mode 32, FP64
+// iterative refinement: inner cycles with the inner_prec apply, true residuals with the
+// res_prec apply; who names the entry point in error messages.  Blocking.
+vsie_status gmres_solve(int64_t n, const ApplyFn& apply, const double2* b, double2* x,
+                        const vsie_solve_opts* opts, vsie_solve_info* info, cudaStream_t st, int inner_prec,
+                        int res_prec, const char* who);
 vsie_status apply_one(vsie_handle* h, const double2* x, double2* y, int precision,
                       cudaStream_t st);
 

@@ -1,0 +1,112 @@
+"""The nested PMCHWT boundary element path of the library (vsie_bem_*) against the FP64
+oracle (oracle/bem_oracle.py): the preconditioned operator applied to seeded vectors
+(every entry of the result), the near-pair lists, the right-hand side, the far field and
+the solution; on finer meshes, against the layered-sphere series."""
+import numpy as np
+import pytest
+
+from oracle import bem_oracle as BO
+from oracle import series
+from paper_2607_06429_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RADII, RHO, C, K0 = [1.0, 0.5], [1.5, 3.0], [0.8, 0.6], 3.0
+
+
+def _setup():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2607_06429_b300 import binding as B
+    from paper_2607_06429_b300 import build as BUILD
+    BUILD.build()
+    return torch, B
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+CASES = {
+    "nested_ico2_ico1": dict(subdiv=(2, 1), radii=RADII, rho=RHO, c=C),
+    "single_ico2": dict(subdiv=(2,), radii=[1.0], rho=[1.5], c=[0.8]),
+    "nested_ico1_far2_near5": dict(subdiv=(1, 1), radii=RADII, rho=RHO, c=C, far_order=2, near_order=5,
+                                   near_factor=1.5),
+}
+
+
+def _pair(case):
+    torch, B = _setup()
+    p = dict(CASES[case])
+    kw = {k: p.pop(k) for k in ("far_order", "near_order", "near_factor") if k in p}
+    op = B.BemOperator.nested_spheres(p["subdiv"], p["radii"], K0, p["rho"], p["c"], **kw)
+    D = BO.BemDiscretisation.nested_spheres(p["subdiv"], p["radii"], K0, p["rho"], p["c"], **kw)
+    return torch, B, op, D
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_bem_apply_matches_the_oracle_matrix(case):
+    torch, B, op, D = _pair(case)
+    assert op.n == D.n
+    A = D.assemble()
+    for seed in (1, 2):
+        x = W.random_vector(D.n, 700 + seed)
+        ref = A @ x
+        xd = torch.from_numpy(x).cuda()
+        y64 = op.apply(xd, precision=64).cpu().numpy()
+        y32 = op.apply(xd, precision=32).cpu().numpy()
+        assert _rel(y64, ref) <= 1e-11
+        assert _rel(y32, ref) <= 2e-6
+        # entry by entry: the largest error relative to the row scale
+        assert np.max(np.abs(y64 - ref)) <= 1e-10 * np.max(np.abs(ref))
+    # deterministic
+    assert torch.equal(op.apply(xd, precision=32), op.apply(xd, precision=32))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_bem_near_pairs_rhs_and_far_field_match_the_oracle(case):
+    torch, B, op, D = _pair(case)
+    n_near = 0
+    for m in range(len(D.S)):
+        for l in range(len(D.S)):
+            if any(m in dom["sides"] and l in dom["sides"] for dom in D.domains):
+                n_near += D.near_pairs(m, l)[0].size
+    assert op.n_near_pairs == n_near
+    b = op.rhs([1.0, 0.3, -0.2]).cpu().numpy()
+    assert _rel(b, D.rhs([1.0, 0.3, -0.2])) <= 1e-13
+    dirs = W.fibonacci_dirs(24)
+    x = W.random_vector(D.n, 9)
+    ff = op.far_field(torch.from_numpy(x).cuda(), dirs).cpu().numpy()
+    assert _rel(ff, D.far_field(x, dirs)) <= 1e-13
+
+
+def test_bem_solve_matches_the_oracle_solution_and_the_series():
+    torch, B, op, D = _pair("nested_ico2_ico1")
+    y_ref = D.solve([1.0, 0.0, 0.0])
+    b = op.rhs([1.0, 0.0, 0.0])
+    x64, info64 = op.solve(b, mode=64, tol=1e-12, max_iters=800)
+    x32, info32 = op.solve(b, mode=32, tol=1e-10, max_iters=800)
+    assert info64.rel_residual <= 1e-12 and info32.rel_residual <= 1e-10
+    assert info32.refinements >= 1 and info32.fp32_applies > info32.fp64_applies
+    assert _rel(x64.cpu().numpy(), y_ref) <= 1e-9
+    assert _rel(x32.cpu().numpy(), y_ref) <= 1e-8
+    dirs = W.fibonacci_dirs(32)
+    ff = op.far_field(x32, dirs).cpu().numpy()
+    ref = series.layered_sphere_far_field(dirs, [1, 0, 0], K0, RADII, RHO, C)
+    e_gpu, e_oracle = _rel(ff, ref), _rel(D.far_field(y_ref, dirs), ref)
+    assert abs(e_gpu - e_oracle) <= 1e-6 and e_gpu < 0.08
+
+
+def test_bem_converges_to_the_layered_sphere_series_on_finer_meshes():
+    torch, B = _setup()
+    dirs = W.fibonacci_dirs(64)
+    ref = series.layered_sphere_far_field(dirs, [1, 0, 0], K0, RADII, RHO, C)
+    errs, iters = [], []
+    for sub in ((3, 2), (4, 3)):
+        op = B.BemOperator.nested_spheres(sub, RADII, K0, RHO, C)
+        x, info = op.solve(op.rhs([1.0, 0.0, 0.0]), mode=32, tol=1e-6, max_iters=2000)
+        errs.append(_rel(op.far_field(x, dirs).cpu().numpy(), ref))
+        iters.append(info.iterations)
+        op.close()
+    assert errs[0] < 0.02 and errs[1] < 0.006 and errs[0] / errs[1] > 3.0

@@ -89,8 +89,8 @@ def test_field_and_frequency_calls_reject_null_handle(lib):
 
 
 def test_header_is_plain_c_and_matches_the_binding_layouts(tmp_path):
-    """include/vsie.h compiles as pedantic C99, and the structs the binding mirrors have
-    the same sizes on both sides."""
+    """include/vsie.h and include/vsie_bem.h compile as pedantic C99, and the structs the
+    binding mirrors have the same sizes on both sides."""
     import shutil
     import subprocess
     cc = shutil.which("gcc") or shutil.which("cc")
@@ -98,11 +98,11 @@ def test_header_is_plain_c_and_matches_the_binding_layouts(tmp_path):
         pytest.skip("no C compiler")
     src = tmp_path / "abi.c"
     src.write_text(
-        '#include <stdio.h>\n#include "vsie.h"\n'
+        '#include <stdio.h>\n#include "vsie.h"\n#include "vsie_bem.h"\n'
         "int main(void) {\n"
-        '  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(vsie_mesh), sizeof(vsie_material),\n'
+        '  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(vsie_mesh), sizeof(vsie_material),\n'
         "         sizeof(vsie_options), sizeof(vsie_solve_opts), sizeof(vsie_solve_info),\n"
-        "         sizeof(vsie_cuboid_grid));\n"
+        "         sizeof(vsie_cuboid_grid), sizeof(vsie_bem_desc), sizeof(vsie_tuning));\n"
         "  return 0;\n}\n")
     exe = tmp_path / "abi"
     subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
@@ -110,7 +110,41 @@ def test_header_is_plain_c_and_matches_the_binding_layouts(tmp_path):
     sizes = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
                                             text=True).stdout.split()]
     assert sizes == [ctypes.sizeof(B._Mesh), ctypes.sizeof(B._Material), ctypes.sizeof(B._Options),
-                     ctypes.sizeof(B._SolveOpts), ctypes.sizeof(B._SolveInfo), ctypes.sizeof(B._CuboidGrid)]
+                     ctypes.sizeof(B._SolveOpts), ctypes.sizeof(B._SolveInfo), ctypes.sizeof(B._CuboidGrid),
+                     ctypes.sizeof(B._BemDesc), ctypes.sizeof(B._Tuning)]
+
+
+def test_bem_calls_reject_bad_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.vsie_bem_create(None, ctypes.byref(h)) == 1
+    d = B._BemDesc()
+    d.n_interfaces = 3
+    assert lib.vsie_bem_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert b"n_interfaces" in lib.vsie_last_error()
+    from paper_2607_06429_b300.workloads import icosphere
+    v, t = icosphere(1, 1.0)
+    v = np.ascontiguousarray(v)
+    t = np.ascontiguousarray(t, dtype=np.int32)
+    d.n_interfaces = 1
+    d.h_vert[0] = v.ctypes.data
+    d.h_tri[0] = t.ctypes.data
+    d.n_vert[0], d.n_tri[0] = v.shape[0], t.shape[0]
+    d.k0, d.rho0, d.c0, d.rho[0], d.c[0] = 2.0, 1.0, 1.0, 1.5, 0.8
+    d.far_order = 9
+    assert lib.vsie_bem_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert b"order" in lib.vsie_last_error()
+    d.far_order = 3
+    t_bad = t.copy()
+    t_bad[5, 1] = v.shape[0]
+    d.h_tri[0] = t_bad.ctypes.data
+    assert lib.vsie_bem_create(ctypes.byref(d), ctypes.byref(h)) == 2     # VSIE_ERR_MESH
+    d.h_tri[0] = t.ctypes.data
+    d.k0 = -1.0
+    assert lib.vsie_bem_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert not h.value
+    assert lib.vsie_bem_apply(None, None, None, 32, None) == 1
+    assert lib.vsie_bem_solve(None, None, None, None, None, None) == 1
+    assert lib.vsie_bem_sizes(None, None, None, None) == 1
 
 
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
