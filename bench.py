@@ -548,6 +548,115 @@ def cuboid_timing(torch, B, W, N=91, steps=2):
             "oracle_sample": f"{len(rows)} seeded rows (FP64 numpy, 1 thread)"}
 
 
+def bem_timing(torch, B, W, subdiv=(4, 3), k0=3.0, steps=3, vsie_grid=48):
+    """The nested PMCHWT boundary element solver (Sec. 2.4: the paper's comparison method for
+    piecewise-constant media, P1 Galerkin) on icosphere interfaces r = 1, 0.5 with layers
+    (rho, c) = (1.5, 0.8), (3.0, 0.6) at k0 = 3: FP32/FP64 apply rates, the apply against the
+    N-body kernel's FP32-pipe bound, mixed and FP64 GMRES to the paper's 1e-5, the far field
+    against the layered-sphere series, the FP64 oracle matrix on a small mesh of the same
+    problem, and the same problem solved by the VSIE (tetrahedral layered ball) for the
+    paper's VSIE-versus-BEM comparison (benchmark 2)."""
+    from oracle import bem_oracle as BO
+    from oracle import series
+    radii, rho, c = [1.0, 0.5], [1.5, 3.0], [0.8, 0.6]
+    dirs = W.fibonacci_dirs(64)
+    ref = series.layered_sphere_far_field(dirs, [1, 0, 0], k0, radii, rho, c)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))  # noqa: E731
+    out = {"workload": f"nested_spheres_ico{subdiv[0]}_ico{subdiv[1]}_k{k0:g}"}
+    t0 = time.perf_counter()
+    op = B.BemOperator.nested_spheres(subdiv, radii, k0, rho, c)
+    torch.cuda.synchronize()
+    out["create_s"] = time.perf_counter() - t0
+    nt = [20 * 4 ** s for s in subdiv]
+    q = op.n_points // sum(nt)
+    np0, np1 = nt[0] * q, nt[1] * q
+    pairs = float(np0) ** 2 + float(np0 + np1) ** 2 + float(np1) ** 2
+    out.update(n_unknowns=op.n, n_points=op.n_points, n_near_pairs=op.n_near_pairs, pairs_per_apply=pairs)
+    x = torch.from_numpy(W.random_vector(op.n, 11)).cuda()
+    y = torch.empty_like(x)
+    for prec in (32, 64):
+        op.apply(x, y, precision=prec)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_steps = steps if prec == 32 else 1
+        a.record()
+        for _ in range(n_steps):
+            op.apply(x, y, precision=prec)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / n_steps
+        out[f"apply_ms_fp{prec}"] = ms
+        out[f"pairs_per_s_fp{prec}"] = pairs / (ms * 1e-3)
+    # bem_nbody_kernel<float>: 57 FP32-pipe operations and 3 MUFU operations per pair, so the
+    # FP32 pipe binds (128 lanes per SM per clock)
+    props = torch.cuda.get_device_properties(0)
+    f_hz = 2032e6
+    bound = props.multi_processor_count * 128 * f_hz / 57.0
+    out["roofline_fp32"] = {"bound": "alu", "achieved": out["pairs_per_s_fp32"] / 1e9, "peak": bound / 1e9,
+                            "unit": "Gpairs/s", "frac": out["pairs_per_s_fp32"] / bound,
+                            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes/clk at 2032 MHz "
+                                          "/ 57 FP32-pipe operations per pair (whole apply timed)"}
+    b = op.rhs([1.0, 0.0, 0.0])
+    for mode in (32, 64):
+        t = time.perf_counter()
+        xs, info = op.solve(b, mode=mode, tol=1e-5, max_iters=3000, inner_tol=1e-3)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        out[f"solve_mode{mode}"] = {"seconds": dt, "iterations": info.iterations, "refinements": info.refinements,
+                                    "rel_residual": info.rel_residual, "fp32_applies": info.fp32_applies,
+                                    "fp64_applies": info.fp64_applies}
+        if mode == 32:
+            ff_bem = op.far_field(xs, dirs).cpu().numpy()
+            out["far_field_rel_err_vs_series"] = rel(ff_bem, ref)
+    op.close()
+    # the oracle's dense matrix on the ico-1 / ico-1 mesh of the same problem
+    small = B.BemOperator.nested_spheres((1, 1), radii, k0, rho, c)
+    D = BO.BemDiscretisation.nested_spheres((1, 1), radii, k0, rho, c)
+    xh = W.random_vector(D.n, 12)
+    with one_thread():
+        t = time.perf_counter()
+        yref = D.assemble() @ xh
+        dt = time.perf_counter() - t
+    xd = torch.from_numpy(xh).cuda()
+    out["rel_err_vs_oracle"] = {"fp64": rel(small.apply(xd, precision=64).cpu().numpy(), yref),
+                                "fp32": rel(small.apply(xd, precision=32).cpu().numpy(), yref),
+                                "mesh": "ico1/ico1 (168 unknowns), full matrix", "oracle_seconds": dt}
+    small.close()
+    # the VSIE on the same layered ball (tetrahedra, centroid collocation)
+    w = W.layered_ball(vsie_grid, 5, 4, k0, R2=0.5, rho1=rho[0], c1=c[0], rho2=rho[1], c2=c[1])
+    vop = B.Operator.from_workload(w)
+    t = time.perf_counter()
+    p, vinfo = vop.solve(vop.plane_wave_rhs([1.0, 0.0, 0.0])[0].contiguous(), mode=32, tol=1e-5)
+    torch.cuda.synchronize()
+    vdt = time.perf_counter() - t
+    ff_vsie = vop.far_field(p, dirs).cpu().numpy()
+    vop.close()
+    out["vsie_same_problem"] = {"workload": w.name, "n": int(w.n), "solve_s": vdt, "iterations": vinfo.iterations,
+                                "far_field_rel_err_vs_series": rel(ff_vsie, ref),
+                                "far_field_rel_diff_vs_bem": rel(ff_vsie, ff_bem)}
+    return out
+
+
+def bem_apply_only(args):
+    """--steps FP32 applies of the nested-sphere boundary element operator (the bem section's
+    problem) and one JSON line with their mean time: the command the profiles use."""
+    import torch
+    from paper_2607_06429_b300 import binding as B
+    from paper_2607_06429_b300 import workloads as W
+    sub = tuple(int(v) for v in args.bem_apply_only.split(","))
+    op = B.BemOperator.nested_spheres(sub, [1.0, 0.5], 3.0, [1.5, 3.0], [0.8, 0.6])
+    x = torch.from_numpy(W.random_vector(op.n, 1)).cuda()
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        op.apply(x, y, precision=32)
+    torch.cuda.synchronize()
+    print(json.dumps({"bem_mesh": list(sub), "n_unknowns": op.n, "n_points": op.n_points,
+                      "ms_per_apply": (time.perf_counter() - t) * 1e3 / max(1, args.steps)}))
+    op.close()
+
+
 def large_timing(torch, B, W, nrhs=16):
     """The large workload (128^3 grid, k0 = 25, 7,250,176 unknowns, 8,560,896 far-field
     source points) with 16 plane waves: one timed tensor-core multi-RHS apply, the FP32
@@ -747,11 +856,18 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the cuboid-grid apply, exterior-field and adjoint timings")
     ap.add_argument("--multifreq-mesh", default="auto", choices=["auto", "nested24_k10", "nested80_k10", "none"])
+    ap.add_argument("--no-bem", action="store_true",
+                    help="skip the nested PMCHWT boundary element section")
+    ap.add_argument("--bem-apply-only", default=None, metavar="S1,S2",
+                    help="profiling: only --steps FP32 applies of the boundary element operator on "
+                         "icosphere interfaces of these subdivisions, then exit")
     ap.add_argument("--large", action="store_true",
                     help="also time the k0 = 25, 128^3 workload's 16-RHS apply (about 5 minutes)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.bem_apply_only:
+        return bem_apply_only(args)
 
     sec = Sections(args.budget_s)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -944,6 +1060,10 @@ def main():
         multifreq = sec.run("multifreq", lambda: multifreq_timing(
             torch, B, W, mesh=mesh, steps=1 if mesh == "nested80_k10" else 2), estimate_s=30)
 
+    bem = None
+    if not args.no_bem and args.precision == 32:
+        bem = sec.run("bem", lambda: bem_timing(torch, B, W), estimate_s=90)
+
     large = None
     if args.large and args.precision == 32:
         large = sec.run("large", lambda: large_timing(torch, B, W), estimate_s=300)
@@ -970,6 +1090,7 @@ def main():
         "batched": batched,
         "multifreq": multifreq,
         "large": large,
+        "bem": bem,
         "extras": extras,
         "cpu_baseline": cpu,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
