@@ -611,7 +611,7 @@ def bem_timing(torch, B, W, subdiv=(4, 3), k0=3.0, steps=3, vsie_grid=48):
     op.close()
     # the oracle's dense matrix on the ico-1 / ico-1 mesh of the same problem
     small = B.BemOperator.nested_spheres((1, 1), radii, k0, rho, c)
-    D = BO.BemDiscretisation.nested_spheres((1, 1), radii, k0, rho, c)
+    D = BO.BemDiscretisation.nested([W.icosphere(1, R) for R in radii], k0, rho, c)
     xh = W.random_vector(D.n, 12)
     with one_thread():
         t = time.perf_counter()

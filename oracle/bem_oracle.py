@@ -256,14 +256,11 @@ class BemDiscretisation:
         self.k0 = domains[0]["k"]
 
     @classmethod
-    def nested_spheres(cls, subdiv, radii, k0, rho, c, rho0=1.0, c0=1.0, **kw):
-        """Concentric icosphere interfaces (radii decreasing) with homogeneous layers
-        (rho[l], c[l] inside interface l, down to the next); exterior (rho0, c0)."""
-        from paper_2607_06429_b300.workloads import icosphere
-        subdiv = [subdiv] * len(radii) if np.isscalar(subdiv) else list(subdiv)
-        surfaces = [icosphere(s, R) for s, R in zip(subdiv, radii)]
+    def nested(cls, surfaces, k0, rho, c, rho0=1.0, c0=1.0, **kw):
+        """Nested closed interfaces (list of (vert, tri), outermost first) with homogeneous
+        layers: (rho[l], c[l]) inside interface l, down to the next; exterior (rho0, c0)."""
         omega = k0 * c0
-        L = len(radii)
+        L = len(surfaces)
         domains = [{"k": k0, "rho": rho0, "sides": {0: -1}}]
         for l in range(L):
             sides = {l: +1}

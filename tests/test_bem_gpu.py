@@ -41,7 +41,8 @@ def _pair(case):
     p = dict(CASES[case])
     kw = {k: p.pop(k) for k in ("far_order", "near_order", "near_factor") if k in p}
     op = B.BemOperator.nested_spheres(p["subdiv"], p["radii"], K0, p["rho"], p["c"], **kw)
-    D = BO.BemDiscretisation.nested_spheres(p["subdiv"], p["radii"], K0, p["rho"], p["c"], **kw)
+    D = BO.BemDiscretisation.nested([W.icosphere(sd, R) for sd, R in zip(p["subdiv"], p["radii"])], K0,
+                                    p["rho"], p["c"], **kw)
     return torch, B, op, D
 
 

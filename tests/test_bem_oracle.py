@@ -21,6 +21,10 @@ from oracle import series
 from paper_2607_06429_b300.workloads import fibonacci_dirs, icosphere
 
 
+def _nested(subdiv, radii, k0, rho, c, **kw):
+    return BO.BemDiscretisation.nested([icosphere(sd, R) for sd, R in zip(subdiv, radii)], k0, rho, c, **kw)
+
+
 def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
@@ -163,7 +167,7 @@ def test_operators_on_a_sphere_converge_to_the_spherical_harmonic_spectrum():
 
 
 def test_cross_surface_blocks_are_transposes():
-    D = BO.BemDiscretisation.nested_spheres((1, 1), [1.0, 0.5], 3.0, [1.5, 3.0], [0.8, 0.6])
+    D = _nested((1, 1), [1.0, 0.5], 3.0, [1.5, 3.0], [0.8, 0.6])
     k1 = D.domains[1]["k"]
     V01, K01, Kp01, W01 = D.operator_blocks(0, 1, k1)
     V10, K10, Kp10, W10 = D.operator_blocks(1, 0, k1)
@@ -181,13 +185,13 @@ def _series_error(D, dirs):
 
 def test_pmchwt_converges_to_the_layered_sphere_series():
     dirs = fibonacci_dirs(32)
-    e11 = _series_error(BO.BemDiscretisation.nested_spheres((1, 1), RADII, K0, RHO, C), dirs)
-    e21 = _series_error(BO.BemDiscretisation.nested_spheres((2, 1), RADII, K0, RHO, C), dirs)
+    e11 = _series_error(_nested((1, 1), RADII, K0, RHO, C), dirs)
+    e21 = _series_error(_nested((2, 1), RADII, K0, RHO, C), dirs)
     assert e11 < 0.2 and e21 < 0.08 and e11 / e21 > 2.0
 
 
 def test_identical_media_do_not_scatter():
-    D = BO.BemDiscretisation.nested_spheres((1, 1), RADII, K0, [1.0, 1.0], [1.0, 1.0])
+    D = _nested((1, 1), RADII, K0, [1.0, 1.0], [1.0, 1.0])
     y = D.solve([1, 0, 0])
     ff = D.far_field(y, fibonacci_dirs(32))
     ref = series.layered_sphere_far_field(fibonacci_dirs(32), [1, 0, 0], K0, RADII, RHO, C)
@@ -200,13 +204,13 @@ def test_identical_media_do_not_scatter():
 
 @functools.lru_cache(maxsize=1)
 def _base_error():
-    return _series_error(BO.BemDiscretisation.nested_spheres((1, 1), RADII, K0, RHO, C), fibonacci_dirs(32))
+    return _series_error(_nested((1, 1), RADII, K0, RHO, C), fibonacci_dirs(32))
 
 
 @pytest.mark.parametrize("mistake", ["w_without_k2_term", "k_sign", "dn_sign_in_rhs", "rho_in_v"])
 def test_planted_mistakes_fail_the_series_pin(mistake, monkeypatch):
     dirs = fibonacci_dirs(32)
-    D = BO.BemDiscretisation.nested_spheres((1, 1), RADII, K0, RHO, C)
+    D = _nested((1, 1), RADII, K0, RHO, C)
     base = _base_error()
     orig_blocks = BO.BemDiscretisation.operator_blocks
 
