@@ -657,16 +657,18 @@ __global__ void __launch_bounds__(kBemThreads) bem_nbody_kernel(const R* __restr
                                                                  int64_t np, R kappa, int64_t chunk,
                                                                  double* __restrict__ part) {
   __shared__ R sh[kBemThreads * kSrcRec];
+  // the FP64 sums of this thread's targets live in shared memory (touched once per tile),
+  // which keeps them out of the registers the pair loop needs
+  __shared__ double acc[kBemTgt * kOut][kBemThreads];
   const int64_t tb = (int64_t)blockIdx.x * kBemThreads * kBemTgt;
   const int64_t c0 = (int64_t)blockIdx.y * chunk, c1 = min(np, c0 + chunk);
   R tx[kBemTgt][6];
   bool live[kBemTgt];
-  double acc[kBemTgt][kOut];
   for (int m = 0; m < kBemTgt; ++m) {
     const int64_t i = tb + threadIdx.x + m * kBemThreads;
     live[m] = i < np;
     for (int d = 0; d < 6; ++d) tx[m][d] = live[m] ? tgt[kTgtRec * (p0 + i) + d] : R(0);
-    for (int o = 0; o < kOut; ++o) acc[m][o] = 0.0;
+    for (int o = 0; o < kOut; ++o) acc[m * kOut + o][threadIdx.x] = 0.0;
   }
   const R twopi = (R)6.28318530717958647692;
   for (int64_t s0 = c0; s0 < c1; s0 += kBemThreads) {
@@ -715,13 +717,13 @@ __global__ void __launch_bounds__(kBemThreads) bem_nbody_kernel(const R* __restr
       }
     }
     for (int m = 0; m < kBemTgt; ++m)
-      for (int o = 0; o < kOut; ++o) acc[m][o] += (double)a[m][o];
+      for (int o = 0; o < kOut; ++o) acc[m * kOut + o][threadIdx.x] += (double)a[m][o];
   }
   for (int m = 0; m < kBemTgt; ++m) {
     const int64_t i = tb + threadIdx.x + m * kBemThreads;
     if (!live[m]) continue;
     double* out = part + ((int64_t)blockIdx.y * np + i) * kOut;
-    for (int o = 0; o < kOut; ++o) out[o] = acc[m][o];
+    for (int o = 0; o < kOut; ++o) out[o] = acc[m * kOut + o][threadIdx.x];
   }
 }
 
@@ -893,9 +895,11 @@ __global__ void bem_far_field_kernel(const double2* __restrict__ x, const double
 
 // ----------------------------------------------------------------- host side
 
+// Source chunks of a layer's N-body launch: about two waves of 7 resident blocks on every
+// SM, chunks of at least 512 sources.
 static int bem_nchunk(int64_t np) {
   const int64_t tblocks = (np + kBemThreads * kBemTgt - 1) / (kBemThreads * kBemTgt);
-  const int64_t want = (4 * 148 + tblocks - 1) / std::max<int64_t>(1, tblocks);
+  const int64_t want = (14 * 148 + tblocks - 1) / std::max<int64_t>(1, tblocks);
   const int64_t most = std::max<int64_t>(1, np / (4 * kBemThreads));
   return (int)std::max<int64_t>(1, std::min<int64_t>({want, most, 64}));
 }
