@@ -574,11 +574,11 @@ def bem_timing(torch, B, W, subdiv=(4, 3), k0=3.0, steps=3, vsie_grid=48):
     out.update(n_unknowns=op.n, n_points=op.n_points, n_near_pairs=op.n_near_pairs, pairs_per_apply=pairs)
     x = torch.from_numpy(W.random_vector(op.n, 11)).cuda()
     y = torch.empty_like(x)
-    for prec in (32, 64):
+    for prec in (32, 48, 64):
         op.apply(x, y, precision=prec)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n_steps = steps if prec == 32 else 1
+        n_steps = steps if prec != 64 else 1
         a.record()
         for _ in range(n_steps):
             op.apply(x, y, precision=prec)
@@ -1055,6 +1055,10 @@ def main():
     if not args.no_solve:
         solve24 = sec.run("solve_nested24", lambda: solve_timing(torch, B, W, fp64_tol8=False), estimate_s=90)
 
+    bem = None
+    if not args.no_bem and args.precision == 32:
+        bem = sec.run("bem", lambda: bem_timing(torch, B, W), estimate_s=90)
+
     multifreq = None
     if not args.no_batched and args.precision == 32 and args.multifreq_mesh != "none":
         mesh = args.multifreq_mesh
@@ -1063,10 +1067,6 @@ def main():
         op.close()  # room for the eight operators of the multi-frequency plan
         multifreq = sec.run("multifreq", lambda: multifreq_timing(
             torch, B, W, mesh=mesh, steps=1 if mesh == "nested80_k10" else 2), estimate_s=30)
-
-    bem = None
-    if not args.no_bem and args.precision == 32:
-        bem = sec.run("bem", lambda: bem_timing(torch, B, W), estimate_s=90)
 
     large = None
     if args.large and args.precision == 32:

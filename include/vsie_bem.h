@@ -79,8 +79,9 @@ vsie_status vsie_bem_sizes(const vsie_bem* b, int64_t* n_unknowns, int64_t* n_po
 
 /* d_y = P A d_x (P: the lumped-mass row scaling); d_x, d_y complex128 of n_unknowns,
  * distinct.  precision 32: the far-rule N-body sums in FP32 (per-tile partial sums folded
- * into FP64), 64: in FP64; the near corrections and the P1 gathers in FP64 either way.
- * Asynchronous.  Errors: VSIE_ERR_ARG (null, aliasing, precision), VSIE_ERR_CUDA. */
+ * into FP64); 48: in double-float arithmetic on the FP32 pipe (FP64-class accuracy); 64: in
+ * FP64; the near corrections and the P1 gathers in FP64 in every case.  Asynchronous.
+ * Errors: VSIE_ERR_ARG (null, aliasing, precision), VSIE_ERR_CUDA. */
 vsie_status vsie_bem_apply(vsie_bem* b, const void* d_x, void* d_y, int32_t precision, void* stream);
 
 /* d_b = P (int phi_a p_inc, int phi_a (1/rho0) dp_inc/dn) on interface 1 (zero on interface
@@ -90,8 +91,8 @@ vsie_status vsie_bem_rhs(vsie_bem* b, const double* h_direction, void* d_b, void
 
 /* GMRES on P A x = P b with the options and report of vsie_solve: mode 64 FP64 GMRES,
  * mode 32 FP64 iterative refinement around FP32-apply inner cycles (residuals with the
- * FP64 apply); adjoint and initial_guess must be 0.  Blocking; allocates the Krylov basis.
- * Errors: as vsie_solve. */
+ * double-float apply, precision 48); adjoint and initial_guess must be 0.  Blocking;
+ * allocates the Krylov basis.  Errors: as vsie_solve. */
 vsie_status vsie_bem_solve(vsie_bem* b, const void* d_b, void* d_x, const vsie_solve_opts* opts,
                            vsie_solve_info* info, void* stream);
 

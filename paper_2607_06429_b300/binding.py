@@ -557,7 +557,8 @@ class BemOperator:
             pass
 
     def apply(self, x, y=None, precision=32, stream=None):
-        """y = P A x (vsie_bem_apply); x: CUDA complex128 (n,)."""
+        """y = P A x (vsie_bem_apply); x: CUDA complex128 (n,); precision 32, 48 (double-float)
+        or 64."""
         import torch
         if y is None:
             y = torch.empty_like(x)

@@ -28,6 +28,7 @@
 #include <cmath>
 #include <vector>
 
+#include "dfloat.h"
 #include "vsie_bem.h"
 #include "vsie_internal.h"
 
@@ -42,6 +43,10 @@ constexpr int kBemTgt = 2;        // targets per thread
 constexpr int kSrcRec = 20;       // x y z nx ny nz | q uK b c (complex) | a (3 complex)
 constexpr int kTgtRec = 6;        // x y z nx ny nz
 constexpr int kOut = 10;          // S1, S2, A_x, A_y, A_z (complex)
+constexpr int kDfTgt = 12;        // double-float target record: x y z nx ny nz (hi, lo each)
+constexpr int kDfSrc = 40;        // double-float source record: the 20 values (hi, lo each)
+constexpr int kDfThreads = 128;   // double-float N-body: one target per thread
+constexpr int kDfTile = 64;       // sources per shared-memory tile
 
 struct BemDomain {
   double k, rho;
@@ -130,6 +135,8 @@ struct vsie_bem {
   float* tgt32 = nullptr;
   double* src64[3] = {nullptr, nullptr, nullptr};  // per layer, nq x 20
   float* src32[3] = {nullptr, nullptr, nullptr};
+  float* tgtdf = nullptr;                            // nq x 12
+  float* srcdf[3] = {nullptr, nullptr, nullptr};   // per layer, nq x 40
   double* pout = nullptr;       // nq x 10 (the N-body sums, signed, all layers)
   double* part = nullptr;       // N-body chunk partials
   size_t part_elems = 0;
@@ -247,6 +254,25 @@ __global__ void bem_src_geom_kernel(const double* __restrict__ tgt64, int64_t nq
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nq) return;
   for (int d = 0; d < 6; ++d) src[kSrcRec * p + d] = (R)tgt64[6 * p + d];
+}
+
+// Double-float records: positions and normals split into (hi, lo) floats, for the targets
+// and the per-layer source arrays (charges are written per apply).
+__global__ void bem_df_geom_kernel(const double* __restrict__ tgt64, int64_t nq, float* __restrict__ tgt,
+                                   float* __restrict__ s0, float* __restrict__ s1, float* __restrict__ s2) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nq) return;
+  float* outs[3] = {s0, s1, s2};
+  for (int d = 0; d < 6; ++d) {
+    const dfs v = dfs_make(tgt64[6 * p + d]);
+    tgt[kDfTgt * p + 2 * d] = v.h;
+    tgt[kDfTgt * p + 2 * d + 1] = v.l;
+    for (int j = 0; j < 3; ++j)
+      if (outs[j]) {
+        outs[j][kDfSrc * p + 2 * d] = v.h;
+        outs[j][kDfSrc * p + 2 * d + 1] = v.l;
+      }
+  }
 }
 
 // Lumped mass per vertex: sum of A_T/3 over its triangles, in triangle order.
@@ -570,13 +596,36 @@ __global__ void bem_near_blocks_kernel(const double* __restrict__ vert, const in
 // weight w, the sign sigma_jl, rho_j, k_j and 1/(4 pi):
 //   q = rho sigma w v, uK = sigma w u, b = -k^2 sigma w u / rho, c = sigma w v,
 //   a = sigma w curl(u) / rho.
+// Charge k (0..13) of a source record: R precision, or (hi, lo) floats for the double-float
+// records (tagged by R = dfs).
+template <class R>
+struct ChargeStore {
+  using T = R;
+  static __device__ __forceinline__ void put(R* o, int k, double v) { o[6 + k] = (R)v; }
+  static constexpr int stride = kSrcRec;
+};
+template <>
+struct ChargeStore<dfs> {
+  using T = float;
+  static __device__ __forceinline__ void put(float* o, int k, double v) {
+    const dfs d = dfs_make(v);
+    o[12 + 2 * k] = d.h;
+    o[13 + 2 * k] = d.l;
+  }
+  static constexpr int stride = kDfSrc;
+};
+
 template <class R>
 __global__ void bem_prolong_kernel(const double2* __restrict__ x, const int* __restrict__ tri,
                                    const int* __restrict__ tsurf, const int64_t* __restrict__ uidx,
                                    const int64_t* __restrict__ vidx, const double* __restrict__ geo,
                                    const double* __restrict__ qw, const BemRule* __restrict__ rule, int64_t nt,
-                                   BemDomain d0, BemDomain d1, BemDomain d2, int ndom, R* __restrict__ s0,
-                                   R* __restrict__ s1, R* __restrict__ s2) {
+                                   BemDomain d0, BemDomain d1, BemDomain d2, int ndom,
+                                   typename ChargeStore<R>::T* __restrict__ s0,
+                                   typename ChargeStore<R>::T* __restrict__ s1,
+                                   typename ChargeStore<R>::T* __restrict__ s2) {
+  using CS = ChargeStore<R>;
+  using T = typename CS::T;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   const int Q = rule->q;
@@ -594,7 +643,7 @@ __global__ void bem_prolong_kernel(const double2* __restrict__ x, const int* __r
   }
   const int sl = tsurf[t];
   const BemDomain doms[3] = {d0, d1, d2};
-  R* outs[3] = {s0, s1, s2};
+  T* outs[3] = {s0, s1, s2};
   for (int q = 0; q < Q; ++q) {
     const int64_t p = t * Q + q;
     double ur = 0, ui = 0, vr = 0, vi = 0;
@@ -609,19 +658,19 @@ __global__ void bem_prolong_kernel(const double2* __restrict__ x, const int* __r
       const BemDomain& D = doms[j];
       if (D.sigma[sl] == 0) continue;
       const double w = D.sigma[sl] * qw[p] * kInv4Pi;
-      R* o = outs[j] + kSrcRec * p;
-      o[6] = (R)(D.rho * w * vr);
-      o[7] = (R)(D.rho * w * vi);
-      o[8] = (R)(w * ur);
-      o[9] = (R)(w * ui);
+      T* o = outs[j] + CS::stride * p;
+      CS::put(o, 0, D.rho * w * vr);
+      CS::put(o, 1, D.rho * w * vi);
+      CS::put(o, 2, w * ur);
+      CS::put(o, 3, w * ui);
       const double kb = -D.k * D.k * w / D.rho;
-      o[10] = (R)(kb * ur);
-      o[11] = (R)(kb * ui);
-      o[12] = (R)(w * vr);
-      o[13] = (R)(w * vi);
+      CS::put(o, 4, kb * ur);
+      CS::put(o, 5, kb * ui);
+      CS::put(o, 6, w * vr);
+      CS::put(o, 7, w * vi);
       for (int d = 0; d < 3; ++d) {
-        o[14 + 2 * d] = (R)(w * cur[d][0] / D.rho);
-        o[15 + 2 * d] = (R)(w * cur[d][1] / D.rho);
+        CS::put(o, 8 + 2 * d, w * cur[d][0] / D.rho);
+        CS::put(o, 9 + 2 * d, w * cur[d][1] / D.rho);
       }
     }
   }
@@ -724,6 +773,84 @@ __global__ void __launch_bounds__(kBemThreads) bem_nbody_kernel(const R* __restr
     if (!live[m]) continue;
     double* out = part + ((int64_t)blockIdx.y * np + i) * kOut;
     for (int o = 0; o < kOut; ++o) out[o] = acc[m * kOut + o][threadIdx.x];
+  }
+}
+
+// Double-float N-body sums of one layer (FP64-class accuracy on the FP32 pipe): one target
+// per thread, every operation of the pair evaluation in double-float (positions,
+// 1/r by a Newton-refined rsqrt, the phase kappa r reduced to revolutions, cos and sin of
+// 2 pi f by the library's Taylor evaluation, the five complex sums), per-tile sums folded into
+// FP64.  kappa = k/(2 pi) as a double-float.  part[chunk][i][10] as the other N-body kernels.
+__global__ void __launch_bounds__(kDfThreads) bem_nbody_df_kernel(const float* __restrict__ tgt,
+                                                                   const float* __restrict__ src, int64_t p0,
+                                                                   int64_t np, float kap_h, float kap_l,
+                                                                   int64_t chunk, double* __restrict__ part) {
+  __shared__ float sh[kDfTile * kDfSrc];
+  __shared__ double acc[kOut][kDfThreads];
+  const int64_t i = (int64_t)blockIdx.x * kDfThreads + threadIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.y * chunk, c1 = min(np, c0 + chunk);
+  const bool live = i < np;
+  dfs t[6];
+  for (int d = 0; d < 6; ++d)
+    t[d] = live ? dfs{tgt[kDfTgt * (p0 + i) + 2 * d], tgt[kDfTgt * (p0 + i) + 2 * d + 1]} : dfs{0.0f, 0.0f};
+  for (int o = 0; o < kOut; ++o) acc[o][threadIdx.x] = 0.0;
+  const dfs kap{kap_h, kap_l};
+  for (int64_t s0 = c0; s0 < c1; s0 += kDfTile) {
+    const int ns = (int)((c1 - s0) < (int64_t)kDfTile ? (c1 - s0) : (int64_t)kDfTile);
+    __syncthreads();
+    for (int e = threadIdx.x; e < ns * kDfSrc; e += kDfThreads) sh[e] = src[kDfSrc * (p0 + s0) + e];
+    __syncthreads();
+    dfs a[kOut];
+    for (int o = 0; o < kOut; ++o) a[o] = dfs{0.0f, 0.0f};
+    for (int j = 0; j < ns; ++j) {
+      const float* s = sh + kDfSrc * j;
+      const dfs dx = dfs_sub(t[0], dfs{s[0], s[1]});
+      const dfs dy = dfs_sub(t[1], dfs{s[2], s[3]});
+      const dfs dz = dfs_sub(t[2], dfs{s[4], s[5]});
+      const dfs r2 = dfs_add(dfs_add(dfs_sqr(dx), dfs_sqr(dy)), dfs_sqr(dz));
+      if (!(r2.h > 0.0f)) continue;  // zero distance contributes nothing
+      const dfs rinv = dfs_rsqrt(r2);
+      const dfs tt = dfs_mul(dfs_mul(r2, rinv), kap);  // kr / (2 pi)
+      const float nr = rintf(tt.h);
+      dfs cs, sn;
+      dfs_cossin_2pi(dfs_two_sum(__fsub_rn(tt.h, nr), tt.l), cs, sn);
+      const dfs Fr = dfs_mul(cs, rinv), Fi = dfs_mul(sn, rinv);
+      const dfs rinv3 = dfs_mul(dfs_sqr(rinv), rinv);
+      const dfs kr = dfs_mul(tt, dfc_two_pi());
+      const dfs Er = dfs_neg(dfs_mul(dfs_add(cs, dfs_mul(kr, sn)), rinv3));
+      const dfs Ei = dfs_mul(dfs_sub(dfs_mul(kr, cs), sn), rinv3);
+      const dfs snx{s[6], s[7]}, sny{s[8], s[9]}, snz{s[10], s[11]};
+      const dfs dns = dfs_add(dfs_add(dfs_mul(dx, snx), dfs_mul(dy, sny)), dfs_mul(dz, snz));
+      const dfs dnx = dfs_add(dfs_add(dfs_mul(dx, t[3]), dfs_mul(dy, t[4])), dfs_mul(dz, t[5]));
+      const dfs nn = dfs_add(dfs_add(dfs_mul(t[3], snx), dfs_mul(t[4], sny)), dfs_mul(t[5], snz));
+      // charge k at s[12 + 2k], s[13 + 2k]
+#define BEM_CH(k) dfs{s[12 + 2 * (k)], s[13 + 2 * (k)]}
+      // S1 += F q + (E dns) uK
+      const dfs e1r = dfs_mul(Er, dns), e1i = dfs_mul(Ei, dns);
+      a[0] = dfs_add(a[0], dfs_sub(dfs_add(dfs_mul(Fr, BEM_CH(0)), dfs_mul(e1r, BEM_CH(2))),
+                                   dfs_add(dfs_mul(Fi, BEM_CH(1)), dfs_mul(e1i, BEM_CH(3)))));
+      a[1] = dfs_add(a[1], dfs_add(dfs_add(dfs_mul(Fr, BEM_CH(1)), dfs_mul(Fi, BEM_CH(0))),
+                                   dfs_add(dfs_mul(e1r, BEM_CH(3)), dfs_mul(e1i, BEM_CH(2)))));
+      // S2 += (F nn) b + (E dnx) c
+      const dfs f2r = dfs_mul(Fr, nn), f2i = dfs_mul(Fi, nn);
+      const dfs e2r = dfs_mul(Er, dnx), e2i = dfs_mul(Ei, dnx);
+      a[2] = dfs_add(a[2], dfs_sub(dfs_add(dfs_mul(f2r, BEM_CH(4)), dfs_mul(e2r, BEM_CH(6))),
+                                   dfs_add(dfs_mul(f2i, BEM_CH(5)), dfs_mul(e2i, BEM_CH(7)))));
+      a[3] = dfs_add(a[3], dfs_add(dfs_add(dfs_mul(f2r, BEM_CH(5)), dfs_mul(f2i, BEM_CH(4))),
+                                   dfs_add(dfs_mul(e2r, BEM_CH(7)), dfs_mul(e2i, BEM_CH(6)))));
+      // A += F a
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        a[4 + 2 * d] = dfs_add(a[4 + 2 * d], dfs_sub(dfs_mul(Fr, BEM_CH(8 + 2 * d)), dfs_mul(Fi, BEM_CH(9 + 2 * d))));
+        a[5 + 2 * d] = dfs_add(a[5 + 2 * d], dfs_add(dfs_mul(Fr, BEM_CH(9 + 2 * d)), dfs_mul(Fi, BEM_CH(8 + 2 * d))));
+      }
+#undef BEM_CH
+    }
+    for (int o = 0; o < kOut; ++o) acc[o][threadIdx.x] += dfs_value(a[o]);
+  }
+  if (live) {
+    double* out = part + ((int64_t)blockIdx.y * np + i) * kOut;
+    for (int o = 0; o < kOut; ++o) out[o] = acc[o][threadIdx.x];
   }
 }
 
@@ -904,9 +1031,21 @@ static int bem_nchunk(int64_t np) {
   return (int)std::max<int64_t>(1, std::min<int64_t>({want, most, 64}));
 }
 
+// The same for the double-float launch (one target per thread, 128 per block).
+static int bem_nchunk_df(int64_t np) {
+  const int64_t tblocks = (np + kDfThreads - 1) / kDfThreads;
+  const int64_t want = (8 * 148 + tblocks - 1) / std::max<int64_t>(1, tblocks);
+  const int64_t most = std::max<int64_t>(1, np / (4 * kDfTile));
+  return (int)std::max<int64_t>(1, std::min<int64_t>({want, most, 64}));
+}
+
 static vsie_status bem_apply_impl(vsie_bem* b, const double2* x, double2* y, int precision, cudaStream_t st) {
   const int64_t nt = b->nt;
-  if (precision == 32)
+  if (precision == 48)
+    bem_prolong_kernel<dfs><<<nblk(nt, 128), 128, 0, st>>>(x, b->tri, b->tsurf, b->uidx, b->vidx, b->tgeo, b->qw,
+                                                           b->d_far, nt, b->dom[0], b->dom[1], b->dom[2], b->ndom,
+                                                           b->srcdf[0], b->srcdf[1], b->srcdf[2]);
+  else if (precision == 32)
     bem_prolong_kernel<float><<<nblk(nt, 128), 128, 0, st>>>(x, b->tri, b->tsurf, b->uidx, b->vidx, b->tgeo, b->qw,
                                                              b->d_far, nt, b->dom[0], b->dom[1], b->dom[2], b->ndom,
                                                              b->src32[0], b->src32[1], b->src32[2]);
@@ -918,11 +1057,18 @@ static vsie_status bem_apply_impl(vsie_bem* b, const double2* x, double2* y, int
   VSIE_CUDA(cudaMemsetAsync(b->pout, 0, sizeof(double) * kOut * b->nq, st));
   for (int j = 0; j < b->ndom; ++j) {
     const BemDomain& D = b->dom[j];
-    const int nch = bem_nchunk(D.np);
+    const bool df = precision == 48;
+    const int nch = df ? bem_nchunk_df(D.np) : bem_nchunk(D.np);
     const int64_t chunk = (D.np + nch - 1) / nch;
-    const dim3 grid((unsigned)((D.np + kBemThreads * kBemTgt - 1) / (kBemThreads * kBemTgt)), (unsigned)nch);
+    const dim3 grid((unsigned)(df ? (D.np + kDfThreads - 1) / kDfThreads
+                                  : (D.np + kBemThreads * kBemTgt - 1) / (kBemThreads * kBemTgt)),
+                    (unsigned)nch);
     const double kappa = D.k / (2.0 * kBPi);
-    if (precision == 32)
+    if (df) {
+      const float kh = (float)kappa;
+      bem_nbody_df_kernel<<<grid, kDfThreads, 0, st>>>(b->tgtdf, b->srcdf[j], D.p0, D.np, kh,
+                                                       (float)(kappa - (double)kh), chunk, b->part);
+    } else if (precision == 32)
       bem_nbody_kernel<float><<<grid, kBemThreads, 0, st>>>(b->tgt32, b->src32[j], D.p0, D.np, (float)kappa, chunk,
                                                             b->part);
     else
@@ -992,13 +1138,16 @@ static vsie_status bem_build(vsie_bem* b, const vsie_bem_desc* d) {
   VSIE_TRY(balloc_t(b, &b->pout, (size_t)kOut * b->nq));
   VSIE_TRY(balloc_t(b, &b->zloc, (size_t)6 * b->nt));
   VSIE_TRY(balloc_t(b, &b->near_ptr, (size_t)b->nt + 1));
+  VSIE_TRY(balloc_t(b, &b->tgtdf, (size_t)kDfTgt * b->nq));
   for (int j = 0; j < b->ndom; ++j) {
     VSIE_TRY(balloc_t(b, &b->src64[j], (size_t)kSrcRec * b->nq));
     VSIE_TRY(balloc_t(b, &b->src32[j], (size_t)kSrcRec * b->nq));
+    VSIE_TRY(balloc_t(b, &b->srcdf[j], (size_t)kDfSrc * b->nq));
   }
   size_t part = 0;
   for (int j = 0; j < b->ndom; ++j)
-    part = std::max(part, (size_t)bem_nchunk(b->dom[j].np) * (size_t)b->dom[j].np * kOut);
+    part = std::max(part, (size_t)std::max(bem_nchunk(b->dom[j].np), bem_nchunk_df(b->dom[j].np)) *
+                              (size_t)b->dom[j].np * kOut);
   VSIE_TRY(balloc_t(b, &b->part, part));
   b->part_elems = part;
   int* d_bad = nullptr;
@@ -1029,6 +1178,7 @@ static vsie_status bem_build(vsie_bem* b, const vsie_bem_desc* d) {
     bem_src_geom_kernel<double><<<nblk(b->nq), 256>>>(b->tgt64, b->nq, b->src64[j]);
     bem_src_geom_kernel<float><<<nblk(b->nq), 256>>>(b->tgt64, b->nq, b->src32[j]);
   }
+  bem_df_geom_kernel<<<nblk(b->nq), 256>>>(b->tgt64, b->nq, b->tgtdf, b->srcdf[0], b->srcdf[1], b->srcdf[2]);
   VSIE_CUDA(cudaGetLastError());
   // near pairs: interfaces 0 and 1 bound a common layer when one layer touches both
   int touch01 = 0;
@@ -1176,8 +1326,8 @@ extern "C" vsie_status vsie_bem_sizes(const vsie_bem* b, int64_t* n_unknowns, in
 extern "C" vsie_status vsie_bem_apply(vsie_bem* b, const void* d_x, void* d_y, int32_t precision, void* stream) {
   clear_error();
   TraceRange trace("vsie_bem_apply");
-  if (!b || !d_x || !d_y || d_x == d_y || (precision != 32 && precision != 64)) {
-    set_error("vsie_bem_apply: null or aliased vectors, or precision not 32/64");
+  if (!b || !d_x || !d_y || d_x == d_y || (precision != 32 && precision != 48 && precision != 64)) {
+    set_error("vsie_bem_apply: null or aliased vectors, or precision not 32/48/64");
     return VSIE_ERR_ARG;
   }
   return bem_apply_impl(b, (const double2*)d_x, (double2*)d_y, precision, (cudaStream_t)stream);
@@ -1185,6 +1335,7 @@ extern "C" vsie_status vsie_bem_apply(vsie_bem* b, const void* d_x, void* d_y, i
 
 extern "C" vsie_status vsie_bem_rhs(vsie_bem* b, const double* h_direction, void* d_b, void* stream) {
   clear_error();
+  TraceRange trace("vsie_bem_rhs");
   if (!b || !h_direction || !d_b) {
     set_error("vsie_bem_rhs: null argument");
     return VSIE_ERR_ARG;
@@ -1220,16 +1371,16 @@ extern "C" vsie_status vsie_bem_solve(vsie_bem* b, const void* d_b, void* d_x, c
     return VSIE_ERR_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  const ApplyFn apply = [&](const double2* x, double2* y, int prec) {
-    return bem_apply_impl(b, x, y, prec == 32 ? 32 : 64, st);
-  };
-  return gmres_solve(b->n, apply, (const double2*)d_b, (double2*)d_x, opts, info, st, opts->mode, 64,
-                     "vsie_bem_solve");
+  const ApplyFn apply = [&](const double2* x, double2* y, int prec) { return bem_apply_impl(b, x, y, prec, st); };
+  // refinement residuals of mode 32 with the double-float sums (FP64-class on the FP32 pipe)
+  return gmres_solve(b->n, apply, (const double2*)d_b, (double2*)d_x, opts, info, st, opts->mode,
+                     opts->mode == 32 ? 48 : 64, "vsie_bem_solve");
 }
 
 extern "C" vsie_status vsie_bem_far_field(vsie_bem* b, const void* d_x, const double* h_dirs, int32_t ndir,
                                           void* d_out, void* stream) {
   clear_error();
+  TraceRange trace("vsie_bem_far_field");
   if (!b || !d_x || !h_dirs || !d_out || ndir < 1) {
     set_error("vsie_bem_far_field: null argument or ndir < 1");
     return VSIE_ERR_ARG;

@@ -149,6 +149,7 @@ using namespace vsie;
 extern "C" vsie_status vsie_lsq_grad_alpha(const vsie_mesh* mesh, const int8_t* tet_domain, const double* alpha,
                                            double* grad_alpha) {
   clear_error();
+  TraceRange trace("vsie_lsq_grad_alpha");
   VSIE_TRY(check_mesh(mesh, "vsie_lsq_grad_alpha"));
   if (!alpha || !grad_alpha) {
     set_error("vsie_lsq_grad_alpha: null alpha or output");
@@ -170,6 +171,7 @@ extern "C" vsie_status vsie_lsq_grad_alpha(const vsie_mesh* mesh, const int8_t* 
 extern "C" vsie_status vsie_lsq_grad_alpha_adjoint(const vsie_mesh* mesh, const int8_t* tet_domain,
                                                    const double* d_grad, double* d_alpha) {
   clear_error();
+  TraceRange trace("vsie_lsq_grad_alpha_adjoint");
   VSIE_TRY(check_mesh(mesh, "vsie_lsq_grad_alpha_adjoint"));
   if (!d_grad || !d_alpha) {
     set_error("vsie_lsq_grad_alpha_adjoint: null input or output");

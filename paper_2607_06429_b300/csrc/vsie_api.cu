@@ -849,6 +849,7 @@ extern "C" vsie_status vsie_apply_timed(vsie_handle* h, const void* d_x, void* d
                                         int32_t precision, void* stream, double* kernel_ms,
                                         int32_t* launches) {
   clear_error();
+  TraceRange trace("vsie_apply_timed");
   VSIE_TRY(check_apply_args(h, d_x, d_y, 1, precision, "vsie_apply_timed"));
   if (!kernel_ms) {
     set_error("vsie_apply_timed: null kernel_ms");
@@ -972,6 +973,7 @@ extern "C" vsie_status vsie_gradient_channels(vsie_handle* h, const void* d_lam,
 extern "C" vsie_status vsie_source_points(const vsie_handle* h, double* h_xyz, int32_t* h_owner,
                                           int32_t* h_class) {
   clear_error();
+  TraceRange trace("vsie_source_points");
   if (!h) {
     set_error("vsie_source_points: null handle");
     return VSIE_ERR_ARG;
@@ -1073,6 +1075,7 @@ extern "C" vsie_status vsie_autotune(vsie_handle* h, int32_t flags, vsie_tuning*
 
 extern "C" vsie_status vsie_set_tuning(vsie_handle* h, const vsie_tuning* t) {
   clear_error();
+  TraceRange trace("vsie_set_tuning");
   if (!h || !t) {
     set_error("vsie_set_tuning: null handle or tuning");
     return VSIE_ERR_ARG;

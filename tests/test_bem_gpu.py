@@ -56,11 +56,14 @@ def test_bem_apply_matches_the_oracle_matrix(case):
         ref = A @ x
         xd = torch.from_numpy(x).cuda()
         y64 = op.apply(xd, precision=64).cpu().numpy()
+        y48 = op.apply(xd, precision=48).cpu().numpy()
         y32 = op.apply(xd, precision=32).cpu().numpy()
         assert _rel(y64, ref) <= 1e-11
+        assert _rel(y48, ref) <= 1e-11
         assert _rel(y32, ref) <= 2e-6
         # entry by entry: the largest error relative to the row scale
         assert np.max(np.abs(y64 - ref)) <= 1e-10 * np.max(np.abs(ref))
+        assert np.max(np.abs(y48 - ref)) <= 1e-10 * np.max(np.abs(ref))
     # deterministic
     assert torch.equal(op.apply(xd, precision=32), op.apply(xd, precision=32))
 
