@@ -114,3 +114,24 @@ def test_bem_converges_to_the_layered_sphere_series_on_finer_meshes():
         iters.append(info.iterations)
         op.close()
     assert errs[0] < 0.02 and errs[1] < 0.006 and errs[0] / errs[1] > 3.0
+
+
+def test_bem_errors_are_reported_without_device_faults():
+    torch, B = _setup()
+    v, t = W.icosphere(1, 1.0)
+    v = np.array(v)
+    v[t[3, 1]] = v[t[3, 0]]                 # collapse one triangle to zero area
+    with pytest.raises(B.VsieError) as e:
+        B.BemOperator([(v, t)], 2.0, [1.5], [0.8])
+    assert e.value.status == 2 and "zero area" in str(e.value)
+    op = B.BemOperator.nested_spheres((1,), [1.0], 2.0, [1.5], [0.8])
+    x = torch.from_numpy(W.random_vector(op.n, 3)).cuda()
+    with pytest.raises(B.VsieError):
+        op.apply(x, precision=33)
+    with pytest.raises(B.VsieError):
+        op.apply(x, y=x, precision=32)     # aliased
+    with pytest.raises(B.VsieError):
+        op.rhs([0.0, 0.0, 0.0])
+    # the handle still works after the rejected calls
+    y = op.apply(x, precision=64)
+    assert torch.isfinite(torch.view_as_real(y)).all()
