@@ -504,12 +504,15 @@ __global__ void __launch_bounds__(BT_ALL_THREADS, 1) batch_tc_kernel(BatchArgs a
         }
         uint32_t rh[8], rl[8], ih[8], il[8];
 #pragma unroll
+        // hi = the value rounded to TF32; lo = the exact FP32 remainder, passed as it is: the
+        // MMA reads its leading TF32 bits, and since the remainder's sign does not follow the
+        // value's, dropping its low bits adds an unbiased error below 2^-21 of the value
         for (int q = 0; q < 8; ++q) {
           const float h1 = tf32(cre[q]), h2 = tf32(cim[q]);
           rh[q] = __float_as_uint(h1);
-          rl[q] = __float_as_uint(tf32(cre[q] - h1));
+          rl[q] = __float_as_uint(cre[q] - h1);
           ih[q] = __float_as_uint(h2);
-          il[q] = __float_as_uint(tf32(cim[q] - h2));
+          il[q] = __float_as_uint(cim[q] - h2);
         }
         {
           // -Q_re (hi for threads 0-255, lo for 256-511), two 16-byte vectors each
