@@ -125,3 +125,31 @@ def test_set_tuning_rejects_out_of_range_values_and_keeps_the_shapes():
     rows = np.arange(0, w.n, max(1, w.n // 20))
     y = op.apply(x, precision=32).cpu().numpy()
     assert _rel(y[rows], D.matrix_rows(rows) @ x.cpu().numpy()) <= 1e-5
+
+
+def test_concurrent_sums_are_captured_in_a_cuda_graph():
+    """The fork/join of the concurrent G and K sums (a second stream, two events) records
+    into a CUDA graph like any other launch sequence: replays equal the direct apply bit
+    for bit, and no allocation happens during capture."""
+    torch, B = _setup()
+    w = W.nested_k10(16, 3, 10.0)
+    op = B.Operator.from_workload(w)
+    op.set_tuning(gk_blocks_per_sm=(5, 3))
+    x = torch.from_numpy(W.random_vector(w.n, 17)).cuda()
+    y = torch.empty_like(x)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        op.apply(x, y, precision=32)      # warm: every buffer of the path exists
+    torch.cuda.synchronize()
+    ref = y.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        op.apply(x, y, precision=32)
+    y.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y, ref)
+    x.copy_(torch.from_numpy(W.random_vector(w.n, 18)).cuda())
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y, op.apply(x, precision=32))
