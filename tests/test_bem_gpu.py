@@ -135,3 +135,25 @@ def test_bem_errors_are_reported_without_device_faults():
     # the handle still works after the rejected calls
     y = op.apply(x, precision=64)
     assert torch.isfinite(torch.view_as_real(y)).all()
+
+
+def test_vsie_and_bem_agree_on_the_same_layered_ball():
+    """The paper's comparison for piecewise-constant layers (its benchmark 2): the VSIE on
+    a tetrahedral layered ball and the PMCHWT BEM on icosphere interfaces solve the same
+    transmission problem; their far fields agree to within their discretisation errors,
+    which both shrink against the layered-sphere series."""
+    torch, B = _setup()
+    dirs = W.fibonacci_dirs(64)
+    ref = series.layered_sphere_far_field(dirs, [1, 0, 0], K0, RADII, RHO, C)
+    bem = B.BemOperator.nested_spheres((4, 3), RADII, K0, RHO, C)
+    xb, _ = bem.solve(bem.rhs([1.0, 0.0, 0.0]), mode=32, tol=1e-6, max_iters=2000)
+    ff_bem = bem.far_field(xb, dirs).cpu().numpy()
+    bem.close()
+    w = W.layered_ball(32, 4, 3, K0, R2=RADII[1], rho1=RHO[0], c1=C[0], rho2=RHO[1], c2=C[1])
+    op = B.Operator.from_workload(w)
+    p, _ = op.solve(op.plane_wave_rhs([1.0, 0.0, 0.0])[0].contiguous(), mode=32, tol=1e-6)
+    ff_vsie = op.far_field(p, dirs).cpu().numpy()
+    op.close()
+    e_bem, e_vsie, d = _rel(ff_bem, ref), _rel(ff_vsie, ref), _rel(ff_vsie, ff_bem)
+    assert e_bem < 0.006 and e_vsie < 0.03
+    assert d < 0.02
