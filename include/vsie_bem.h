@@ -99,7 +99,8 @@ vsie_status vsie_bem_solve(vsie_bem* b, const void* d_b, void* d_x, const vsie_s
 /* Far-field pattern (p_s ~ e^{i k0 R}/R p_inf(xhat)) from the exterior representation on
  * interface 1: p_inf(xhat) = (1/4 pi) int e^{-i k0 xhat.y} [-i k0 (xhat.n_y) u(y) - rho0 v(y)]
  * dy, far rule.  d_x: solution (complex128, n_unknowns); h_dirs: 3 x ndir unit vectors;
- * d_out: complex128 ndir.  FP64, asynchronous.  Errors: VSIE_ERR_ARG. */
+ * d_out: complex128 ndir.  FP64; blocking (the directions go through a stream-ordered
+ * device buffer that is freed before returning).  Errors: VSIE_ERR_ARG, VSIE_ERR_CUDA. */
 vsie_status vsie_bem_far_field(vsie_bem* b, const void* d_x, const double* h_dirs, int32_t ndir, void* d_out,
                                void* stream);
 
