@@ -251,3 +251,27 @@ def test_planted_mistakes_fail_the_series_pin(mistake, monkeypatch):
     bad = _series_error(D, dirs)
     assert base < 0.2
     assert bad > 2.0 * base and bad > 0.25
+
+
+def test_single_interface_converges_to_the_one_layer_series():
+    """One penetrable ball (exterior and one layer, no inner interface): the same
+    formulation with a single interface against the series with one radius."""
+    dirs = fibonacci_dirs(32)
+    k0, R, rho, c = 2.0, 1.0, 1.5, 0.8
+    ref = series.layered_sphere_far_field(dirs, [1, 0, 0], k0, [R], [rho], [c])
+    errs = []
+    for sd in (1, 2):
+        D = _nested((sd,), [R], k0, [rho], [c])
+        assert [d["sides"] for d in D.domains] == [{0: -1}, {0: +1}]
+        errs.append(_rel(D.far_field(D.solve([1, 0, 0]), dirs), ref))
+    assert errs[1] < 0.04 and errs[0] / errs[1] > 2.5
+
+
+def test_lumped_mass_is_the_row_sum_of_the_mass_matrix():
+    v, t = icosphere(2, 0.7)
+    S = BO.Surface(v, t)
+    M = S.mass()
+    assert np.allclose(M.sum(axis=1), S.lumped_mass(), rtol=1e-14, atol=0)
+    assert abs(S.lumped_mass().sum() - S.area.sum()) < 1e-13 * S.area.sum()
+    # the area of the inscribed polyhedron approaches the sphere's from below
+    assert S.area.sum() < 4 * np.pi * 0.7 ** 2 and S.area.sum() > 0.97 * 4 * np.pi * 0.7 ** 2
