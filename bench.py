@@ -642,8 +642,9 @@ def bem_timing(torch, B, W, subdiv=(4, 3), k0=3.0, steps=3, vsie_grid=48, fp64_s
 
 
 def bem_apply_only(args):
-    """--steps FP32 applies of the nested-sphere boundary element operator (the bem section's
-    problem) and one JSON line with their mean time: the command the profiles use."""
+    """--steps applies (at --precision: 32, 48 or 64) of the nested-sphere boundary element
+    operator (the bem section's problem) and one JSON line with their times: the command the
+    profiles use."""
     import torch
     from paper_2607_06429_b300 import binding as B
     from paper_2607_06429_b300 import workloads as W
@@ -656,12 +657,12 @@ def bem_apply_only(args):
     for _ in range(max(1, args.steps)):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        op.apply(x, y, precision=32)
+        op.apply(x, y, precision=args.precision)
         b.record()
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
     print(json.dumps({"bem_mesh": list(sub), "n_unknowns": op.n, "n_points": op.n_points,
-                      "ms_per_apply": ms}))
+                      "precision": args.precision, "ms_per_apply": ms}))
     op.close()
 
 
@@ -867,8 +868,8 @@ def main():
     ap.add_argument("--no-bem", action="store_true",
                     help="skip the nested PMCHWT boundary element section")
     ap.add_argument("--bem-apply-only", default=None, metavar="S1,S2",
-                    help="profiling: only --steps FP32 applies of the boundary element operator on "
-                         "icosphere interfaces of these subdivisions, then exit")
+                    help="profiling: only --steps applies (at --precision) of the boundary element "
+                         "operator on icosphere interfaces of these subdivisions, then exit")
     ap.add_argument("--large", action="store_true",
                     help="also time the k0 = 25, 128^3 workload's 16-RHS apply (about 5 minutes)")
     args = ap.parse_args()
