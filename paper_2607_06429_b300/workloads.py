@@ -155,6 +155,37 @@ def icosphere(subdiv: int, radius: float):
     return v, f.astype(np.int32)
 
 
+def cube_surface(n: int, half: float):
+    """Closed triangulation of the surface of the cube [-half, half]^3: an n x n grid of
+    squares on every face, each split into two triangles, vertices shared along the edges,
+    every triangle oriented outward.  Returns (vert, tri)."""
+    n = int(n)
+    idx = -np.ones((n + 1,) * 3, dtype=np.int64)
+    g = np.arange(n + 1)
+    I, J, K = np.meshgrid(g, g, g, indexing="ij")
+    on = (I == 0) | (I == n) | (J == 0) | (J == n) | (K == 0) | (K == n)
+    idx[on] = np.arange(int(on.sum()))
+    vert = np.stack([I[on], J[on], K[on]], axis=1).astype(np.float64) * (2.0 * half / n) - half
+    tris = []
+    for axis in range(3):
+        for side in (0, n):
+            a, b = [d for d in range(3) if d != axis]
+            for i in range(n):
+                for j in range(n):
+                    corner = []
+                    for di, dj in ((0, 0), (1, 0), (1, 1), (0, 1)):
+                        c = [0, 0, 0]
+                        c[axis], c[a], c[b] = side, i + di, j + dj
+                        corner.append(idx[tuple(c)])
+                    tris.append([corner[0], corner[1], corner[2]])
+                    tris.append([corner[0], corner[2], corner[3]])
+    tri = np.array(tris, dtype=np.int64)
+    p0, p1, p2 = vert[tri[:, 0]], vert[tri[:, 1]], vert[tri[:, 2]]
+    outward = np.einsum("ij,ij->i", np.cross(p1 - p0, p2 - p0), p0 + p1 + p2) > 0
+    tri[~outward] = tri[~outward][:, [0, 2, 1]]
+    return vert, tri.astype(np.int32)
+
+
 def _centroids(vert, idx):
     return vert[idx].mean(axis=1)
 

@@ -157,3 +157,35 @@ def test_vsie_and_bem_agree_on_the_same_layered_ball():
     e_bem, e_vsie, d = _rel(ff_bem, ref), _rel(ff_vsie, ref), _rel(ff_vsie, ff_bem)
     assert e_bem < 0.006 and e_vsie < 0.03
     assert d < 0.02
+
+
+def test_bem_and_cuboid_vsie_agree_on_the_papers_nested_cubes():
+    """The paper's density benchmark (Sec. 3: cubes of 7 and 5 mm, rho2 = rho0/2,
+    c1 = c2 = c0/1.2, lambda0 = 3 mm), where it compares its VSIE with a BEM: the library's
+    cuboid VSIE (the paper's discretisation) against its PMCHWT BEM on triangulated cube
+    surfaces.  Only ratios of densities and speeds enter, so the BEM takes them scaled to
+    rho0 = c0 = 1.  As both refine, their far fields approach each other."""
+    torch, B = _setup()
+    d = [1.0, 0.0, 0.0]
+    dirs = W.fibonacci_dirs(64)
+    k0 = 2.0 * np.pi / 3.0
+    ff_vsie = {}
+    for h in (0.25, 0.125):
+        op = B.Operator.from_cuboid(W.nested_cubes(h))
+        x, info = op.solve(op.plane_wave_rhs(np.array(d))[0], mode=32, tol=1e-8)
+        assert info.rel_residual <= 1e-8
+        ff_vsie[h] = op.far_field(x, dirs).cpu().numpy()
+        op.close()
+    ff_bem = {}
+    for n1, n2 in ((14, 10), (28, 20)):
+        bem = B.BemOperator([W.cube_surface(n1, 3.5), W.cube_surface(n2, 2.5)], k0, [1.0, 0.5],
+                            [1.0 / 1.2, 1.0 / 1.2], rho0=1.0, c0=1.0)
+        xb, info = bem.solve(bem.rhs(d), mode=32, tol=1e-6, max_iters=3000)
+        assert info.rel_residual <= 1e-6
+        ff_bem[n1] = bem.far_field(xb, dirs).cpu().numpy()
+        bem.close()
+    coarse, fine = _rel(ff_bem[14], ff_vsie[0.125]), _rel(ff_bem[28], ff_vsie[0.125])
+    print(f"nested cubes: BEM (h = 0.5 / 0.25 mm) vs cuboid VSIE (h = 0.125 mm) far field "
+          f"{coarse:.4e} / {fine:.4e}; VSIE h = 0.25 vs 0.125 {_rel(ff_vsie[0.25], ff_vsie[0.125]):.4e}; "
+          f"BEM coarse vs fine {_rel(ff_bem[14], ff_bem[28]):.4e}")
+    assert fine < coarse and fine < 0.03
