@@ -275,3 +275,20 @@ def test_lumped_mass_is_the_row_sum_of_the_mass_matrix():
     assert abs(S.lumped_mass().sum() - S.area.sum()) < 1e-13 * S.area.sum()
     # the area of the inscribed polyhedron approaches the sphere's from below
     assert S.area.sum() < 4 * np.pi * 0.7 ** 2 and S.area.sum() > 0.97 * 4 * np.pi * 0.7 ** 2
+
+
+@pytest.mark.parametrize("n", [1, 3, 6])
+def test_cube_surface_is_a_closed_outward_triangulation(n):
+    from collections import Counter
+    from paper_2607_06429_b300.workloads import cube_surface
+    v, t = cube_surface(n, 2.5)
+    assert t.shape == (12 * n * n, 3) and v.shape == (6 * n * n + 2, 3)
+    edges = Counter()
+    for a, b, c in t:
+        for x, y in ((a, b), (b, c), (c, a)):
+            edges[(x, y)] += 1
+    assert all(k == 1 for k in edges.values()) and all((y, x) in edges for (x, y) in edges)
+    S = BO.Surface(v, t)
+    assert abs(S.area.sum() - 6 * 5.0 ** 2) < 1e-12
+    assert np.all(np.einsum("ij,ij->i", S.nrm, S.cen) > 0)          # outward
+    assert len(v) - len(edges) // 2 + len(t) == 2                    # Euler characteristic
