@@ -638,6 +638,31 @@ def bem_timing(torch, B, W, subdiv=(4, 3), k0=3.0, steps=3, vsie_grid=48, fp64_s
     out["vsie_same_problem"] = {"workload": w.name, "n": int(w.n), "solve_s": vdt, "iterations": vinfo.iterations,
                                 "far_field_rel_err_vs_series": rel(ff_vsie, ref),
                                 "far_field_rel_diff_vs_bem": rel(ff_vsie, ff_bem)}
+    # the paper's VSIE-versus-BEM density benchmark: nested cubes of 7 and 5 mm, rho2 = rho0/2,
+    # c1 = c2 = c0/1.2, lambda0 = 3 mm; the cuboid VSIE against the BEM on cube surfaces
+    cw = W.nested_cubes(0.125)
+    cop = B.Operator.from_cuboid(cw)
+    t = time.perf_counter()
+    xc, cinfo = cop.solve(cop.plane_wave_rhs(np.array([1.0, 0.0, 0.0]))[0], mode=32, tol=1e-5)
+    torch.cuda.synchronize()
+    cdt = time.perf_counter() - t
+    ff_cub = cop.far_field(xc, dirs).cpu().numpy()
+    cn = cop.n
+    cop.close()
+    cbem = B.BemOperator([W.cube_surface(28, 3.5), W.cube_surface(20, 2.5)], 2.0 * np.pi / 3.0, [1.0, 0.5],
+                         [1.0 / 1.2, 1.0 / 1.2])
+    t = time.perf_counter()
+    xcb, cbinfo = cbem.solve(cbem.rhs([1.0, 0.0, 0.0]), mode=32, tol=1e-5, max_iters=3000)
+    torch.cuda.synchronize()
+    cbdt = time.perf_counter() - t
+    ff_cbem = cbem.far_field(xcb, dirs).cpu().numpy()
+    out["papers_nested_cubes"] = {
+        "vsie": {"discretisation": "cuboid, h = 0.125 mm", "n": int(cn), "solve_s": cdt,
+                 "iterations": cinfo.iterations},
+        "bem": {"discretisation": "P1 on cube surfaces, 0.25 mm", "n": cbem.n, "solve_s": cbdt,
+                "iterations": cbinfo.iterations},
+        "far_field_rel_diff": rel(ff_cub, ff_cbem)}
+    cbem.close()
     return out
 
 
