@@ -152,3 +152,14 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(B, "_lib", None)
     with pytest.raises(ImportError):
         B.load_library(str(tmp_path / "libvsie.so"))
+
+
+def test_bem_binding_checks_its_arguments_on_the_host(lib):
+    from paper_2607_06429_b300.workloads import icosphere
+    s = icosphere(1, 1.0)
+    with pytest.raises(ValueError):
+        B.BemOperator([s], 2.0, [1.5, 3.0], [0.8])          # one layer, two densities
+    with pytest.raises(ValueError):
+        B.BemOperator([s, s, s], 2.0, [1.0] * 3, [1.0] * 3)  # at most two interfaces
+    with pytest.raises(B.VsieError):
+        B.BemOperator([s], -2.0, [1.5], [0.8])               # rejected by the library, no device work
