@@ -292,3 +292,19 @@ def test_cube_surface_is_a_closed_outward_triangulation(n):
     assert abs(S.area.sum() - 6 * 5.0 ** 2) < 1e-12
     assert np.all(np.einsum("ij,ij->i", S.nrm, S.cen) > 0)          # outward
     assert len(v) - len(edges) // 2 + len(t) == 2                    # Euler characteristic
+
+
+def test_near_pairs_are_symmetric_and_contain_every_touching_pair():
+    D = _nested((2, 1), RADII, K0, RHO, C)
+    S = D.S[0]
+    T, Tp = D.near_pairs(0, 0)
+    pairs = set(zip(T.tolist(), Tp.tolist()))
+    assert all((b, a) in pairs for a, b in pairs)
+    touching = {(a, b) for a in range(S.n_tri) for b in range(S.n_tri)
+                if set(S.tri[a].tolist()) & set(S.tri[b].tolist())}
+    assert touching <= pairs
+    d2 = ((S.cen[T] - S.cen[Tp]) ** 2).sum(1)
+    far_ok = d2 < D.near_factor ** 2 * np.maximum(S.diam2[T], S.diam2[Tp])
+    assert all(far_ok[i] or (T[i], Tp[i]) in touching for i in range(T.size))
+    # across the two interfaces (r = 1 and 0.5) no pair is near at this resolution
+    assert D.near_pairs(0, 1)[0].size == 0
